@@ -1,0 +1,178 @@
+/*
+ * cfd.h -- C ABI of the GB300 (sm_103a) implementation of the OpenCFD-SCU
+ * stage right-hand side and TVD-RK3 step (arXiv:2209.15333).
+ *
+ * The library evaluates, on one GPU, the per-stage right-hand side
+ *     L(U) = J * ( - sum_d delta_d fhat_d  +  sum_d D_d Fv_d )
+ * of the curvilinear compressible Navier-Stokes equations (Eq. 1) with
+ * Steger-Warming flux-vector splitting (Eqs. 19-30), UD7 / WENO7 / WENO5 or
+ * hybrid reconstruction switched by the modified Jameson sensor
+ * (Eq. 41-43, Section 2.2.3), masked-WENO5 boundary closures
+ * (Section 2.2.4), 6th/8th-order central viscous terms (Eqs. 9-15,
+ * Section 2.3) and the TVD Runge-Kutta update (Eq. 45).
+ *
+ * Conventions
+ *  - Every call returns a cfd_status; nothing aborts, traps or throws.
+ *  - Fields are double, structure-of-arrays [var][nz][ny][nx], xi (i)
+ *    fastest.  Conserved variables U = (rho, rho u, rho v, rho w, E),
+ *    nondimensional as in Eq. 17 (p = rho T/(gamma Ma^2)).
+ *  - Pointers flagged on_device = 1 are device pointers on the context's
+ *    device; they are read or written on the context's stream.  Host
+ *    pointers are read or written before the call returns.  Caller arrays
+ *    stay caller-owned; the context copies what it keeps.
+ *  - Directions without periodicity exclude nothing; periodic directions
+ *    hold no duplicate end node.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - cfd_step is asynchronous.  Errors detected on the device (a
+ *    non-physical state) surface as CFD_ENONPHYS from the next cfd_sync,
+ *    cfd_get_state, cfd_rhs or cfd_step.
+ */
+#ifndef CFD_H
+#define CFD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cfd_ctx cfd_ctx;
+
+typedef enum {
+    CFD_OK = 0,
+    CFD_EINVAL = -1,        /* bad argument (message in cfd_last_error) */
+    CFD_ENOMEM = -2,        /* device or host allocation failed */
+    CFD_ECUDA = -3,         /* a CUDA runtime call failed */
+    CFD_ENONPHYS = -4,      /* rho <= 0, p <= 0 or a NaN was met on the device */
+    CFD_ETIMEOUT = -5,      /* cfd_sync gave up waiting */
+    CFD_EUNSUPPORTED = -6   /* valid request the library does not implement */
+} cfd_status;
+
+/* boundary condition of one face (reading R12 of the paper's Table 8 case) */
+enum {
+    CFD_BC_PERIODIC = 0,        /* both faces of the direction must say so */
+    CFD_BC_WALL_ISOTHERMAL = 1, /* u = 0 (+ blowing), T = T_wall, p_w = (4 p1 - p2)/3 */
+    CFD_BC_INFLOW = 2,          /* Dirichlet from cfd_set_inflow (xi-low face) */
+    CFD_BC_OUTFLOW_EXTRAP = 3   /* zeroth-order extrapolation of primitives */
+};
+
+/* how the metrics argument of cfd_create is laid out */
+enum {
+    CFD_METRICS_3D = 0,       /* [10][nz][ny][nx] */
+    CFD_METRICS_2D = 1,       /* [10][ny][nx], constant along zeta (extruded grids) */
+    CFD_METRICS_UNIFORM = 2   /* [10], the same at every node */
+};
+
+enum { CFD_SUTHERLAND = 0, CFD_POWER = 1 };                 /* Eq. 15 / power law */
+enum { CFD_UD7 = 0, CFD_WENO5 = 1, CFD_WENO7 = 2, CFD_HYBRID = 3 };  /* Table 2, Eq. 41-43 */
+enum { CFD_METRIC_NODAL = 0, CFD_METRIC_FSP = 1 };
+enum { CFD_FP64 = 0, CFD_FP32_BULK = 1 };
+enum { CFD_SENSOR_PLAIN = 0, CFD_SENSOR_MLP = 1 };
+
+typedef struct {
+    int nx, ny, nz;            /* nodes per direction, each >= 1 (>= 8 if not periodic) */
+    int bc_lo[3], bc_hi[3];    /* per direction xi, eta, zeta: CFD_BC_* */
+    int metric_layout;         /* CFD_METRICS_* */
+} cfd_grid;
+
+typedef struct {
+    double gamma, Re, Ma, Pr;  /* Re <= 0: inviscid (Eq. 17-18 parameters) */
+    double T_wall;             /* nondimensional wall temperature */
+    double T_ref;              /* reference temperature in K (Sutherland, Eq. 15) */
+    int visc_law;              /* CFD_SUTHERLAND (S = 110.4 K) or CFD_POWER */
+    double visc_omega;         /* power-law exponent: mu = T^omega */
+    int scheme;                /* CFD_UD7, CFD_WENO5, CFD_WENO7, CFD_HYBRID */
+    double theta1, theta2;     /* hybrid thresholds (paper: 0.02, 0.1) */
+    int visc_order;            /* 6 or 8 */
+    int metric_mode;           /* CFD_METRIC_NODAL (paper) */
+    int precision;             /* CFD_FP64 or CFD_FP32_BULK */
+    int sensor;                /* CFD_SENSOR_PLAIN or CFD_SENSOR_MLP */
+    double weno_eps;           /* epsilon of the WENO weights (1e-6) */
+} cfd_params;
+
+/* cfd_params with the paper's defaults: gamma 1.4, Pr 0.72, theta 0.02/0.1,
+   8th-order viscous terms, hybrid scheme, FP64, plain sensor, eps 1e-6. */
+void cfd_default_params(cfd_params* p);
+
+/*
+ * Create a context on the current CUDA device.  metrics: xi_x, xi_y, xi_z,
+ * eta_x, eta_y, eta_z, zeta_x, zeta_y, zeta_z, J (Eq. 3-4) in the layout
+ * grid->metric_layout, host memory (metrics_on_device = 0) or device memory.
+ * stream: a cudaStream_t, or NULL for a stream the context creates.
+ * Allocates every device buffer the step needs (about 40 doubles per node
+ * in FP64).  Errors: EINVAL (sizes, BC pairs, params), ENOMEM, ECUDA,
+ * EUNSUPPORTED (FSP metric mode, MLP sensor without weights).
+ */
+cfd_status cfd_create(cfd_ctx** out, const cfd_grid* grid, const double* metrics,
+                      int metrics_on_device, const cfd_params* params, void* stream);
+
+/* Inflow profile for CFD_BC_INFLOW on the xi-low face: prim[5][ny] =
+   rho, u, v, w, p per eta index, the same for every zeta (host memory). */
+cfd_status cfd_set_inflow(cfd_ctx* ctx, const double* prim);
+
+/* Wall-normal blowing/suction on the eta-low wall (reading R12):
+   v_n = amp sin(2 pi (x-x0)/(x1-x0)) cos(2 pi m z/Lz) sin(omega t) for x in
+   [x0, x1]; wall_x[nx], wall_z[nz] are the wall node coordinates (host). */
+cfd_status cfd_set_blowing(cfd_ctx* ctx, double amp, double x0, double x1, double omega, int m,
+                           double Lz, const double* wall_x, const double* wall_z);
+
+/* Copy U [5][nz][ny][nx] into the context and apply the boundary
+   conditions at the context time.  block: 0 (single-block contexts). */
+cfd_status cfd_set_state(cfd_ctx* ctx, int block, const double* U, int on_device);
+
+/* Copy the current state out. */
+cfd_status cfd_get_state(cfd_ctx* ctx, int block, double* U, int on_device);
+
+/* L(U) of the current state (one stage right-hand side, Eq. 44); zero on
+   boundary nodes of non-periodic directions. */
+cfd_status cfd_rhs(cfd_ctx* ctx, int block, double* dUdt, int on_device);
+
+/* nsteps TVD-RK3 steps (Eq. 45) with a fixed dt; boundary conditions after
+   every stage.  Replays a captured CUDA graph of one step. */
+cfd_status cfd_step(cfd_ctx* ctx, double dt, int nsteps);
+
+/* dt = cfl / max_n sum_d (|d_x u + d_y v + d_z w| + c |grad d|) of the
+   current state (reading R16), computed on the device. */
+cfd_status cfd_cfl_dt(cfd_ctx* ctx, int block, double cfl, double* dt);
+
+/* Scheme class per node (0 UD7, 1 WENO7, 2 WENO5) of the last evaluation. */
+cfd_status cfd_get_flags(cfd_ctx* ctx, int block, unsigned char* cls, int on_device);
+
+/* Use these node classes instead of the sensor (cls = NULL: back to the
+   sensor).  For comparing arithmetic with the hybrid switch held fixed. */
+cfd_status cfd_force_flags(cfd_ctx* ctx, int block, const unsigned char* cls, int on_device);
+
+/* Simulation time of the context (used by the blowing boundary condition). */
+cfd_status cfd_get_time(cfd_ctx* ctx, double* t);
+cfd_status cfd_set_time(cfd_ctx* ctx, double t);
+
+/* Wait for the context's stream for at most timeout_s seconds: CFD_OK,
+   CFD_ETIMEOUT (work still running; call again), CFD_ENONPHYS or CFD_ECUDA. */
+cfd_status cfd_sync(cfd_ctx* ctx, double timeout_s);
+
+/* Message of the last failure (never NULL; static storage if ctx is NULL). */
+const char* cfd_last_error(const cfd_ctx* ctx);
+
+/* Number of kernel launches issued by the context so far (all entry points). */
+long long cfd_launch_count(const cfd_ctx* ctx);
+
+/* Device probe, not a step of the method: measured dense FMA throughput of
+   the current device in TFLOP/s (2 flops per FMA) for precision CFD_FP64 or
+   CFD_FP32_BULK (float), used as the ALU roofline denominator.  Runs a
+   fixed-length kernel of a few milliseconds on its own stream. */
+cfd_status cfd_fma_peak(int precision, double* tflops);
+
+/* Instrumentation, not a step of the method: run `reps` right-hand-side
+   evaluations of the current state without a graph, with CUDA events between
+   the kernels on the context stream, and return the mean milliseconds per
+   evaluation of: [0] primitives, [1] sensor, [2] viscous fluxes,
+   [3] xi sweep, [4] eta sweep, [5] zeta sweep (incl. J scaling).
+   ms must hold CFD_PROFILE_KERNELS doubles. */
+#define CFD_PROFILE_KERNELS 6
+cfd_status cfd_profile_stage(cfd_ctx* ctx, int reps, double* ms);
+
+/* Free every device buffer and the graph; NULL is allowed. */
+void cfd_destroy(cfd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

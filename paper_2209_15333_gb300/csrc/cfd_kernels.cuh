@@ -1,0 +1,834 @@
+// cfd_kernels.cuh -- sm_103a kernels of the OpenCFD-SCU stage right-hand side
+// (arXiv:2209.15333, Sections 2.1-2.4).
+//
+// Data layout in HBM (structure of arrays, i fastest, N = nx*ny*nz):
+//   U, Un        [5][N]  double  conserved state (stage / step start)
+//   P            [7][N]  real    rho, u, v, w, p, T, c
+//   cls          [N]     uint8   sensor class (0 UD7, 1 WENO7, 2 WENO5)
+//   Fv           [12][N] real    viscous fluxes at nodes, [4*d + row]
+//   R            [5][N]  real    accumulated -sum delta fhat + sum D Fv
+//   met          [31][M] double  metrics per metric point (M = N, nx*ny or 1):
+//                                0-8 raw (xi_x..zeta_z), 9 J, 10-18 alpha = raw/J,
+//                                19-21 sigma_d = |alpha_d|, 22-30 k_d = alpha_d/sigma_d
+#pragma once
+#include <cstdint>
+
+#include "weno_coeffs.cuh"
+
+namespace cfdk {
+
+enum { M_RAW = 0, M_J = 9, M_ALPHA = 10, M_SIG = 19, M_K = 22, M_COUNT = 31 };
+
+struct Geo {
+    int nx, ny, nz;
+    long long N;
+    int per[3];
+    int bc_lo[3], bc_hi[3];
+    int mlayout;          // 0 3-D, 1 2-D, 2 uniform
+    long long M;          // metric points
+    const double* met;    // [31][M]
+};
+
+struct Phys {
+    double gamma, gm1, inv_gm1, Ma, gMa2, inv2g;
+    double invRe, kcoef;  // 1/Re, 1/((gamma-1) Ma^2 Pr Re)
+    double Tw;
+    int viscous, visc_law;
+    double omega, suth_s;  // power exponent, S/T_ref
+    int scheme;            // 0 UD7, 1 WENO5, 2 WENO7, 3 HYBRID
+    double th1, th2, eps;
+    int vorder;
+};
+
+struct BCData {
+    const double* inflow;  // [5][ny] or null
+    double amp, x0, x1, omega, Lz;
+    int m;
+    const double* wall_x;  // [nx]
+    const double* wall_z;  // [nz]
+};
+
+__device__ __forceinline__ int wrapi(int m, int n)
+{
+    int r = m % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ long long midx(const Geo& g, int i, int j, long long n)
+{
+    return g.mlayout == 0 ? n : (g.mlayout == 1 ? (long long)i + (long long)g.nx * j : 0LL);
+}
+
+__device__ __forceinline__ double metv(const Geo& g, int e, long long mi)
+{
+    return __ldg(g.met + (long long)e * g.M + mi);
+}
+
+__device__ __forceinline__ bool is_bnd(const Geo& g, int i, int j, int k)
+{
+    return (!g.per[0] && (i == 0 || i == g.nx - 1)) || (!g.per[1] && (j == 0 || j == g.ny - 1)) ||
+           (!g.per[2] && (k == 0 || k == g.nz - 1));
+}
+
+// ---------------------------------------------------------------------------
+// metric set-up: derived quantities per metric point (Eq. 19, 22, 27)
+// ---------------------------------------------------------------------------
+__global__ void k_metric_derive(double* met, long long M)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < M;
+         t += (long long)gridDim.x * blockDim.x) {
+        double J = met[M_J * M + t];
+        for (int d = 0; d < 3; ++d) {
+            double a[3];
+            for (int e = 0; e < 3; ++e) {
+                a[e] = met[(3 * d + e) * M + t] / J;
+                met[(M_ALPHA + 3 * d + e) * M + t] = a[e];
+            }
+            double s = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            met[(M_SIG + d) * M + t] = s;
+            for (int e = 0; e < 3; ++e) met[(M_K + 3 * d + e) * M + t] = a[e] / s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// primitive recovery (Eq. 5, 8, 16, 17).  The operation order matches the
+// oracle's (no contraction), so that p -- and with it the sensor's class
+// decisions -- are bit-identical to a plain IEEE evaluation.
+// ---------------------------------------------------------------------------
+template <class RT>
+__global__ void k_prim(Geo g, Phys ph, const double* __restrict__ U, RT* __restrict__ P,
+                       int* __restrict__ err)
+{
+    const long long N = g.N;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        double rho = U[n];
+        double u = __ddiv_rn(U[N + n], rho);
+        double v = __ddiv_rn(U[2 * N + n], rho);
+        double w = __ddiv_rn(U[3 * N + n], rho);
+        double q2 = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
+        double ke = __dmul_rn(__dmul_rn(0.5, rho), q2);
+        double p = __dmul_rn(ph.gm1, __dsub_rn(U[4 * N + n], ke));
+        double T = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(ph.gamma, ph.Ma), ph.Ma), p), rho);
+        double c = __ddiv_rn(__dsqrt_rn(T), ph.Ma);
+        if (!(rho > 0.0) || !(p > 0.0) || !(T < 1e300) || !(fabs(u) + fabs(v) + fabs(w) < 1e300))
+            *err = 1;
+        P[n] = (RT)rho;
+        P[N + n] = (RT)u;
+        P[2 * N + n] = (RT)v;
+        P[3 * N + n] = (RT)w;
+        P[4 * N + n] = (RT)p;
+        P[5 * N + n] = (RT)T;
+        P[6 * N + n] = (RT)c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// modified Jameson sensor (Eq. 42-43), evaluated in double with the same
+// operation order as a plain IEEE evaluation, so class decisions match.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sensor_phi(double pm, double p0, double pp)
+{
+    double num = fabs(__dsub_rn(__dadd_rn(-pm, __dmul_rn(2.0, p0)), pp));
+    double den = __dadd_rn(__dadd_rn(pm, __dmul_rn(2.0, p0)), pp);
+    return __ddiv_rn(num, den);
+}
+
+__global__ void k_sensor(Geo g, Phys ph, const double* __restrict__ p, uint8_t* __restrict__ cls)
+{
+    const long long N = g.N;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(n % nx);
+        int j = (int)((n / nx) % ny);
+        int k = (int)(n / ((long long)nx * ny));
+        double p0 = p[n];
+        double phi[3];
+        const int pos[3] = {i, j, k};
+        const int nd[3] = {nx, ny, nz};
+        const long long st[3] = {1, nx, (long long)nx * ny};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int m = pos[d];
+            if (!g.per[d] && (m == 0 || m == nd[d] - 1)) {
+                phi[d] = 0.0;
+                continue;
+            }
+            long long nm = n + (long long)(wrapi(m - 1, nd[d]) - m) * st[d];
+            long long np = n + (long long)(wrapi(m + 1, nd[d]) - m) * st[d];
+            phi[d] = sensor_phi(p[nm], p0, p[np]);
+        }
+        double th = __dadd_rn(__dadd_rn(phi[0], phi[1]), phi[2]);
+        cls[n] = th <= ph.th1 ? 0 : (th <= ph.th2 ? 1 : 2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Steger-Warming split fluxes at one node (Eq. 20-30, Eq. 23 as corrected).
+// With s = l4 + l5 and dl = l5 - l4 the corrected Eq. 23 reads
+//   f0 = a (2(g-1) l1 + s),  f_i = u_i f0 + a c dl k_i,
+//   f4 = a ((g-1) l1 |u|^2 + s H + c dl (u.k)),   a = rho/(2 g),
+// with H = |u|^2/2 + c^2/(g-1) (the same algebra, fewer operations).
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void sw_split(const Phys& ph, R rho, R u, R v, R w, R c, R k1, R k2, R k3,
+                                         R sig, R fp[5], R fm[5])
+{
+    const R gm1 = (R)ph.gm1;
+    R uk = k1 * u + k2 * v + k3 * w;
+    R V = sig * uk;
+    R cs = c * sig;
+    R l4 = V - cs, l5 = V + cs;
+    R q2 = u * u + v * v + w * w;
+    R H = (R)0.5 * q2 + c * c * (R)ph.inv_gm1;
+    R a = rho * (R)ph.inv2g;
+    R gq = gm1 * q2;
+    R ac = a * c;
+    {
+        R l1 = V > (R)0 ? V : (R)0;
+        R a4 = l4 > (R)0 ? l4 : (R)0;
+        R a5 = l5 > (R)0 ? l5 : (R)0;
+        R s = a4 + a5, dl = a5 - a4;
+        R f0 = a * ((R)2 * gm1 * l1 + s);
+        R t = ac * dl;
+        fp[0] = f0;
+        fp[1] = u * f0 + t * k1;
+        fp[2] = v * f0 + t * k2;
+        fp[3] = w * f0 + t * k3;
+        fp[4] = a * (l1 * gq + s * H) + t * uk;
+    }
+    {
+        R l1 = V < (R)0 ? V : (R)0;
+        R a4 = l4 < (R)0 ? l4 : (R)0;
+        R a5 = l5 < (R)0 ? l5 : (R)0;
+        R s = a4 + a5, dl = a5 - a4;
+        R f0 = a * ((R)2 * gm1 * l1 + s);
+        R t = ac * dl;
+        fm[0] = f0;
+        fm[1] = u * f0 + t * k1;
+        fm[2] = v * f0 + t * k2;
+        fm[3] = w * f0 + t * k3;
+        fm[4] = a * (l1 * gq + s * H) + t * uk;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reconstructions at the face j+1/2 from 7 upwind-ordered values
+// v[0..6] = f_{j-3..j+3} (plus side) or f_{j+4..j-2} (minus side, mirrored)
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R ud7(const R v[7])
+{
+    // Eq. 41
+    return ((R)(-3.0 / 420.0)) * v[0] + ((R)(25.0 / 420.0)) * v[1] + ((R)(-101.0 / 420.0)) * v[2] +
+           ((R)(319.0 / 420.0)) * v[3] + ((R)(214.0 / 420.0)) * v[4] + ((R)(-38.0 / 420.0)) * v[5] +
+           ((R)(4.0 / 420.0)) * v[6];
+}
+
+// Smoothness indicator as a weighted sum of squares of constant-annihilating
+// linear combinations (derivative coefficients of the sub-stencil polynomial):
+// its rounding error scales with |f| sqrt(beta) rather than |f|^2.
+template <class R, int NR, int NS>
+__device__ __forceinline__ R beta_rows(const double (&S)[NS], const double (&SD)[NR], const R* f)
+{
+    constexpr int r = NS / NR;
+    R b = (R)0;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        R h = (R)0;
+#pragma unroll
+        for (int l = 0; l < r; ++l) h += (R)S[i * r + l] * f[l];
+        b += (R)SD[i] * (h * h);
+    }
+    return b;
+}
+
+// WENO7 (Balsara-Shu) on v[0..6]; one division (weights over a common
+// denominator, the division hoisting the paper describes).
+template <class R>
+__device__ __forceinline__ R weno7(const R v[7], R eps)
+{
+    constexpr double D[4] = W7_D;
+    constexpr double SD[3] = W7_SD;
+    constexpr double C0[4] = W7_C0, C1[4] = W7_C1, C2[4] = W7_C2, C3[4] = W7_C3;
+    constexpr double S0[12] = W7_S0, S1[12] = W7_S1, S2[12] = W7_S2, S3[12] = W7_S3;
+    R q0 = (R)C0[0] * v[0] + (R)C0[1] * v[1] + (R)C0[2] * v[2] + (R)C0[3] * v[3];
+    R q1 = (R)C1[0] * v[1] + (R)C1[1] * v[2] + (R)C1[2] * v[3] + (R)C1[3] * v[4];
+    R q2 = (R)C2[0] * v[2] + (R)C2[1] * v[3] + (R)C2[2] * v[4] + (R)C2[3] * v[5];
+    R q3 = (R)C3[0] * v[3] + (R)C3[1] * v[4] + (R)C3[2] * v[5] + (R)C3[3] * v[6];
+    R b0 = eps + beta_rows<R>(S0, SD, v + 0);
+    R b1 = eps + beta_rows<R>(S1, SD, v + 1);
+    R b2 = eps + beta_rows<R>(S2, SD, v + 2);
+    R b3 = eps + beta_rows<R>(S3, SD, v + 3);
+    R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2, t3 = b3 * b3;
+    R p01 = t0 * t1, p23 = t2 * t3;
+    R w0 = (R)D[0] * t1 * p23, w1 = (R)D[1] * t0 * p23;
+    R w2 = (R)D[2] * t3 * p01, w3 = (R)D[3] * t2 * p01;
+    return (w0 * q0 + w1 * q1 + w2 * q2 + w3 * q3) / (w0 + w1 + w2 + w3);
+}
+
+// WENO5 (Jiang-Shu) on v[1..5] = f_{j-2..j+2}; mask bit k drops sub-stencil k
+// (the boundary closure of Section 2.2.4).
+template <class R>
+__device__ __forceinline__ R weno5(const R v[7], R eps, int mask)
+{
+    constexpr double D[3] = W5_D;
+    constexpr double SD[2] = W5_SD;
+    constexpr double C0[3] = W5_C0, C1[3] = W5_C1, C2[3] = W5_C2;
+    constexpr double S0[6] = W5_S0, S1[6] = W5_S1, S2[6] = W5_S2;
+    R q0 = (R)C0[0] * v[1] + (R)C0[1] * v[2] + (R)C0[2] * v[3];
+    R q1 = (R)C1[0] * v[2] + (R)C1[1] * v[3] + (R)C1[2] * v[4];
+    R q2 = (R)C2[0] * v[3] + (R)C2[1] * v[4] + (R)C2[2] * v[5];
+    R b0 = eps + beta_rows<R>(S0, SD, v + 1);
+    R b1 = eps + beta_rows<R>(S1, SD, v + 2);
+    R b2 = eps + beta_rows<R>(S2, SD, v + 3);
+    R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2;
+    R w0 = (mask & 1) ? (R)0 : (R)D[0] * t1 * t2;
+    R w1 = (mask & 2) ? (R)0 : (R)D[1] * t0 * t2;
+    R w2 = (mask & 4) ? (R)0 : (R)D[2] * t0 * t1;
+    return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+// one face value from upwind-ordered values; use: 0 UD7, 1 WENO7, 2 WENO5
+template <class R>
+__device__ __forceinline__ R recon(int use, const R v[7], R eps, int mask)
+{
+    if (use == 0) return ud7<R>(v);
+    if (use == 1) return weno7<R>(v, eps);
+    return weno5<R>(v, eps, mask);
+}
+
+// Face flux at j+1/2 of component q from the 8 node values f_{j-3..j+4}.
+template <class R>
+__device__ __forceinline__ R face_flux(int use, const R fp8[8], const R fm8[8], R eps, int maskp, int maskm)
+{
+    R vp[7], vm[7];
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+        vp[o] = fp8[o];
+        vm[o] = fm8[7 - o];
+    }
+    return recon<R>(use, vp, eps, maskp) + recon<R>(use, vm, eps, maskm);
+}
+
+// scheme class of face j+1/2 (nodes j-3..j+4 of one line): returns use and masks.
+// Non-periodic lines: a face whose stencil leaves [0, n-1] uses masked WENO5.
+__device__ __forceinline__ int face_use(const Phys& ph, int per, int n, int j, int cmax, int* maskp,
+                                        int* maskm)
+{
+    *maskp = 0;
+    *maskm = 0;
+    if (!per && (j - 3 < 0 || j + 4 > n - 1)) {
+        int mp = 0, mm = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // plus side: nodes j-2+k .. j+k ; minus side: nodes j+1-k .. j+3-k
+            if (j - 2 + k < 0 || j + k > n - 1) mp |= 1 << k;
+            if (j + 1 - k < 0 || j + 3 - k > n - 1) mm |= 1 << k;
+        }
+        *maskp = mp;
+        *maskm = mm;
+        return 2;
+    }
+    switch (ph.scheme) {
+    case 0: return 0;
+    case 1: return 2;
+    case 2: return 1;
+    default: return cmax;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// central first derivative in index space with the closures of Section 2.3
+// ---------------------------------------------------------------------------
+template <class R, class Ld>
+__device__ __forceinline__ R dcentral(int order, int per, int n, int m, Ld f)
+{
+    if (per) {
+        if (order == 8)
+            return ((R)(672.0 / 840.0)) * (f(wrapi(m + 1, n)) - f(wrapi(m - 1, n))) +
+                   ((R)(-168.0 / 840.0)) * (f(wrapi(m + 2, n)) - f(wrapi(m - 2, n))) +
+                   ((R)(32.0 / 840.0)) * (f(wrapi(m + 3, n)) - f(wrapi(m - 3, n))) +
+                   ((R)(-3.0 / 840.0)) * (f(wrapi(m + 4, n)) - f(wrapi(m - 4, n)));
+        return ((R)(45.0 / 60.0)) * (f(wrapi(m + 1, n)) - f(wrapi(m - 1, n))) +
+               ((R)(-9.0 / 60.0)) * (f(wrapi(m + 2, n)) - f(wrapi(m - 2, n))) +
+               ((R)(1.0 / 60.0)) * (f(wrapi(m + 3, n)) - f(wrapi(m - 3, n)));
+    }
+    if (m == 0) return (R)(-1.5) * f(0) + (R)2 * f(1) - (R)0.5 * f(2);
+    if (m == n - 1) return (R)1.5 * f(n - 1) - (R)2 * f(n - 2) + (R)0.5 * f(n - 3);
+    if (m == 1 || m == n - 2) return (R)0.5 * (f(m + 1) - f(m - 1));
+    if (m == 2 || m == n - 3)
+        return ((R)(8.0 / 12.0)) * (f(m + 1) - f(m - 1)) - ((R)(1.0 / 12.0)) * (f(m + 2) - f(m - 2));
+    if (m == 3 || m == n - 4 || order == 6)
+        return ((R)(45.0 / 60.0)) * (f(m + 1) - f(m - 1)) + ((R)(-9.0 / 60.0)) * (f(m + 2) - f(m - 2)) +
+               ((R)(1.0 / 60.0)) * (f(m + 3) - f(m - 3));
+    return ((R)(672.0 / 840.0)) * (f(m + 1) - f(m - 1)) + ((R)(-168.0 / 840.0)) * (f(m + 2) - f(m - 2)) +
+           ((R)(32.0 / 840.0)) * (f(m + 3) - f(m - 3)) + ((R)(-3.0 / 840.0)) * (f(m + 4) - f(m - 4));
+}
+
+// ---------------------------------------------------------------------------
+// viscous fluxes at nodes (Eqs. 9-15 with readings R13-R15)
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R viscosity(const Phys& ph, R T)
+{
+    if (ph.visc_law == 1) return (R)pow((double)T, ph.omega);
+    R s = (R)ph.suth_s;
+    return T * sqrt(T) * ((R)1 + s) / (T + s);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_visc_flux(Geo g, Phys ph, const R* __restrict__ P, R* __restrict__ Fv)
+{
+    const long long N = g.N;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int ord = ph.vorder;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(n % nx);
+        int j = (int)((n / nx) % ny);
+        int k = (int)(n / ((long long)nx * ny));
+        const long long st[3] = {1, nx, (long long)nx * ny};
+        const int pos[3] = {i, j, k};
+        const int nd[3] = {nx, ny, nz};
+        // dq[var][d]: var = u, v, w, T (P rows 1, 2, 3, 5)
+        R dq[4][3];
+#pragma unroll
+        for (int var = 0; var < 4; ++var) {
+            const R* f = P + (long long)(var < 3 ? var + 1 : 5) * N;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const long long base = n - (long long)pos[d] * st[d];
+                const long long s = st[d];
+                dq[var][d] = dcentral<R>(ord, g.per[d], nd[d], pos[d],
+                                         [&](int m) { return __ldg(f + base + (long long)m * s); });
+            }
+        }
+        const long long mi = midx(g, i, j, n);
+        R mraw[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) mraw[e] = (R)metv(g, M_RAW + e, mi);
+        R gr[4][3];
+#pragma unroll
+        for (int var = 0; var < 4; ++var)
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+                gr[var][x] = mraw[x] * dq[var][0] + mraw[3 + x] * dq[var][1] + mraw[6 + x] * dq[var][2];
+        R T = P[5 * N + n];
+        R mu = viscosity<R>(ph, T);
+        R mr = mu * (R)ph.invRe;
+        R div = gr[0][0] + gr[1][1] + gr[2][2];
+        R tau[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? ((R)(2.0 / 3.0)) * div : (R)0));
+        R kc = mu * (R)ph.kcoef;
+        R u = P[N + n], v = P[2 * N + n], w = P[3 * N + n];
+        R Th[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Th[a] = u * tau[a][0] + v * tau[a][1] + w * tau[a][2] + kc * gr[3][a];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            R a0 = (R)metv(g, M_ALPHA + 3 * d, mi), a1 = (R)metv(g, M_ALPHA + 3 * d + 1, mi),
+              a2 = (R)metv(g, M_ALPHA + 3 * d + 2, mi);
+#pragma unroll
+            for (int row = 0; row < 3; ++row)
+                Fv[(long long)(4 * d + row) * N + n] = a0 * tau[0][row] + a1 * tau[1][row] + a2 * tau[2][row];
+            Fv[(long long)(4 * d + 3) * N + n] = a0 * Th[0] + a1 * Th[1] + a2 * Th[2];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the directional sweeps
+// ---------------------------------------------------------------------------
+struct SweepArgs {
+    Geo g;
+    Phys ph;
+    const void* P;         // [7][N] real
+    const uint8_t* cls;    // [N] or null (non-hybrid)
+    const void* Fv;        // [12][N] real or null (inviscid)
+    void* R;               // [5][N] real accumulator
+    // epilogue of the last sweep
+    const double* U;       // stage state  U^(k)
+    const double* Un;      // step state   U^n
+    double* Uout;          // RK output (may alias U or Un)
+    double* Lout;          // L(U) output (rhs mode) or null
+    const double* dt;      // device scalar
+    double rk_a, rk_b;     // U_out = a Un + b (U + dt L)
+    int seg_len;           // streaming segment length
+};
+
+// epilogue modes
+enum { EP_STORE = 0, EP_ACCUM = 1, EP_FINAL_RHS = 2, EP_FINAL_RK = 3 };
+
+template <class R, int EP>
+__device__ __forceinline__ void epilogue(const SweepArgs& A, long long n, int i, int j, int k, const R val[5])
+{
+    const long long N = A.g.N;
+    R* Racc = (R*)A.R;
+    if (EP == EP_STORE) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Racc[q * N + n] = val[q];
+    } else if (EP == EP_ACCUM) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Racc[q * N + n] += val[q];
+    } else {
+        const bool bnd = is_bnd(A.g, i, j, k);
+        const double J = metv(A.g, M_J, midx(A.g, i, j, n));
+        if (EP == EP_FINAL_RHS) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) A.Lout[q * N + n] = bnd ? 0.0 : J * (double)(Racc[q * N + n] + val[q]);
+        } else {
+            if (bnd) return;  // boundary nodes are set by the boundary conditions
+            const double dt = *A.dt;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                double L = J * (double)(Racc[q * N + n] + val[q]);
+                double uk = A.U[q * N + n];
+                double un = A.rk_a != 0.0 ? A.Un[q * N + n] : 0.0;
+                A.Uout[q * N + n] = A.rk_a * un + A.rk_b * (uk + dt * L);
+            }
+        }
+    }
+}
+
+// viscous contribution D_d Fv_d at node position m of a line (4 rows -> val[1..4])
+template <class R>
+__device__ __forceinline__ void visc_div(const SweepArgs& A, int d, long long base, long long stride, int n, int m,
+                                         R val[5])
+{
+    const R* Fv = (const R*)A.Fv;
+    const long long N = A.g.N;
+#pragma unroll
+    for (int row = 0; row < 4; ++row) {
+        const R* f = Fv + (long long)(4 * d + row) * N + base;
+        val[row + 1] += dcentral<R>(A.ph.vorder, A.g.per[d], n, m,
+                                    [&](int mm) { return __ldg(f + (long long)mm * stride); });
+    }
+}
+
+// split fluxes of node (i, j, k) along direction d
+template <class R>
+__device__ __forceinline__ void node_split(const SweepArgs& A, int d, long long n, int i, int j, R fp[5], R fm[5])
+{
+    const R* P = (const R*)A.P;
+    const long long N = A.g.N;
+    const long long mi = midx(A.g, i, j, n);
+    R rho = P[n], u = P[N + n], v = P[2 * N + n], w = P[3 * N + n], c = P[6 * N + n];
+    R k1 = (R)metv(A.g, M_K + 3 * d, mi), k2 = (R)metv(A.g, M_K + 3 * d + 1, mi),
+      k3 = (R)metv(A.g, M_K + 3 * d + 2, mi), sg = (R)metv(A.g, M_SIG + d, mi);
+    sw_split<R>(A.ph, rho, u, v, w, c, k1, k2, k3, sg, fp, fm);
+}
+
+// xi sweep: one CTA per segment of BX nodes of one x-line, halo of 4 nodes.
+template <class R, int BX, int EP>
+__global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
+{
+    __shared__ R sf[10][BX + 8];
+    __shared__ R sh[5][BX + 1];
+    __shared__ uint8_t sc[BX + 8];
+    const Geo& g = A.g;
+    const int n = g.nx;
+    const int per = g.per[0];
+    const int j = blockIdx.y, k = blockIdx.z;
+    const int lo = per ? 0 : 1;                 // first node that gets a right-hand side
+    const int i0 = lo + blockIdx.x * BX;
+    const long long row = (long long)n * (j + (long long)g.ny * k);
+    const int t = threadIdx.x;
+    for (int s = t; s < BX + 8; s += BX) {
+        int i = i0 - 4 + s;
+        bool ok = per || (i >= 0 && i < n);
+        R fp[5], fm[5];
+        uint8_t c = 0;
+        if (ok) {
+            int ii = per ? wrapi(i, n) : i;
+            node_split<R>(A, 0, row + ii, ii, j, fp, fm);
+            if (A.cls) c = A.cls[row + ii];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) fp[q] = fm[q] = (R)0;
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            sf[q][s] = fp[q];
+            sf[5 + q][s] = fm[q];
+        }
+        sc[s] = c;
+    }
+    __syncthreads();
+    // faces: thread t -> face (i0+t)+1/2 stored at sh[.][t+1]; face (i0-1)+1/2 at sh[.][0]
+    for (int f = t; f < BX + 1; f += BX) {
+        int slot = f == BX ? 0 : f + 1;
+        int jf = i0 - 1 + slot;  // face jf + 1/2
+        int s0 = slot;           // smem index of node jf-3
+        bool need = per ? true : (jf >= 0 && jf <= n - 2);
+        if (!need || jf - (i0 - 1) > min(BX, (per ? n : n - 1) - i0)) continue;
+        int cm = 0;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) cm = max(cm, (int)sc[s0 + o]);
+        int mp, mm;
+        int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            R p8[8], m8[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                p8[o] = sf[q][s0 + o];
+                m8[o] = sf[5 + q][s0 + o];
+            }
+            sh[q][slot] = face_flux<R>(use, p8, m8, (R)A.ph.eps, mp, mm);
+        }
+    }
+    __syncthreads();
+    const int hi = per ? n : n - 1;
+    int i = i0 + t;
+    if (i < hi) {
+        long long nn = row + i;
+        R val[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) val[q] = -(sh[q][t + 1] - sh[q][t]);
+        if (A.Fv) visc_div<R>(A, 0, row, 1, n, i, val);
+        epilogue<R, EP>(A, nn, i, j, k, val);
+    }
+    // zero the non-periodic boundary nodes of the accumulator
+    if (EP == EP_STORE && !per && blockIdx.x == 0 && t < 2) {
+        int ib = t == 0 ? 0 : n - 1;
+        R* Racc = (R*)A.R;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Racc[q * g.N + row + ib] = (R)0;
+    }
+}
+
+// eta / zeta sweep: each warp owns 32 consecutive x of one line family and
+// streams along the sweep direction, keeping the split fluxes of the last 8
+// nodes in a per-lane shared-memory ring (every lane touches only its own
+// column, so no synchronisation is needed).
+template <class R, int DIR, int EP>
+__global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geo& g = A.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    R* ring = reinterpret_cast<R*>(smem_raw) + (size_t)warp * (8 * 10 * 32);
+    const int nx = g.nx;
+    const int n = DIR == 1 ? g.ny : g.nz;
+    const int nother = DIR == 1 ? g.nz : g.ny;
+    const long long stride = DIR == 1 ? (long long)nx : (long long)nx * g.ny;
+    const int per = g.per[DIR];
+    const int lo = per ? 0 : 1, hi = per ? n : n - 1;  // right-hand-side nodes [lo, hi)
+    const int S = A.seg_len;
+    const int nseg = (hi - lo + S - 1) / S;
+    const int nxc = (nx + 31) / 32;
+    const long long wid = (long long)blockIdx.x * 4 + warp;
+    const int xc = (int)(wid % nxc);
+    const long long rest = wid / nxc;
+    const int o = (int)(rest % nother);
+    const long long seg = rest / nother;
+    if (seg >= nseg) return;
+    const int i = xc * 32 + lane;
+    const bool lane_ok = i < nx;
+    const int m0 = lo + (int)seg * S;
+    const int m1 = min(m0 + S, hi);
+    // node (i, m, o): j = m, k = o (DIR 1) or j = o, k = m (DIR 2)
+    const long long base = DIR == 1 ? (long long)i + (long long)nx * g.ny * o : (long long)i + (long long)nx * o;
+    R fprev[5];
+    unsigned long long cwin = 0ull;
+    const int nsteps = (m1 - m0) + 8;
+    for (int s = 0; s < nsteps; ++s) {
+        const int m = m0 - 4 + s;
+        const int slot = s & 7;
+        R fp[5], fm[5];
+        uint8_t c = 0;
+        bool ok = lane_ok && (per || (m >= 0 && m < n));
+        if (ok) {
+            int mm = per ? wrapi(m, n) : m;
+            long long nn = base + (long long)mm * stride;
+            int jj = DIR == 1 ? mm : o;
+            node_split<R>(A, DIR, nn, i, jj, fp, fm);
+            if (A.cls) c = A.cls[nn];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) fp[q] = fm[q] = (R)0;
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            ring[(slot * 10 + q) * 32 + lane] = fp[q];
+            ring[(slot * 10 + 5 + q) * 32 + lane] = fm[q];
+        }
+        cwin = (cwin << 8) | c;
+        if (s >= 7) {
+            const int jf = m - 4;  // face jf + 1/2 with nodes m-7 .. m
+            int cm = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) cm = max(cm, (int)((cwin >> (8 * b)) & 0xff));
+            int mp, mm;
+            int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+            R fh[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                R p8[8], m8[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    int sl = (s - 7 + b) & 7;
+                    p8[b] = ring[(sl * 10 + q) * 32 + lane];
+                    m8[b] = ring[(sl * 10 + 5 + q) * 32 + lane];
+                }
+                fh[q] = face_flux<R>(use, p8, m8, (R)A.ph.eps, mp, mm);
+            }
+            if (s >= 8 && lane_ok) {
+                const int mn = m - 4;  // node
+                const long long nn = base + (long long)mn * stride;
+                R val[5];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) val[q] = -(fh[q] - fprev[q]);
+                if (A.Fv) {
+                    const long long lb = base;
+                    visc_div<R>(A, DIR, lb, stride, n, mn, val);
+                }
+                const int jj = DIR == 1 ? mn : o, kk = DIR == 1 ? o : mn;
+                epilogue<R, EP>(A, nn, i, jj, kk, val);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) fprev[q] = fh[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// boundary conditions on the conserved state (reading R12), one direction per
+// launch, faces lo and hi; applied in the order xi, eta, zeta.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cons_prim(const Phys& ph, const double* U, long long N, long long n, double o[5])
+{
+    double rho = U[n];
+    double u = U[N + n] / rho, v = U[2 * N + n] / rho, w = U[3 * N + n] / rho;
+    double p = ph.gm1 * (U[4 * N + n] - 0.5 * rho * (u * u + v * v + w * w));
+    o[0] = rho; o[1] = u; o[2] = v; o[3] = w; o[4] = p;
+}
+
+__device__ __forceinline__ void put_prim(const Phys& ph, double* U, long long N, long long n, double rho, double u,
+                                         double v, double w, double p)
+{
+    U[n] = rho;
+    U[N + n] = rho * u;
+    U[2 * N + n] = rho * v;
+    U[3 * N + n] = rho * w;
+    U[4 * N + n] = p * ph.inv_gm1 + 0.5 * rho * (u * u + v * v + w * w);
+}
+
+__global__ void k_bc(Geo g, Phys ph, BCData bc, double* U, int d, const double* tptr, const double* dtptr,
+                     double tfrac)
+{
+    const long long N = g.N;
+    const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+    const long long s = d == 0 ? 1 : (d == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
+    const int a = (d + 1) % 3, b = (d + 2) % 3;
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    const int na = dims[a], nb = dims[b];
+    const long long nface = (long long)na * nb;
+    const double t = (tptr ? *tptr : 0.0) + (dtptr ? tfrac * *dtptr : 0.0);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * nface;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int side = (int)(e / nface);
+        const long long f = e % nface;
+        const int type = side ? g.bc_hi[d] : g.bc_lo[d];
+        if (type == 0) continue;
+        int pos[3];
+        pos[a] = (int)(f % na);
+        pos[b] = (int)(f / na);
+        const int mb = side ? nd - 1 : 0, m1 = side ? nd - 2 : 1, m2 = side ? nd - 3 : 2;
+        pos[d] = mb;
+        const long long n = pos[0] + (long long)g.nx * (pos[1] + (long long)g.ny * pos[2]);
+        const long long n1 = n + (long long)(m1 - mb) * s, n2 = n + (long long)(m2 - mb) * s;
+        if (type == 3) {
+            double o[5];
+            cons_prim(ph, U, N, n1, o);
+            put_prim(ph, U, N, n, o[0], o[1], o[2], o[3], o[4]);
+        } else if (type == 2) {
+            if (!bc.inflow) continue;
+            const int jj = pos[1];
+            const double* fl = bc.inflow;
+            put_prim(ph, U, N, n, fl[jj], fl[g.ny + jj], fl[2 * g.ny + jj], fl[3 * g.ny + jj], fl[4 * g.ny + jj]);
+        } else if (type == 1) {
+            double o1[5], o2[5];
+            cons_prim(ph, U, N, n1, o1);
+            cons_prim(ph, U, N, n2, o2);
+            const double pw = (4.0 * o1[4] - o2[4]) / 3.0;
+            const double rhow = ph.gMa2 * pw / ph.Tw;
+            double u = 0.0, v = 0.0, w = 0.0;
+            if (d == 1 && side == 0 && bc.amp != 0.0 && bc.wall_x && bc.wall_z) {
+                const double x = bc.wall_x[pos[0]], z = bc.wall_z[pos[2]];
+                if (x >= bc.x0 && x <= bc.x1) {
+                    const double pi = 3.14159265358979323846;
+                    const double vn = bc.amp * sin(2.0 * pi * (x - bc.x0) / (bc.x1 - bc.x0)) *
+                                      cos(2.0 * pi * bc.m * z / bc.Lz) * sin(bc.omega * t);
+                    const long long mi = midx(g, pos[0], pos[1], n);
+                    const double ex = metv(g, 3, mi), ey = metv(g, 4, mi), ez = metv(g, 5, mi);
+                    const double nr = sqrt(ex * ex + ey * ey + ez * ez);
+                    u = vn * ex / nr; v = vn * ey / nr; w = vn * ez / nr;
+                }
+            }
+            put_prim(ph, U, N, n, rhow, u, v, w, pw);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CFL time step (reading R16): max over nodes, as ordered bits of a non-
+// negative double
+// ---------------------------------------------------------------------------
+template <class RT>
+__global__ void k_cfl(Geo g, const RT* __restrict__ P, unsigned long long* out)
+{
+    const long long N = g.N;
+    double mx = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(n % g.nx);
+        int j = (int)((n / g.nx) % g.ny);
+        long long mi = midx(g, i, j, n);
+        double u = P[N + n], v = P[2 * N + n], w = P[3 * N + n], c = P[6 * N + n];
+        double s = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double dx = metv(g, 3 * d, mi), dy = metv(g, 3 * d + 1, mi), dz = metv(g, 3 * d + 2, mi);
+            s += fabs(dx * u + dy * v + dz * w) + c * sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        mx = fmax(mx, s);
+    }
+    for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// FMA-throughput probe: 8 independent dependency chains per thread
+template <class T>
+__global__ void k_fma_probe(T* out, int iters, T a, T b)
+{
+    T x[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) x[r] = (T)(threadIdx.x + r) * (T)1e-3;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) x[r] = x[r] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s += x[r];
+    if (s == (T)12345.678) out[0] = s;  // keeps the chains alive
+}
+
+__global__ void k_set_scalar(double* dst, double v)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+
+__global__ void k_advance_time(double* t, const double* dt)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *t += *dt;
+}
+
+}  // namespace cfdk

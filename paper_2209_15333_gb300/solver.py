@@ -1,0 +1,136 @@
+"""Python handle around one ``cfd_ctx`` (include/cfd.h).
+
+Host arrays are numpy float64; device arrays are torch CUDA tensors (used only
+for device memory and streams).  All arithmetic happens in the CUDA library.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or a torch tensor."""
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+class Solver:
+    def __init__(self, shape, metrics, *, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), stream=None, **params):
+        """shape = (nx, ny, nz); metrics: numpy/torch (10,), (10, ny, nx) or (10, nz, ny, nx)."""
+        nx, ny, nz = shape
+        self.shape = (nz, ny, nx)
+        m = metrics
+        ndim = m.dim() if _is_torch(m) else np.asarray(m).ndim
+        layout = {1: L.METRICS_UNIFORM, 3: L.METRICS_2D, 4: L.METRICS_3D}[ndim]
+        if not _is_torch(m):
+            m = np.ascontiguousarray(m, dtype=np.float64)
+        self._metrics = m
+        self.grid = L.make_grid(nx, ny, nz, bc_lo, bc_hi, layout)
+        self.params = L.default_params(**params)
+        self.ctx = C.c_void_p()
+        mp, mdev = _ptr(m)
+        if stream is None:
+            stream_ptr = None
+        else:
+            stream_ptr = C.c_void_p(getattr(stream, "cuda_stream", stream))
+        L.check(L.lib().cfd_create(C.byref(self.ctx), C.byref(self.grid), mp, mdev, C.byref(self.params),
+                                   stream_ptr))
+
+    # ---- state ----
+    def set_state(self, U, block=0):
+        p, dev = _ptr(U)
+        L.check(L.lib().cfd_set_state(self.ctx, block, p, dev), self.ctx)
+
+    def get_state(self, out=None, block=0):
+        if out is None:
+            out = np.empty((5,) + self.shape)
+        p, dev = _ptr(out)
+        L.check(L.lib().cfd_get_state(self.ctx, block, p, dev), self.ctx)
+        return out
+
+    def rhs(self, out=None, block=0):
+        if out is None:
+            out = np.empty((5,) + self.shape)
+        p, dev = _ptr(out)
+        L.check(L.lib().cfd_rhs(self.ctx, block, p, dev), self.ctx)
+        return out
+
+    def step(self, dt, nsteps=1):
+        L.check(L.lib().cfd_step(self.ctx, dt, nsteps), self.ctx)
+
+    def cfl_dt(self, cfl=0.5, block=0):
+        dt = C.c_double()
+        L.check(L.lib().cfd_cfl_dt(self.ctx, block, cfl, C.byref(dt)), self.ctx)
+        return dt.value
+
+    def flags(self, block=0):
+        out = np.empty(self.shape, dtype=np.uint8)
+        L.check(L.lib().cfd_get_flags(self.ctx, block, C.c_void_p(out.ctypes.data), 0), self.ctx)
+        return out
+
+    def force_flags(self, cls, block=0):
+        if cls is None:
+            L.check(L.lib().cfd_force_flags(self.ctx, block, None, 0), self.ctx)
+            return
+        c = np.ascontiguousarray(cls, dtype=np.uint8)
+        self._forced = c
+        L.check(L.lib().cfd_force_flags(self.ctx, block, C.c_void_p(c.ctypes.data), 0), self.ctx)
+
+    def set_inflow(self, prim):
+        p = np.ascontiguousarray(prim, dtype=np.float64)
+        L.check(L.lib().cfd_set_inflow(self.ctx, C.c_void_p(p.ctypes.data)), self.ctx)
+
+    def set_blowing(self, amp, x0, x1, omega, m, Lz, wall_x, wall_z):
+        wx = np.ascontiguousarray(wall_x, dtype=np.float64)
+        wz = np.ascontiguousarray(wall_z, dtype=np.float64)
+        L.check(L.lib().cfd_set_blowing(self.ctx, amp, x0, x1, omega, m, Lz, C.c_void_p(wx.ctypes.data),
+                                        C.c_void_p(wz.ctypes.data)), self.ctx)
+
+    def time(self):
+        t = C.c_double()
+        L.check(L.lib().cfd_get_time(self.ctx, C.byref(t)), self.ctx)
+        return t.value
+
+    def set_time(self, t):
+        L.check(L.lib().cfd_set_time(self.ctx, t), self.ctx)
+
+    def sync(self, timeout_s=60.0):
+        L.check(L.lib().cfd_sync(self.ctx, timeout_s), self.ctx)
+
+    def profile_stage(self, reps=3):
+        """Mean ms per right-hand-side evaluation of each kernel (events)."""
+        ms = (C.c_double * 6)()
+        L.check(L.lib().cfd_profile_stage(self.ctx, reps, ms), self.ctx)
+        names = ["prim", "sensor", "visc_flux", "sweep_xi", "sweep_eta", "sweep_zeta"]
+        return dict(zip(names, list(ms)))
+
+    def launches(self):
+        return L.lib().cfd_launch_count(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            L.lib().cfd_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
