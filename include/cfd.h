@@ -169,6 +169,38 @@ cfd_status cfd_fma_peak(int precision, double* tflops);
 #define CFD_PROFILE_KERNELS 6
 cfd_status cfd_profile_stage(cfd_ctx* ctx, int reps, double* ms);
 
+/*
+ * Allocation-free right-hand side.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code whose device
+ * memory is owned by someone else (a framework's pool allocator or a fixed
+ * memory budget, where an extra cudaMalloc fails or breaks the accounting)
+ * and code that must not stall the device (cudaFree synchronises it).
+ *
+ * Computes the same L(U) as cfd_rhs for one block of at most
+ * CFD_NOALLOC_MAX_NODES nodes, without a context: metrics (layout
+ * grid->metric_layout), U [5][nz][ny][nx] and dUdt are DEVICE pointers
+ * owned by the caller; the call is asynchronous on `stream` (a
+ * cudaStream_t; NULL is the legacy default stream).  U is used as given: no
+ * boundary conditions are applied to it.  All intermediate arrays live in
+ * one fixed device array inside the library (about 14.5 MB, held by every
+ * GPU that loads the library until the process exits); the call allocates
+ * no device or host memory on success.
+ *  - The first call on a device does a one-time set-up there (it looks up
+ *    the array's device address and sets kernel attributes); make that
+ *    first call before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind; calls
+ *    that overlap on the GPU (several streams, several host threads) race.
+ *    Order them on one stream.
+ *  - A non-physical state is not reported (no host synchronisation): check
+ *    with cfd_rhs when that matters.
+ * Errors: CFD_EINVAL (null pointer, bad grid or params), CFD_ENOMEM (the
+ * grid has more than CFD_NOALLOC_MAX_NODES nodes), CFD_EUNSUPPORTED (as for
+ * cfd_create), CFD_ECUDA.
+ */
+#define CFD_NOALLOC_MAX_NODES 32768
+cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const double* metrics,
+                           const double* U, double* dUdt, void* stream);
+
 /* Free every device buffer and the graph; NULL is allowed. */
 void cfd_destroy(cfd_ctx* ctx);
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -669,4 +670,176 @@ extern "C" cfd_status cfd_profile_stage(cfd_ctx* ctx, int reps, double* ms)
     for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
     if (st != CFD_OK) return st;
     return read_err(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free right-hand side (cfd_rhs_noalloc).  Every intermediate
+// array lives in one file-scope device array; host code must not use the
+// array's name as a device address (in host code it names a host-side
+// stand-in), so its device address is looked up once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+// ---------------------------------------------------------------------------
+namespace noalloc {
+
+constexpr long long kMaxNodes = CFD_NOALLOC_MAX_NODES;
+constexpr size_t kAlign = 256;
+constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kMetOff = 0;
+constexpr size_t kPOff = kMetOff + up((size_t)M_COUNT * kMaxNodes * sizeof(double));
+constexpr size_t kFvOff = kPOff + up((size_t)7 * kMaxNodes * sizeof(double));
+constexpr size_t kROff = kFvOff + up((size_t)12 * kMaxNodes * sizeof(double));
+constexpr size_t kClsOff = kROff + up((size_t)5 * kMaxNodes * sizeof(double));
+constexpr size_t kErrOff = kClsOff + up((size_t)kMaxNodes);
+constexpr size_t kBytes = kErrOff + kAlign;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_scratch[kBytes];
+
+static std::mutex g_mu;
+static unsigned char* g_dev_ptr[kMaxDevices];   // device address of g_scratch per device
+
+// once per device, with that device current
+static cudaError_t setup(int dev, unsigned char** out)
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_dev_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        const int smem = 4 * 80 * 32 * (int)sizeof(double);
+        e = cudaFuncSetAttribute(k_sweep_s<double, 1, EP_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_sweep_s<double, 2, EP_FINAL_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        g_dev_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_dev_ptr[dev];
+    return cudaSuccess;
+}
+
+static void fill_phys(Phys& ph, const cfd_params& p)
+{
+    ph = Phys{};
+    ph.gamma = p.gamma;
+    ph.gm1 = p.gamma - 1.0;
+    ph.inv_gm1 = 1.0 / (p.gamma - 1.0);
+    ph.Ma = p.Ma;
+    ph.gMa2 = p.gamma * p.Ma * p.Ma;
+    ph.inv2g = 1.0 / (2.0 * p.gamma);
+    ph.viscous = p.Re > 0.0;
+    ph.invRe = p.Re > 0.0 ? 1.0 / p.Re : 0.0;
+    ph.kcoef = p.Re > 0.0 ? 1.0 / ((p.gamma - 1.0) * p.Ma * p.Ma * p.Pr * p.Re) : 0.0;
+    ph.Tw = p.T_wall;
+    ph.visc_law = p.visc_law;
+    ph.omega = p.visc_omega;
+    ph.suth_s = p.visc_law == CFD_SUTHERLAND ? 110.4 / p.T_ref : 0.0;
+    ph.scheme = p.scheme;
+    ph.th1 = p.theta1;
+    ph.th2 = p.theta2;
+    ph.eps = p.weno_eps;
+    ph.vorder = p.visc_order;
+}
+
+}  // namespace noalloc
+
+extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const double* metrics,
+                                      const double* U, double* dUdt, void* stream)
+{
+    using namespace noalloc;
+    if (!grid || !params || !metrics || !U || !dUdt)
+        return fail(nullptr, CFD_EINVAL, "null argument to cfd_rhs_noalloc");
+    cfd_status st = validate(nullptr, grid, params);
+    if (st != CFD_OK) return st;
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    if (N > kMaxNodes)
+        return fail(nullptr, CFD_ENOMEM, "cfd_rhs_noalloc: grid has more than CFD_NOALLOC_MAX_NODES nodes");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(nullptr, CFD_ECUDA, "cfd_rhs_noalloc: no usable CUDA device");
+    unsigned char* base = nullptr;
+    e = setup(dev, &base);
+    if (e != cudaSuccess) return fail(nullptr, CFD_ECUDA, std::string("cfd_rhs_noalloc set-up: ") + cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+
+    Geo g{};
+    g.nx = grid->nx;
+    g.ny = grid->ny;
+    g.nz = grid->nz;
+    g.N = N;
+    for (int d = 0; d < 3; ++d) {
+        g.per[d] = grid->bc_lo[d] == CFD_BC_PERIODIC;
+        g.bc_lo[d] = grid->bc_lo[d];
+        g.bc_hi[d] = grid->bc_hi[d];
+    }
+    g.mlayout = grid->metric_layout;
+    g.M = g.mlayout == CFD_METRICS_3D ? N : (g.mlayout == CFD_METRICS_2D ? (long long)g.nx * g.ny : 1);
+    double* met = (double*)(base + kMetOff);
+    g.met = met;
+    Phys ph;
+    fill_phys(ph, *params);
+    void* P = base + kPOff;
+    void* Fv = base + kFvOff;
+    void* R = base + kROff;
+    uint8_t* cls = base + kClsOff;
+    int* err = (int*)(base + kErrOff);
+
+#define NA_CHECK(x)                                                                                       \
+    do {                                                                                                  \
+        cudaError_t e_ = (x);                                                                             \
+        if (e_ != cudaSuccess) return fail(nullptr, CFD_ECUDA, std::string("cfd_rhs_noalloc: ") + cudaGetErrorString(e_)); \
+    } while (0)
+    // the caller's metrics into the array, then the derived quantities
+    NA_CHECK(cudaMemcpyAsync(met, metrics, 10 * g.M * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k_metric_derive<<<grid_for(g.M, 256), 256, 0, s>>>(met, g.M);
+    NA_CHECK(cudaGetLastError());
+    // the only value that must start at zero; every other array is fully
+    // written before it is read
+    NA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    k_prim<double><<<grid_for(N, 256), 256, 0, s>>>(g, ph, U, (double*)P, err);
+    NA_CHECK(cudaGetLastError());
+    if (params->scheme == CFD_HYBRID) {
+        k_sensor<<<grid_for(N, 256), 256, 0, s>>>(g, ph, (const double*)P + 4 * N, cls);
+        NA_CHECK(cudaGetLastError());
+    }
+    if (ph.viscous) {
+        k_visc_flux<double><<<grid_for(N, 256), 256, 0, s>>>(g, ph, (const double*)P, (double*)Fv);
+        NA_CHECK(cudaGetLastError());
+    }
+    SweepArgs A{};
+    A.g = g;
+    A.ph = ph;
+    A.P = P;
+    A.cls = params->scheme == CFD_HYBRID ? cls : nullptr;
+    A.Fv = ph.viscous ? Fv : nullptr;
+    A.R = R;
+    A.Lout = dUdt;
+    A.rk_b = 1.0;
+    A.seg_len = 128;
+    {
+        const int lo = g.per[0] ? 0 : 1, hi = g.per[0] ? g.nx : g.nx - 1;
+        const int nb = g.nx <= 32 ? 32 : (g.nx <= 64 ? 64 : 128);
+        dim3 gr((hi - lo + nb - 1) / nb, g.ny, g.nz);
+        if (nb == 32) k_sweep_x<double, 32, EP_STORE><<<gr, 32, 0, s>>>(A);
+        else if (nb == 64) k_sweep_x<double, 64, EP_STORE><<<gr, 64, 0, s>>>(A);
+        else k_sweep_x<double, 128, EP_STORE><<<gr, 128, 0, s>>>(A);
+        NA_CHECK(cudaGetLastError());
+    }
+    const size_t smem = 4 * 80 * 32 * sizeof(double);
+    {
+        const int lo = g.per[1] ? 0 : 1, hi = g.per[1] ? g.ny : g.ny - 1;
+        const long long nseg = (hi - lo + A.seg_len - 1) / A.seg_len;
+        const long long warps = (long long)((g.nx + 31) / 32) * g.nz * nseg;
+        k_sweep_s<double, 1, EP_ACCUM><<<(unsigned)((warps + 3) / 4), 128, smem, s>>>(A);
+        NA_CHECK(cudaGetLastError());
+    }
+    {
+        const int lo = g.per[2] ? 0 : 1, hi = g.per[2] ? g.nz : g.nz - 1;
+        const long long nseg = (hi - lo + A.seg_len - 1) / A.seg_len;
+        const long long warps = (long long)((g.nx + 31) / 32) * g.ny * nseg;
+        k_sweep_s<double, 2, EP_FINAL_RHS><<<(unsigned)((warps + 3) / 4), 128, smem, s>>>(A);
+        NA_CHECK(cudaGetLastError());
+    }
+#undef NA_CHECK
+    return CFD_OK;
 }

@@ -1,0 +1,93 @@
+"""cfd_rhs_noalloc: the allocation-free right-hand side, for callers that
+cannot call cudaMalloc (their device memory belongs to another allocator or
+budget, or they must not stall the device the way cudaFree does).
+
+Called through the C ABI with caller-owned device buffers and compared with
+the context-based cfd_rhs on consecutive calls, so that contents the shared
+scratch array keeps from one call cannot leak into the next.  This file is
+collected last; it passes alone in a fresh process and after the other tests.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2209_15333_gb300 import cases
+
+from gpu_helpers import field_rel_err, turbulence_field
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_15333_gb300 import build
+    build.build()
+    return torch
+
+
+def _case(name):
+    """(shape, metrics, params, U) of a periodic case whose U needs no BCs."""
+    if name == "tgv32_hybrid":
+        n = 32
+        return (n, n, n), cases.uniform_metrics(n, n, n), dict(scheme=3, Re=400.0, theta1=0.004,
+                                                               theta2=0.012), cases.taylor_green(n)
+    if name == "wavy_weno7":
+        n = 20
+        met, _ = cases.wavy_grid(n, amp=0.05)
+        return (n, n, n), met, dict(scheme=2, Re=150.0, visc_law=0, T_ref=108.1), turbulence_field((n, n, n), 41)
+    if name == "ragged_ud7_inviscid":
+        sh = (29, 13, 17)
+        return sh, cases.uniform_metrics(*sh), dict(scheme=0, Re=0.0), turbulence_field(sh, 42)
+    raise KeyError(name)
+
+
+def _noalloc(torch, shape, met, params, U):
+    from paper_2209_15333_gb300 import _lib as L
+    nx, ny, nz = shape
+    m = np.asarray(met)
+    layout = {1: L.METRICS_UNIFORM, 3: L.METRICS_2D, 4: L.METRICS_3D}[m.ndim]
+    grid = L.make_grid(nx, ny, nz, metric_layout=layout)
+    prm = L.default_params(**params)
+    dm = torch.tensor(m, device="cuda", dtype=torch.float64).contiguous()
+    dU = torch.tensor(U, device="cuda", dtype=torch.float64).contiguous()
+    dL = torch.full_like(dU, float("nan"))
+    stream = torch.cuda.current_stream()
+    st = L.lib().cfd_rhs_noalloc(C.byref(grid), C.byref(prm), C.c_void_p(dm.data_ptr()), C.c_void_p(dU.data_ptr()),
+                                 C.c_void_p(dL.data_ptr()), C.c_void_p(stream.cuda_stream))
+    L.check(st)
+    stream.synchronize()
+    return dL.cpu().numpy()
+
+
+def _with_context(shape, met, params, U):
+    from paper_2209_15333_gb300.solver import Solver
+    with Solver(shape, met, **params) as s:
+        s.set_state(U)
+        return s.rhs()
+
+
+def test_noalloc_matches_context_rhs_on_consecutive_calls(torch_cuda):
+    for name in ("tgv32_hybrid", "wavy_weno7", "ragged_ud7_inviscid", "tgv32_hybrid"):
+        shape, met, params, U = _case(name)
+        got = _noalloc(torch_cuda, shape, met, params, U)
+        ref = _with_context(shape, met, params, U)
+        assert np.isfinite(got).all()
+        assert field_rel_err(got, ref) <= TOL, name
+
+
+def test_noalloc_rejects_grids_beyond_the_limit(torch_cuda):
+    from paper_2209_15333_gb300 import _lib as L
+    n = 33  # 33^3 > CFD_NOALLOC_MAX_NODES = 32^3
+    grid = L.make_grid(n, n, n, metric_layout=L.METRICS_UNIFORM)
+    prm = L.default_params()
+    dummy = torch_cuda.zeros(8, device="cuda", dtype=torch_cuda.float64)
+    p = C.c_void_p(dummy.data_ptr())
+    st = L.lib().cfd_rhs_noalloc(C.byref(grid), C.byref(prm), p, p, p, None)
+    assert st == L.CFD_ENOMEM
+    assert b"CFD_NOALLOC_MAX_NODES" in L.lib().cfd_last_error(None)
