@@ -1,17 +1,19 @@
 """Benchmark: grid-point stage updates per second of the TVD-RK3 step on the
 256^3 decaying isotropic-turbulence workload (hybrid UD7/WENO7/WENO5 scheme,
-viscous, periodic box), through the C ABI of the CUDA library.
+8th-order viscous terms, periodic box), through the C ABI of the CUDA library.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--precision fp64] [--n 256]
+                    [--precision both|mixed|fp64] [--n 256]
 
-Prints one JSON line on rank 0.  The path does not exchange data between
-ranks (each rank advances its own independent box), so N > 1 runs replicas
-(weak scaling) with a barrier and max-over-ranks timing.
+Rank 0 prints one JSON line.  The headline `value` is the FP32-bulk/FP64-state
+form; the plain FP64 form is reported beside it under "fp64", each with its
+error against the FP64 oracle after one RK3 step of the full field.  The path
+exchanges no data between ranks (independent boxes), so N > 1 runs replicas
+with a barrier and max-over-ranks timing (weak scaling).
 """
 import argparse
+import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -26,6 +28,21 @@ sys.path.insert(0, ROOT)
 SEED = 20220930
 MT = 0.5
 GAMMA = 1.4
+KERNEL_NAMES = ["prim", "sensor", "visc_flux", "sweep_xi", "sweep_eta", "sweep_zeta"]
+
+# Algorithmic work per node of each kernel (stated in the design doc, section 5):
+# FP64 form: counted flops (FMA = 2; division, sqrt, pow = 1);
+# mixed form: compulsory bytes (inputs read once, outputs written once).
+FP64_FLOPS = {"prim": 25, "sensor": 20, "visc_flux": 305, "sweep_xi": 247, "sweep_eta": 252, "sweep_zeta": 277}
+MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_eta": 77, "sweep_zeta": 164}
+# DRAM bytes per node measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a
+# 160^3 stage, valid for the kernel source with this hash prefix; scaled to the full
+# launch by the node count (traffic grows with it: the arrays exceed L2).
+NCU_TRAFFIC = {
+    "fp64": {"src": "", "per_node": {"visc_flux": 185.4, "sweep_xi": 106.4, "sweep_eta": 153.5,
+                                      "sweep_zeta": 155.5}},
+    "mixed": {"src": "", "per_node": {}},
+}
 
 
 def parse():
@@ -34,18 +51,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-only", action="store_true", help="one stage profile, for ncu runs")
+    ap.add_argument("--profile-only", action="store_true", help="one profiled stage per precision (ncu runs)")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 def workload(n):
@@ -55,6 +69,23 @@ def workload(n):
     params = dict(gamma=GAMMA, Re=Re, Ma=MT, Pr=0.72, visc_law=1, visc_omega=0.76, scheme=3, theta1=0.02,
                   theta2=0.1, visc_order=8)
     return U, met, params, Re
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in ("cfd_kernels.cuh", "weno_coeffs.cuh"):
+        with open(os.path.join(ROOT, "paper_2209_15333_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def field_rel_err(a, b):
+    e = 0.0
+    for q in range(a.shape[0]):
+        den = float(np.abs(b[q]).max())
+        num = float(np.abs(a[q] - b[q]).max())
+        e = max(e, num / den if den > 0 else num)
+    return e
 
 
 class ClockSampler:
@@ -74,8 +105,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except OSError:
             self.proc = None
 
@@ -120,101 +150,92 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# algorithmic FP64 flops per node of each kernel of the UD7 path, counted from
-# the kernel source (FMA = 2 flops; division and square root = 1 flop each)
-ALGO_FLOPS = {
-    "sweep": None,  # filled from flop_counts()
-}
+def fma_peaks():
+    import ctypes as C
+    from paper_2209_15333_gb300 import _lib
+    out = {}
+    for name, prec in (("fp64", 0), ("fp32", 1)):
+        v = C.c_double()
+        _lib.check(_lib.lib().cfd_fma_peak(prec, C.byref(v)))
+        out[name] = v.value
+    return out
 
 
-def flop_counts():
-    """Per-node flop counts of the UD7 / viscous path."""
-    sw = 53               # split fluxes of one node, one direction (both signs)
-    recon = 5 * 2 * 13 + 5  # UD7 +/- for 5 components (7 coefficients: 6 FMA + 1 MUL) and the sum
-    diff = 5
-    visc_div = 4 * (2 * 4 + 1 + 3)  # 8th-order central of 4 rows
-    per_sweep = sw + recon + diff + visc_div
-    visc_flux = 12 * 12 + 9 * 3 * 2 + 60 + 40
-    return {"sweep": per_sweep, "visc_flux": visc_flux}
-
-
-def time_oracle(n, steps_of_three=1, threads=None):
-    """The oracle, as it stands, on host cores: one RK3 step of an n^3 box of
-    the same workload recipe.  Returns (point-stage/s, seconds, threads)."""
+def oracle_step(n, U, dt, threads=None):
+    """The oracle, as it stands: one RK3 step of the n^3 field on host cores."""
     import oracle
     from paper_2209_15333_gb300 import cases
-    U, met, params, Re = workload(n)
+    _, met, params, Re = workload_params(n)
     M = cases.expand_metrics(met, (n, n, n))
     th = threads or (os.cpu_count() or 1)
     c = oracle.Case(n, n, n, gamma=GAMMA, Re=Re, Ma=MT, Pr=0.72, visc_law=1, visc_omega=0.76, scheme=3,
                     theta1=0.02, theta2=0.1, visc_order=8, nthreads=th)
-    dt = oracle.cfl_dt(c, M, U, 0.5)
     t0 = time.perf_counter()
-    oracle.step(c, M, U, dt, steps_of_three)
-    el = time.perf_counter() - t0
-    return n ** 3 * 3 * steps_of_three / el, el, th
+    U1 = oracle.step(c, M, U, dt, 1)
+    return U1, time.perf_counter() - t0, th
 
 
-def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle on the machine's host cores (rank 0 only)."""
+_WL = {}
+
+
+def workload_params(n):
+    if n not in _WL:
+        _WL[n] = workload(n)
+    return _WL[n]
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return
     n = min(args.n, 128)
+    U, met, params, Re = workload_params(n)
+    import oracle
+    from paper_2209_15333_gb300 import cases
+    M = cases.expand_metrics(met, (n, n, n))
+    dt = oracle.cfl_dt(oracle.Case(n, n, n, Ma=MT), M, U, 0.5)
     for _ in range(args.warmup):
-        time_oracle(n)
-    tot, pts = 0.0, 0
-    th = os.cpu_count() or 1
+        oracle_step(n, U, dt)
+    tot, th = 0.0, 1
     for _ in range(args.steps):
-        v, el, th = time_oracle(n)
+        _, el, th = oracle_step(n, U, dt)
         tot += el
-        pts += n ** 3 * 3
-    value = pts / tot
+    value = n ** 3 * 3 * args.steps / tot
     line = {
-        "impl": "reference", "metric": "grid-point stage updates/s", "value": value,
-        "unit": "point-stage/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "isotropic turbulence %d^3 sample of the %d^3 case, hybrid, FP64" % (n, args.n)},
+        "impl": "reference", "metric": "grid-point stage updates/s", "value": value, "unit": "point-stage/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "decaying isotropic turbulence, hybrid, viscous; oracle sample %d^3 of the %d^3 case"
+                   % (n, args.n)},
         "cpu_baseline": {"value": value, "unit": "point-stage/s", "cores": th, "kind": "oracle",
-                         "sample": "one RK3 step per timed step of a %d^3 box of the same recipe" % n},
+                         "sample": "one RK3 step of a %d^3 box of the same recipe per timed step" % n},
         "e2e": {"value": value, "unit": "point-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse()
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
+def run_precision(args, prec, U, met, params, world, local, dt):
+    """Time K graph-replayed steps of one precision; returns a result dict."""
     import torch
-    torch.cuda.set_device(local)
-    from paper_2209_15333_gb300 import build
-    build.build()
     from paper_2209_15333_gb300.solver import Solver
-
     n = args.n
-    U, met, params, Re = workload(n)
     N = n ** 3
     stream = torch.cuda.Stream()
-    s = Solver((n, n, n), met, stream=stream, **params)
+    s = Solver((n, n, n), met, stream=stream, precision=1 if prec == "mixed" else 0, **params)
     Ud = torch.tensor(U, device="cuda")
     s.set_state(Ud)
-    dt = s.cfl_dt(0.5)
     if args.profile_only:
         s.profile_stage(1)
-        torch.cuda.synchronize()
-        return
-
+        s.close()
+        return None
+    # accuracy: one RK3 step from the initial field
+    s.step(dt, 1)
+    U1 = s.get_state()
+    s.set_state(Ud)
+    s.set_time(0.0)
     for _ in range(args.warmup):
         s.step(dt, 1)
     s.sync(600.0)
-
     clocks = ClockSampler(local)
     clocks.start()
     l0 = s.launches()
@@ -236,77 +257,126 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     cls = s.flags()
-    frac = np.bincount(cls.ravel(), minlength=3) / cls.size
+    frac = np.bincount(cls.ravel(), minlength=3)[:3] / cls.size
     value = world * N * 3 * args.steps / (ms * 1e-3)
-
-    # end to end through the public API with host buffers: H2D of the state,
-    # one step, D2H of the result, every step
+    # end to end through the public API with pinned host buffers
     host_in = torch.from_numpy(s.get_state()).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         s.set_state(host_in)
         s.step(dt, 1)
         s.get_state(out=host_out)
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * N * 3 * args.steps / e2e_s
-
-    # per-kernel times (CUDA events on the context stream, no graph)
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
     prof = s.profile_stage(3)
-    dom = max(prof, key=prof.get)
-    fc = flop_counts()
-    fp64_peak = None
-    try:
-        import ctypes as C
-        from paper_2209_15333_gb300 import _lib
-        v = C.c_double()
-        _lib.check(_lib.lib().cfd_fma_peak(0, C.byref(v)))
-        fp64_peak = v.value
-        v32 = C.c_double()
-        _lib.check(_lib.lib().cfd_fma_peak(1, C.byref(v32)))
-        fp32_peak = v32.value
-    except Exception:
-        fp32_peak = None
-    peaks, peak_kind = measured_peaks()
-    kind = "sweep" if dom.startswith("sweep") else dom
-    flops = fc.get(kind, fc["sweep"]) * N
-    achieved = flops / (prof[dom] * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": (achieved / fp64_peak) if fp64_peak else None, "traffic": None,
-            "peak_source": "cfd_fma_peak FP64 FMA probe (measured in this run)",
-            "kernel_ms": prof}
-    alg_bytes = (40 + 26.7 + 40) * N * 3 * args.steps
-    hbm_frac = alg_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        v, el, th = time_oracle(n)
-        cpu = {"value": v, "unit": "point-stage/s", "cores": th, "kind": "oracle",
-               "sample": "one RK3 step (3 stages) of the full %d^3 field, %.1f s" % (n, el)}
-
-    if rank == 0:
-        line = {
-            "metric": "grid-point stage updates/s", "value": value, "unit": "point-stage/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "decaying isotropic turbulence %d^3 periodic, hybrid UD7/WENO7/WENO5, "
-                                   "8th-order viscous, FP64" % n, "grid": [n, n, n], "Re": Re, "Mt": MT,
-                       "seed": SEED, "l2": "inputs larger than L2 (state %d MB)" % (40 * N // 2 ** 20),
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "class_fraction": [float(x) for x in frac]},
-            "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": "point-stage/s", "h2d_bytes_per_step": 40 * N,
-                    "d2h_bytes_per_step": 40 * N},
-            "gpu_launches": launches,
-            "roofline": roof,
-            "hbm_algorithmic": {"bytes_per_point_stage": 106.7, "frac": hbm_frac, "peak_gbs": peaks["hbm_gbs"],
-                                "peak_source": peak_kind},
-            "fp32_fma_peak_tflops": fp32_peak,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
     s.close()
+    return dict(value=value, ms=ms, launches=launches, clocks=clk, class_fraction=[float(x) for x in frac],
+                e2e=world * N * 3 * args.steps / e2e_s, prof=prof, U1=U1)
+
+
+def roofline(prec, r, N, peaks, fma, src_hash):
+    prof = r["prof"]
+    dom = max(prof, key=prof.get)
+    tr = NCU_TRAFFIC[prec]
+    traffic = None
+    if tr["src"] and tr["src"] == src_hash and dom in tr["per_node"]:
+        traffic = tr["per_node"][dom] * N
+    if prec == "fp64":
+        achieved = FP64_FLOPS[dom] * N / (prof[dom] * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fma["fp64"], "unit": "TFLOP/s",
+                "frac": achieved / fma["fp64"], "traffic": traffic,
+                "peak_source": "FP64 FMA throughput measured in this run (cfd_fma_peak)", "kernel_ms": prof}
+    achieved = MIXED_BYTES[dom] * N / (prof[dom] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "kernel_ms": prof}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2209_15333_gb300 import build
+    build.build()
+    from paper_2209_15333_gb300.solver import Solver
+
+    n = args.n
+    N = n ** 3
+    U, met, params, Re = workload_params(n)
+    with Solver((n, n, n), met, **params) as s0:
+        s0.set_state(U)
+        dt = s0.cfl_dt(0.5)
+    precs = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
+    res = {p: run_precision(args, p, U, met, params, world, local, dt) for p in precs}
+    if args.profile_only:
+        return
+    fma = fma_peaks()
+    peaks, peak_kind = measured_peaks()
+    src_hash = kernel_src_hash()
+    cpu, U1o = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        U1o, el, th = oracle_step(n, U, dt)
+        cpu = {"value": N * 3 / el, "unit": "point-stage/s", "cores": th, "kind": "oracle",
+               "sample": "one RK3 step (3 stages) of the full %d^3 field, %.1f s" % (n, el)}
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    alg_b = (40 + 26.7 + 40)
+
+    def summary(p):
+        r = res[p]
+        d = {"value": r["value"], "unit": "point-stage/s", "ms_per_step": r["ms"] / args.steps,
+             "dtype": "f32+f64" if p == "mixed" else "f64",
+             "roofline": roofline(p, r, N, peaks, fma, src_hash),
+             "hbm_algorithmic": {"bytes_per_point_stage": alg_b,
+                                 "frac": alg_b * r["value"] / world / 1e9 / peaks["hbm_gbs"]},
+             "err_vs_oracle_1step": field_rel_err(r["U1"], U1o) if U1o is not None else None,
+             "class_fraction": r["class_fraction"], "gpu_launches": r["launches"], "clocks": r["clocks"],
+             "e2e": r["e2e"]}
+        if p == "fp64":
+            d["fp64_alu_frac_whole_step"] = sum(FP64_FLOPS.values()) * r["value"] / world / 1e12 / fma["fp64"]
+        return d
+
+    head = "mixed" if "mixed" in res else precs[0]
+    h = summary(head)
+    line = {
+        "metric": "grid-point stage updates/s", "value": h["value"], "unit": "point-stage/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
+        "config": {"workload": "decaying isotropic turbulence %d^3 periodic, hybrid UD7/WENO7/WENO5, 8th-order "
+                               "viscous, %s" % (n, "FP32 bulk / FP64 state" if head == "mixed" else "FP64"),
+                   "grid": [n, n, n], "Re": Re, "Mt": MT, "seed": SEED,
+                   "l2": "inputs larger than L2 (state %d MB)" % (40 * N // 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU", "precision": head},
+        "clocks": h["clocks"],
+        "e2e": {"value": h["e2e"], "unit": "point-stage/s", "h2d_bytes_per_step": 40 * N, "d2h_bytes_per_step": 40 * N},
+        "gpu_launches": h["gpu_launches"],
+        "roofline": h["roofline"],
+        "hbm_algorithmic": dict(h["hbm_algorithmic"], peak_gbs=peaks["hbm_gbs"], peak_source=peak_kind),
+        "err_vs_oracle_1step": h["err_vs_oracle_1step"],
+        "class_fraction": h["class_fraction"],
+        "fma_peak_tflops": fma,
+        "kernel_src": src_hash,
+        "cpu_baseline": cpu,
+    }
+    if head == "mixed" and "fp64" in res:
+        line["fp64"] = summary("fp64")
+    print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -201,6 +201,18 @@ cfd_status cfd_profile_stage(cfd_ctx* ctx, int reps, double* ms);
 cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const double* metrics,
                            const double* U, double* dUdt, void* stream);
 
+/* Tuning control, not a step of the method.  The eta (dir 1) and zeta
+   (dir 2) sweeps have two implementations with bit-identical results:
+   kind 0 streams each x-row of 32 lanes along the line in segments of
+   `param` nodes (no recomputation; best when FP64 arithmetic binds), kind 1
+   works on tiles of 32 x `param` (16 or 32) nodes with a 4-node halo (more
+   parallelism; best when latency binds).  By default the context times all
+   four on its first cfd_rhs / cfd_step and keeps the fastest (cached per
+   process by precision, grid and scheme); cfd_set_sweep_variant fixes one
+   and turns the tuning off. */
+cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param);
+cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param);
+
 /* Free every device buffer and the graph; NULL is allowed. */
 void cfd_destroy(cfd_ctx* ctx);
 

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "CFD_OK", -1: "CFD_EINVAL", -2: "CFD_ENOMEM", -3: "CFD_ECUDA"
 EXPORTS = ["cfd_default_params", "cfd_create", "cfd_set_inflow", "cfd_set_blowing", "cfd_set_state",
            "cfd_get_state", "cfd_rhs", "cfd_step", "cfd_cfl_dt", "cfd_get_flags", "cfd_force_flags",
            "cfd_get_time", "cfd_set_time", "cfd_sync", "cfd_last_error", "cfd_launch_count", "cfd_fma_peak",
-           "cfd_profile_stage", "cfd_rhs_noalloc",
+           "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
            "cfd_destroy"]
 
 
@@ -82,6 +82,8 @@ def lib():
         L.cfd_launch_count.restype = C.c_longlong
         L.cfd_fma_peak.argtypes = [C.c_int, dp]
         L.cfd_profile_stage.argtypes = [vp, C.c_int, dp]
+        L.cfd_set_sweep_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int]
+        L.cfd_get_sweep_variant.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cfd_rhs_noalloc.argtypes = [C.POINTER(CfdGrid), C.POINTER(CfdParams), vp, vp, vp, vp]
         L.cfd_destroy.argtypes = [vp]
         L.cfd_destroy.restype = None

@@ -4,6 +4,7 @@
 
 #include <chrono>
 #include <mutex>
+#include <vector>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -42,6 +43,10 @@ struct cfd_ctx {
     BCData bc{};
     Bufs b;
     double* met = nullptr;          // [31][M]
+    float* metf = nullptr;          // [31][M] float mirror
+    int sweep_kind[3] = {0, 0, 0};  // eta/zeta: 0 streaming, 1 tile (chosen by the autotuner)
+    int sweep_param[3] = {0, 128, 128};
+    bool tuned = false;
     int* err = nullptr;             // device non-physical flag
     double* dt = nullptr;           // device scalars
     double* t = nullptr;
@@ -61,6 +66,9 @@ struct cfd_ctx {
 };
 
 static std::string g_static_msg = "no error";
+
+template <class R, int DIR, int EP>
+static cudaError_t set_sweep_attrs();
 
 static cfd_status fail(cfd_ctx* c, cfd_status s, const std::string& m)
 {
@@ -88,6 +96,32 @@ static int grid_for(long long n, int block)
     long long b = (n + block - 1) / block;
     long long cap = (long long)kSMs * 16;
     return (int)std::max(1LL, std::min(b, cap));
+}
+
+// launch shape of the node-parallel kernels: x-chunks by ny by nz
+struct NodeLaunch {
+    dim3 grid, block;
+};
+static NodeLaunch node_launch(const Geo& g)
+{
+    const int bx = g.nx >= 128 ? 128 : (g.nx >= 64 ? 64 : 32);
+    return {dim3((g.nx + bx - 1) / bx, g.ny, g.nz), dim3(bx)};
+}
+
+static void fill_float_consts(Phys& ph)
+{
+    ph.gm1f = (float)ph.gm1;
+    ph.inv_gm1f = (float)ph.inv_gm1;
+    ph.inv2gf = (float)ph.inv2g;
+    ph.invRef = (float)ph.invRe;
+    ph.kcoeff = (float)ph.kcoef;
+    ph.omegaf = (float)ph.omega;
+    ph.suth_sf = (float)ph.suth_s;
+    ph.th1f = (float)ph.th1;
+    ph.th2f = (float)ph.th2;
+    ph.epsf = (float)ph.eps;
+    ph.gMa2f = (float)ph.gMa2;
+    ph.invMaf = (float)(1.0 / ph.Ma);
 }
 
 extern "C" void cfd_default_params(cfd_params* p)
@@ -137,7 +171,7 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
     if (p->visc_law == CFD_SUTHERLAND && !(p->T_ref > 0.0)) return fail(ctx, CFD_EINVAL, "T_ref must be > 0");
     if (!(p->weno_eps > 0.0)) return fail(ctx, CFD_EINVAL, "weno_eps must be > 0");
     if (p->metric_mode != CFD_METRIC_NODAL) return fail(ctx, CFD_EUNSUPPORTED, "only the nodal metric mode");
-    if (p->precision != CFD_FP64) return fail(ctx, CFD_EUNSUPPORTED, "only FP64 in this build");
+    if (p->precision != CFD_FP64 && p->precision != CFD_FP32_BULK) return fail(ctx, CFD_EINVAL, "unknown precision");
     if (p->sensor != CFD_SENSOR_PLAIN) return fail(ctx, CFD_EUNSUPPORTED, "only the plain sensor");
     if (p->scheme == CFD_HYBRID && !(p->theta1 <= p->theta2)) return fail(ctx, CFD_EINVAL, "theta1 > theta2");
     bool wall = false;
@@ -149,7 +183,7 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
 static void free_all(cfd_ctx* c)
 {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void* ptrs[] = {c->b.U, c->b.Uk, c->b.P, c->b.Fv, c->b.R, c->b.cls, c->met, c->err, c->dt, c->t,
+    void* ptrs[] = {c->b.U, c->b.Uk, c->b.P, c->b.Fv, c->b.R, c->b.cls, c->met, c->metf, c->err, c->dt, c->t,
                     c->cflmax, c->inflow, c->wall_x, c->wall_z};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -201,7 +235,8 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     ph.th2 = p.theta2;
     ph.eps = p.weno_eps;
     ph.vorder = p.visc_order;
-    ctx->real_size = sizeof(double);
+    fill_float_consts(ph);
+    ctx->real_size = p.precision == CFD_FP32_BULK ? sizeof(float) : sizeof(double);
 
     const long long N = g.N;
     size_t rs = ctx->real_size;
@@ -225,9 +260,18 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     g.met = ctx->met;
     k_metric_derive<<<grid_for(g.M, 256), 256, 0, ctx->stream>>>(ctx->met, g.M);
     LAUNCH_CHECK();
-    CU(cudaFuncSetAttribute(k_sweep_s<double, 1, EP_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 80 * 32 * 8));
-    CU(cudaFuncSetAttribute(k_sweep_s<double, 2, EP_FINAL_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 80 * 32 * 8));
-    CU(cudaFuncSetAttribute(k_sweep_s<double, 2, EP_FINAL_RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 80 * 32 * 8));
+    CU(cudaMalloc(&ctx->metf, (size_t)M_COUNT * g.M * sizeof(float)));
+    k_metric_float<<<grid_for((long long)M_COUNT * g.M, 256), 256, 0, ctx->stream>>>(ctx->met, ctx->metf,
+                                                                                     (long long)M_COUNT * g.M);
+    LAUNCH_CHECK();
+    g.metf = ctx->metf;
+    CU((set_sweep_attrs<double, 1, EP_ACCUM>()));
+    CU((set_sweep_attrs<double, 2, EP_FINAL_RHS>()));
+    CU((set_sweep_attrs<double, 2, EP_FINAL_RK>()));
+    CU((set_sweep_attrs<float, 1, EP_ACCUM>()));
+    CU((set_sweep_attrs<float, 2, EP_FINAL_RHS>()));
+    CU((set_sweep_attrs<float, 2, EP_FINAL_RK>()));
+    if (p.precision == CFD_FP32_BULK) CU(cudaMemsetAsync(ctx->b.cls, 2, N, ctx->stream));
     ctx->bx = g.nx <= 32 ? 32 : (g.nx <= 64 ? 64 : 128);
     CU(cudaStreamSynchronize(ctx->stream));
     return CFD_OK;
@@ -289,6 +333,28 @@ static cfd_status launch_bc(cfd_ctx* ctx, double* U, double tfrac, bool use_dt)
     return CFD_OK;
 }
 
+template <class R, int DIR, int EP>
+static cfd_status launch_sweep_dir(cfd_ctx* ctx, SweepArgs& A, int kind, int param)
+{
+    const Geo& g = ctx->g;
+    const int n = DIR == 1 ? g.ny : g.nz, nother = DIR == 1 ? g.nz : g.ny;
+    const int lo = g.per[DIR] ? 0 : 1, hi = g.per[DIR] ? n : n - 1;
+    if (kind == 0) {
+        A.seg_len = param;
+        const long long nseg = (hi - lo + param - 1) / param;
+        const long long warps = (long long)((g.nx + 31) / 32) * nother * nseg;
+        k_sweep_s<R, DIR, EP><<<(unsigned)((warps + 3) / 4), 128, 4 * 80 * 32 * sizeof(R), ctx->stream>>>(A);
+    } else {
+        dim3 grid((g.nx + 31) / 32, nother, (hi - lo + param - 1) / param);
+        if (param == 16)
+            k_sweep_t<R, DIR, EP, 16><<<grid, 256, tile_smem_bytes<R, 16>(), ctx->stream>>>(A);
+        else
+            k_sweep_t<R, DIR, EP, 32><<<grid, 256, tile_smem_bytes<R, 32>(), ctx->stream>>>(A);
+    }
+    LAUNCH_CHECK();
+    return CFD_OK;
+}
+
 template <class R, int EPF>
 static cfd_status launch_sweeps(cfd_ctx* ctx, SweepArgs& A, cudaEvent_t* ev = nullptr)
 {
@@ -303,52 +369,36 @@ static cfd_status launch_sweeps(cfd_ctx* ctx, SweepArgs& A, cudaEvent_t* ev = nu
         else k_sweep_x<R, 128, EP_STORE><<<grid, 128, 0, ctx->stream>>>(A);
         LAUNCH_CHECK();
     }
-    const size_t smem = 4 * 80 * 32 * sizeof(R);
     if (ev) cudaEventRecord(ev[1], ctx->stream);
-    // eta
-    {
-        int lo = g.per[1] ? 0 : 1, hi = g.per[1] ? g.ny : g.ny - 1;
-        long long nseg = (hi - lo + A.seg_len - 1) / A.seg_len;
-        long long warps = (long long)((g.nx + 31) / 32) * g.nz * nseg;
-        k_sweep_s<R, 1, EP_ACCUM><<<(unsigned)((warps + 3) / 4), 128, smem, ctx->stream>>>(A);
-        LAUNCH_CHECK();
-    }
+    cfd_status st = launch_sweep_dir<R, 1, EP_ACCUM>(ctx, A, ctx->sweep_kind[1], ctx->sweep_param[1]);
+    if (st != CFD_OK) return st;
     if (ev) cudaEventRecord(ev[2], ctx->stream);
     // zeta (final: L = J R, then RK or output)
-    {
-        int lo = g.per[2] ? 0 : 1, hi = g.per[2] ? g.nz : g.nz - 1;
-        long long nseg = (hi - lo + A.seg_len - 1) / A.seg_len;
-        long long warps = (long long)((g.nx + 31) / 32) * g.ny * nseg;
-        k_sweep_s<R, 2, EPF><<<(unsigned)((warps + 3) / 4), 128, smem, ctx->stream>>>(A);
-        LAUNCH_CHECK();
-    }
+    st = launch_sweep_dir<R, 2, EPF>(ctx, A, ctx->sweep_kind[2], ctx->sweep_param[2]);
+    if (st != CFD_OK) return st;
     if (ev) cudaEventRecord(ev[3], ctx->stream);
     return CFD_OK;
 }
 
-// one evaluation of the right-hand side of Uin; EPF selects the epilogue
-template <int EPF>
-static cfd_status run_stage(cfd_ctx* ctx, const double* Uin, const double* Un, double* Uout, double* Lout,
-                            double a, double b, cudaEvent_t* ev = nullptr)
+template <class R, int DIR, int EP>
+static cudaError_t set_sweep_attrs()
 {
-    const Geo& g = ctx->g;
-    const long long N = g.N;
-    if (ev) cudaEventRecord(ev[0], ctx->stream);
-    k_prim<double><<<grid_for(N, 256), 256, 0, ctx->stream>>>(g, ctx->ph, Uin, (double*)ctx->b.P, ctx->err);
-    LAUNCH_CHECK();
-    if (ev) cudaEventRecord(ev[1], ctx->stream);
-    if (ctx->prm.scheme == CFD_HYBRID && !ctx->forced) {
-        k_sensor<<<grid_for(N, 256), 256, 0, ctx->stream>>>(g, ctx->ph, (const double*)ctx->b.P + 4 * N, ctx->b.cls);
-        LAUNCH_CHECK();
-    }
-    if (ev) cudaEventRecord(ev[2], ctx->stream);
-    if (ctx->ph.viscous) {
-        k_visc_flux<double><<<grid_for(N, 256), 256, 0, ctx->stream>>>(g, ctx->ph, (const double*)ctx->b.P,
-                                                                          (double*)ctx->b.Fv);
-        LAUNCH_CHECK();
-    }
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_s<R, DIR, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(4 * 80 * 32 * sizeof(R)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<R, 16>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<R, 32>());
+    return e;
+}
+
+static SweepArgs make_args(cfd_ctx* ctx, const double* Uin, const double* Un, double* Uout, double* Lout, double a,
+                           double b)
+{
     SweepArgs A{};
-    A.g = g;
+    A.g = ctx->g;
     A.ph = ctx->ph;
     A.P = ctx->b.P;
     A.cls = ctx->prm.scheme == CFD_HYBRID ? ctx->b.cls : nullptr;
@@ -362,8 +412,153 @@ static cfd_status run_stage(cfd_ctx* ctx, const double* Uin, const double* Un, d
     A.rk_a = a;
     A.rk_b = b;
     A.seg_len = ctx->seg_len;
+    return A;
+}
+
+// one evaluation of the right-hand side of Uin; EPF selects the epilogue
+template <class R, int EPF>
+static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un, double* Uout, double* Lout,
+                              double a, double b, cudaEvent_t* ev)
+{
+    const Geo& g = ctx->g;
+    const long long N = g.N;
+    const bool mixed = sizeof(R) == sizeof(float);
+    if (ev) cudaEventRecord(ev[0], ctx->stream);
+    const NodeLaunch nl = node_launch(g);
+    if (mixed)
+        k_prim_mixed<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, Uin, (float*)ctx->b.P, ctx->b.cls, ctx->err);
+    else
+        k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, Uin, (double*)ctx->b.P, ctx->err);
+    LAUNCH_CHECK();
+    if (ev) cudaEventRecord(ev[1], ctx->stream);
+    if (!ctx->forced && (mixed || ctx->prm.scheme == CFD_HYBRID)) {
+        if (mixed)
+            k_sensor32<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const float*)ctx->b.P + 4 * N, ctx->b.cls);
+        else
+            k_sensor<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const double*)ctx->b.P + 4 * N, ctx->b.cls);
+        LAUNCH_CHECK();
+    }
+    if (ev) cudaEventRecord(ev[2], ctx->stream);
+    if (ctx->ph.viscous) {
+        k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P, (R*)ctx->b.Fv);
+        LAUNCH_CHECK();
+    }
+    SweepArgs A = make_args(ctx, Uin, Un, Uout, Lout, a, b);
     if (ev) cudaEventRecord(ev[3], ctx->stream);
-    return launch_sweeps<double, EPF>(ctx, A, ev ? ev + 3 : nullptr);
+    return launch_sweeps<R, EPF>(ctx, A, ev ? ev + 3 : nullptr);
+}
+
+template <int EPF>
+static cfd_status run_stage(cfd_ctx* ctx, const double* Uin, const double* Un, double* Uout, double* Lout,
+                            double a, double b, cudaEvent_t* ev = nullptr)
+{
+    if (ctx->prm.precision == CFD_FP32_BULK) return run_stage_t<float, EPF>(ctx, Uin, Un, Uout, Lout, a, b, ev);
+    return run_stage_t<double, EPF>(ctx, Uin, Un, Uout, Lout, a, b, ev);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: picks the eta and zeta sweep variant (streaming with segment 128
+// or 64, tile with 32 or 16 nodes) by timing each on the context's own state.
+// Results are identical bit for bit across variants; only speed differs.
+// Tuned choices are cached per process by precision, grid and scheme.
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+    int prec, nx, ny, nz, per0, per1, per2, scheme, viscous;
+    bool operator==(const TuneKey& o) const
+    {
+        return prec == o.prec && nx == o.nx && ny == o.ny && nz == o.nz && per0 == o.per0 && per1 == o.per1 &&
+               per2 == o.per2 && scheme == o.scheme && viscous == o.viscous;
+    }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, std::vector<int>>> g_tune_cache;
+}  // namespace
+
+static TuneKey tune_key(const cfd_ctx* ctx)
+{
+    return {ctx->prm.precision, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->g.per[0], ctx->g.per[1], ctx->g.per[2],
+            ctx->prm.scheme, ctx->ph.viscous};
+}
+
+template <class R>
+static cfd_status autotune_t(cfd_ctx* ctx)
+{
+    cfd_status st = run_stage<EP_FINAL_RHS>(ctx, ctx->b.U, nullptr, nullptr, ctx->b.Uk, 0.0, 1.0);
+    if (st != CFD_OK) return st;
+    SweepArgs A = make_args(ctx, ctx->b.U, nullptr, nullptr, ctx->b.Uk, 0.0, 1.0);
+    const int cands[4][2] = {{0, 128}, {0, 64}, {1, 32}, {1, 16}};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (int dir = 1; dir <= 2 && st == CFD_OK; ++dir) {
+        float best = 1e30f;
+        for (int c = 0; c < 4 && st == CFD_OK; ++c) {
+            for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, ctx->stream);
+                if (dir == 1) st = launch_sweep_dir<R, 1, EP_ACCUM>(ctx, A, cands[c][0], cands[c][1]);
+                else st = launch_sweep_dir<R, 2, EP_FINAL_RHS>(ctx, A, cands[c][0], cands[c][1]);
+            }
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, CFD_ECUDA, "autotune timing");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == CFD_OK && ms < best) {
+                best = ms;
+                ctx->sweep_kind[dir] = cands[c][0];
+                ctx->sweep_param[dir] = cands[c][1];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+static cfd_status autotune(cfd_ctx* ctx)
+{
+    if (ctx->tuned) return CFD_OK;
+    const TuneKey key = tune_key(ctx);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto& kv : g_tune_cache)
+            if (kv.first == key) {
+                for (int d = 1; d <= 2; ++d) {
+                    ctx->sweep_kind[d] = kv.second[2 * d - 2];
+                    ctx->sweep_param[d] = kv.second[2 * d - 1];
+                }
+                ctx->tuned = true;
+                return CFD_OK;
+            }
+    }
+    cfd_status st = ctx->prm.precision == CFD_FP32_BULK ? autotune_t<float>(ctx) : autotune_t<double>(ctx);
+    if (st != CFD_OK) return st;
+    ctx->tuned = true;
+    ctx->graph_valid = false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.push_back({key, {ctx->sweep_kind[1], ctx->sweep_param[1], ctx->sweep_kind[2], ctx->sweep_param[2]}});
+    return CFD_OK;
+}
+
+extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param)
+{
+    if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
+    if (dir < 1 || dir > 2 || kind < 0 || kind > 1) return fail(ctx, CFD_EINVAL, "dir must be 1 or 2, kind 0 or 1");
+    if (kind == 1 && param != 16 && param != 32) return fail(ctx, CFD_EINVAL, "tile length must be 16 or 32");
+    if (kind == 0 && (param < 1 || param > 65535)) return fail(ctx, CFD_EINVAL, "segment length out of range");
+    ctx->sweep_kind[dir] = kind;
+    ctx->sweep_param[dir] = param;
+    ctx->tuned = true;
+    ctx->graph_valid = false;
+    return CFD_OK;
+}
+
+extern "C" cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param)
+{
+    if (!ctx || !kind || !param || dir < 1 || dir > 2) return fail(ctx, CFD_EINVAL, "bad argument");
+    *kind = ctx->sweep_kind[dir];
+    *param = ctx->sweep_param[dir];
+    return CFD_OK;
 }
 
 static cfd_status read_err(cfd_ctx* ctx)
@@ -425,6 +620,7 @@ extern "C" cfd_status cfd_set_state(cfd_ctx* ctx, int block, const double* U, in
     const long long N = ctx->g.N;
     CU(cudaMemcpyAsync(ctx->b.U, U, 5 * N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        ctx->stream));
+    if (ctx->prm.precision == CFD_FP32_BULK && !ctx->forced) CU(cudaMemsetAsync(ctx->b.cls, 2, N, ctx->stream));
     st = launch_bc(ctx, ctx->b.U, 0.0, false);
     if (st != CFD_OK) return st;
     if (!on_device) CU(cudaStreamSynchronize(ctx->stream));
@@ -448,6 +644,8 @@ extern "C" cfd_status cfd_rhs(cfd_ctx* ctx, int block, double* dUdt, int on_devi
     if (st != CFD_OK) return st;
     if (!dUdt) return fail(ctx, CFD_EINVAL, "null output");
     const long long N = ctx->g.N;
+    st = autotune(ctx);
+    if (st != CFD_OK) return st;
     double* Lout = dUdt;
     if (!on_device) Lout = ctx->b.Uk;  // stage buffer is free between steps
     st = run_stage<EP_FINAL_RHS>(ctx, ctx->b.U, nullptr, nullptr, Lout, 0.0, 1.0);
@@ -505,7 +703,8 @@ static cfd_status build_graph(cfd_ctx* ctx)
 
 static long long launches_per_step(const cfd_ctx* ctx)
 {
-    long long per_stage = 1 + 3 + (ctx->prm.scheme == CFD_HYBRID && !ctx->forced ? 1 : 0) + (ctx->ph.viscous ? 1 : 0);
+    const bool sensor = !ctx->forced && (ctx->prm.scheme == CFD_HYBRID || ctx->prm.precision == CFD_FP32_BULK);
+    long long per_stage = 1 + 3 + (sensor ? 1 : 0) + (ctx->ph.viscous ? 1 : 0);
     long long bc = 0;
     for (int d = 0; d < 3; ++d) bc += ctx->g.per[d] ? 0 : 1;
     return 3 * (per_stage + bc) + 1;
@@ -518,6 +717,10 @@ extern "C" cfd_status cfd_step(cfd_ctx* ctx, double dt, int nsteps)
     if (nsteps == 0) return CFD_OK;
     k_set_scalar<<<1, 32, 0, ctx->stream>>>(ctx->dt, dt);
     LAUNCH_CHECK();
+    {
+        cfd_status st = autotune(ctx);
+        if (st != CFD_OK) return st;
+    }
     if (!ctx->graph_valid) {
         cfd_status st = build_graph(ctx);
         if (st != CFD_OK) return st;
@@ -535,10 +738,18 @@ extern "C" cfd_status cfd_cfl_dt(cfd_ctx* ctx, int block, double cfl, double* dt
     if (st != CFD_OK) return st;
     if (!dt || !(cfl > 0.0)) return fail(ctx, CFD_EINVAL, "bad cfl or null output");
     const Geo& g = ctx->g;
-    k_prim<double><<<grid_for(g.N, 256), 256, 0, ctx->stream>>>(g, ctx->ph, ctx->b.U, (double*)ctx->b.P, ctx->err);
+    const bool mixed = ctx->prm.precision == CFD_FP32_BULK;
+    const NodeLaunch nl = node_launch(g);
+    if (mixed)
+        k_prim_mixed<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, ctx->b.U, (float*)ctx->b.P, ctx->b.cls, ctx->err);
+    else
+        k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, ctx->b.U, (double*)ctx->b.P, ctx->err);
     LAUNCH_CHECK();
     CU(cudaMemsetAsync(ctx->cflmax, 0, sizeof(unsigned long long), ctx->stream));
-    k_cfl<double><<<grid_for(g.N, 256), 256, 0, ctx->stream>>>(g, (const double*)ctx->b.P, ctx->cflmax);
+    if (mixed)
+        k_cfl<float><<<grid_for(g.N, 256), 256, 0, ctx->stream>>>(g, (const float*)ctx->b.P, ctx->cflmax);
+    else
+        k_cfl<double><<<grid_for(g.N, 256), 256, 0, ctx->stream>>>(g, (const double*)ctx->b.P, ctx->cflmax);
     LAUNCH_CHECK();
     CU(cudaMemcpyAsync(ctx->h_pinned + 4, ctx->cflmax, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     st = read_err(ctx);
@@ -653,6 +864,10 @@ extern "C" cfd_status cfd_fma_peak(int precision, double* tflops)
 extern "C" cfd_status cfd_profile_stage(cfd_ctx* ctx, int reps, double* ms)
 {
     if (!ctx || !ms || reps < 1) return fail(ctx, CFD_EINVAL, "bad argument to cfd_profile_stage");
+    {
+        cfd_status st0 = autotune(ctx);
+        if (st0 != CFD_OK) return st0;
+    }
     cudaEvent_t ev[7];
     for (int i = 0; i < 7; ++i) CU(cudaEventCreate(&ev[i]));
     for (int i = 0; i < CFD_PROFILE_KERNELS; ++i) ms[i] = 0.0;
@@ -750,6 +965,8 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
         return fail(nullptr, CFD_EINVAL, "null argument to cfd_rhs_noalloc");
     cfd_status st = validate(nullptr, grid, params);
     if (st != CFD_OK) return st;
+    if (params->precision != CFD_FP64)
+        return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc computes in FP64 only");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > kMaxNodes)
         return fail(nullptr, CFD_ENOMEM, "cfd_rhs_noalloc: grid has more than CFD_NOALLOC_MAX_NODES nodes");
@@ -796,14 +1013,15 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
     // the only value that must start at zero; every other array is fully
     // written before it is read
     NA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
-    k_prim<double><<<grid_for(N, 256), 256, 0, s>>>(g, ph, U, (double*)P, err);
+    const NodeLaunch nl = node_launch(g);
+    k_prim<double><<<nl.grid, nl.block, 0, s>>>(g, ph, U, (double*)P, err);
     NA_CHECK(cudaGetLastError());
     if (params->scheme == CFD_HYBRID) {
-        k_sensor<<<grid_for(N, 256), 256, 0, s>>>(g, ph, (const double*)P + 4 * N, cls);
+        k_sensor<<<nl.grid, nl.block, 0, s>>>(g, ph, (const double*)P + 4 * N, cls);
         NA_CHECK(cudaGetLastError());
     }
     if (ph.viscous) {
-        k_visc_flux<double><<<grid_for(N, 256), 256, 0, s>>>(g, ph, (const double*)P, (double*)Fv);
+        k_visc_flux<double><<<nl.grid, nl.block, 0, s>>>(g, ph, (const double*)P, (double*)Fv);
         NA_CHECK(cudaGetLastError());
     }
     SweepArgs A{};

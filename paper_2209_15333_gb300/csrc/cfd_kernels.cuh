@@ -10,6 +10,7 @@
 //   met          [31][M] double  metrics per metric point (M = N, nx*ny or 1):
 //                                0-8 raw (xi_x..zeta_z), 9 J, 10-18 alpha = raw/J,
 //                                19-21 sigma_d = |alpha_d|, 22-30 k_d = alpha_d/sigma_d
+//   metf         [31][M] float   the same metrics rounded once, read by the FP32 kernels
 #pragma once
 #include <cstdint>
 
@@ -27,6 +28,7 @@ struct Geo {
     int mlayout;          // 0 3-D, 1 2-D, 2 uniform
     long long M;          // metric points
     const double* met;    // [31][M]
+    const float* metf;    // [31][M] float mirror (FP32 kernels)
 };
 
 struct Phys {
@@ -38,7 +40,17 @@ struct Phys {
     int scheme;            // 0 UD7, 1 WENO5, 2 WENO7, 3 HYBRID
     double th1, th2, eps;
     int vorder;
+    // the constants rounded once to float, for the FP32 kernels (no
+    // double-to-float conversion in the loops: it runs on the FP64 pipe)
+    float gm1f, inv_gm1f, inv2gf, invRef, kcoeff, omegaf, suth_sf, th1f, th2f, epsf, gMa2f, invMaf;
 };
+
+template <class R>
+__device__ __forceinline__ R pk(double d, float f);
+template <>
+__device__ __forceinline__ double pk<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pk<float>(double, float f) { return f; }
 
 struct BCData {
     const double* inflow;  // [5][ny] or null
@@ -48,10 +60,12 @@ struct BCData {
     const double* wall_z;  // [nz]
 };
 
+// periodic wrap for offsets of a few nodes (no integer division)
 __device__ __forceinline__ int wrapi(int m, int n)
 {
-    int r = m % n;
-    return r < 0 ? r + n : r;
+    while (m < 0) m += n;
+    while (m >= n) m -= n;
+    return m;
 }
 
 __device__ __forceinline__ long long midx(const Geo& g, int i, int j, long long n)
@@ -64,6 +78,26 @@ __device__ __forceinline__ double metv(const Geo& g, int e, long long mi)
     return __ldg(g.met + (long long)e * g.M + mi);
 }
 
+template <class R>
+__device__ __forceinline__ R metr(const Geo& g, int e, long long mi);
+template <>
+__device__ __forceinline__ double metr<double>(const Geo& g, int e, long long mi)
+{
+    return __ldg(g.met + (long long)e * g.M + mi);
+}
+template <>
+__device__ __forceinline__ float metr<float>(const Geo& g, int e, long long mi)
+{
+    return __ldg(g.metf + (long long)e * g.M + mi);
+}
+
+// node (i, j, k) of a node-parallel kernel launched on a (x-chunks, ny, nz) grid
+#define NODE_IJK(g)                                                                                   \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;                                              \
+    if (i >= (g).nx) return;                                                                          \
+    const int j = blockIdx.y, k = blockIdx.z;                                                         \
+    const long long n = (long long)i + (long long)(g).nx * ((long long)j + (long long)(g).ny * k)
+
 __device__ __forceinline__ bool is_bnd(const Geo& g, int i, int j, int k)
 {
     return (!g.per[0] && (i == 0 || i == g.nx - 1)) || (!g.per[1] && (j == 0 || j == g.ny - 1)) ||
@@ -73,6 +107,13 @@ __device__ __forceinline__ bool is_bnd(const Geo& g, int i, int j, int k)
 // ---------------------------------------------------------------------------
 // metric set-up: derived quantities per metric point (Eq. 19, 22, 27)
 // ---------------------------------------------------------------------------
+__global__ void k_metric_float(const double* met, float* metf, long long count)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        metf[t] = (float)met[t];
+}
+
 __global__ void k_metric_derive(double* met, long long M)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < M;
@@ -101,8 +142,10 @@ __global__ void k_prim(Geo g, Phys ph, const double* __restrict__ U, RT* __restr
                        int* __restrict__ err)
 {
     const long long N = g.N;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
+    NODE_IJK(g);
+    (void)j;
+    (void)k;
+    {
         double rho = U[n];
         double u = __ddiv_rn(U[N + n], rho);
         double v = __ddiv_rn(U[2 * N + n], rho);
@@ -124,6 +167,58 @@ __global__ void k_prim(Geo g, Phys ph, const double* __restrict__ U, RT* __restr
     }
 }
 
+// Mixed precision: primitives in FP32 arithmetic, except within 4 nodes of a
+// wall and at nodes whose previous sensor class is not UD7 (shocks), where the
+// recovery runs in FP64 (catastrophic cancellation in E - rho|u|^2/2 is worst
+// there); stored as float in both cases.
+__device__ __forceinline__ bool near_wall(const Geo& g, int i, int j, int k)
+{
+    const int pos[3] = {i, j, k};
+    const int nd[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (g.bc_lo[d] == 1 && pos[d] < 4) return true;
+        if (g.bc_hi[d] == 1 && pos[d] > nd[d] - 5) return true;
+    }
+    return false;
+}
+
+__global__ void k_prim_mixed(Geo g, Phys ph, const double* __restrict__ U, float* __restrict__ P,
+                             const uint8_t* __restrict__ cls_prev, int* __restrict__ err)
+{
+    const long long N = g.N;
+    NODE_IJK(g);
+    {
+        float rho, u, v, w, p, T, c;
+        if (cls_prev[n] != 0 || near_wall(g, i, j, k)) {
+            double rd = U[n];
+            double ri = 1.0 / rd;
+            double ud = U[N + n] * ri, vd = U[2 * N + n] * ri, wd = U[3 * N + n] * ri;
+            double pd = ph.gm1 * (U[4 * N + n] - 0.5 * rd * (ud * ud + vd * vd + wd * wd));
+            double Td = ph.gMa2 * pd * ri;
+            rho = (float)rd; u = (float)ud; v = (float)vd; w = (float)wd; p = (float)pd; T = (float)Td;
+            c = sqrtf(T) * ph.invMaf;
+        } else {
+            rho = (float)U[n];
+            float ri = 1.0f / rho;
+            u = (float)U[N + n] * ri;
+            v = (float)U[2 * N + n] * ri;
+            w = (float)U[3 * N + n] * ri;
+            p = ph.gm1f * ((float)U[4 * N + n] - 0.5f * rho * (u * u + v * v + w * w));
+            T = ph.gMa2f * p * ri;
+            c = sqrtf(T) * ph.invMaf;
+        }
+        if (!(rho > 0.0f) || !(p > 0.0f) || !(T < 1e30f) || !(fabsf(u) + fabsf(v) + fabsf(w) < 1e30f)) *err = 1;
+        P[n] = rho;
+        P[N + n] = u;
+        P[2 * N + n] = v;
+        P[3 * N + n] = w;
+        P[4 * N + n] = p;
+        P[5 * N + n] = T;
+        P[6 * N + n] = c;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // modified Jameson sensor (Eq. 42-43), evaluated in double with the same
 // operation order as a plain IEEE evaluation, so class decisions match.
@@ -137,13 +232,9 @@ __device__ __forceinline__ double sensor_phi(double pm, double p0, double pp)
 
 __global__ void k_sensor(Geo g, Phys ph, const double* __restrict__ p, uint8_t* __restrict__ cls)
 {
-    const long long N = g.N;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(n % nx);
-        int j = (int)((n / nx) % ny);
-        int k = (int)(n / ((long long)nx * ny));
+    NODE_IJK(g);
+    {
         double p0 = p[n];
         double phi[3];
         const int pos[3] = {i, j, k};
@@ -165,6 +256,30 @@ __global__ void k_sensor(Geo g, Phys ph, const double* __restrict__ p, uint8_t* 
     }
 }
 
+// the same sensor in FP32 arithmetic on FP32 pressures (mixed precision)
+__global__ void k_sensor32(Geo g, Phys ph, const float* __restrict__ p, uint8_t* __restrict__ cls)
+{
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const float th1 = ph.th1f, th2 = ph.th2f;
+    NODE_IJK(g);
+    {
+        float p0 = p[n];
+        const int pos[3] = {i, j, k};
+        const int nd[3] = {nx, ny, nz};
+        const long long st[3] = {1, nx, (long long)nx * ny};
+        float th = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int m = pos[d];
+            if (!g.per[d] && (m == 0 || m == nd[d] - 1)) continue;
+            float pm = p[n + (long long)(wrapi(m - 1, nd[d]) - m) * st[d]];
+            float pp = p[n + (long long)(wrapi(m + 1, nd[d]) - m) * st[d]];
+            th += fabsf(-pm + 2.0f * p0 - pp) / (pm + 2.0f * p0 + pp);
+        }
+        cls[n] = th <= th1 ? 0 : (th <= th2 ? 1 : 2);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Steger-Warming split fluxes at one node (Eq. 20-30, Eq. 23 as corrected).
 // With s = l4 + l5 and dl = l5 - l4 the corrected Eq. 23 reads
@@ -176,14 +291,14 @@ template <class R>
 __device__ __forceinline__ void sw_split(const Phys& ph, R rho, R u, R v, R w, R c, R k1, R k2, R k3,
                                          R sig, R fp[5], R fm[5])
 {
-    const R gm1 = (R)ph.gm1;
+    const R gm1 = pk<R>(ph.gm1, ph.gm1f);
     R uk = k1 * u + k2 * v + k3 * w;
     R V = sig * uk;
     R cs = c * sig;
     R l4 = V - cs, l5 = V + cs;
     R q2 = u * u + v * v + w * w;
-    R H = (R)0.5 * q2 + c * c * (R)ph.inv_gm1;
-    R a = rho * (R)ph.inv2g;
+    R H = (R)0.5 * q2 + c * c * pk<R>(ph.inv_gm1, ph.inv_gm1f);
+    R a = rho * pk<R>(ph.inv2g, ph.inv2gf);
     R gq = gm1 * q2;
     R ac = a * c;
     {
@@ -263,9 +378,16 @@ __device__ __forceinline__ R weno7(const R v[7], R eps)
     R b2 = eps + beta_rows<R>(S2, SD, v + 2);
     R b3 = eps + beta_rows<R>(S3, SD, v + 3);
     R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2, t3 = b3 * b3;
-    R p01 = t0 * t1, p23 = t2 * t3;
-    R w0 = (R)D[0] * t1 * p23, w1 = (R)D[1] * t0 * p23;
-    R w2 = (R)D[2] * t3 * p01, w3 = (R)D[3] * t2 * p01;
+    R w0, w1, w2, w3;
+    if (sizeof(R) == 8) {
+        R p01 = t0 * t1, p23 = t2 * t3;
+        w0 = (R)D[0] * t1 * p23; w1 = (R)D[1] * t0 * p23;
+        w2 = (R)D[2] * t3 * p01; w3 = (R)D[3] * t2 * p01;
+    } else {
+        // FP32: products of three squared indicators (>= eps^6) would reach
+        // the denormal range, so divide per candidate
+        w0 = (R)D[0] / t0; w1 = (R)D[1] / t1; w2 = (R)D[2] / t2; w3 = (R)D[3] / t3;
+    }
     return (w0 * q0 + w1 * q1 + w2 * q2 + w3 * q3) / (w0 + w1 + w2 + w3);
 }
 
@@ -285,9 +407,15 @@ __device__ __forceinline__ R weno5(const R v[7], R eps, int mask)
     R b1 = eps + beta_rows<R>(S1, SD, v + 2);
     R b2 = eps + beta_rows<R>(S2, SD, v + 3);
     R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2;
-    R w0 = (mask & 1) ? (R)0 : (R)D[0] * t1 * t2;
-    R w1 = (mask & 2) ? (R)0 : (R)D[1] * t0 * t2;
-    R w2 = (mask & 4) ? (R)0 : (R)D[2] * t0 * t1;
+    R w0, w1, w2;
+    if (sizeof(R) == 8) {
+        w0 = (R)D[0] * t1 * t2; w1 = (R)D[1] * t0 * t2; w2 = (R)D[2] * t0 * t1;
+    } else {
+        w0 = (R)D[0] / t0; w1 = (R)D[1] / t1; w2 = (R)D[2] / t2;
+    }
+    if (mask & 1) w0 = (R)0;
+    if (mask & 2) w1 = (R)0;
+    if (mask & 4) w2 = (R)0;
     return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
 }
 
@@ -368,15 +496,36 @@ __device__ __forceinline__ R dcentral(int order, int per, int n, int m, Ld f)
            ((R)(32.0 / 840.0)) * (f(m + 3) - f(m - 3)) + ((R)(-3.0 / 840.0)) * (f(m + 4) - f(m - 4));
 }
 
+// central derivative on a tile: f(m) takes unwrapped line positions, so the
+// periodic form needs no wrap (the tile rows already hold the wrapped nodes)
+template <class R, class Ld>
+__device__ __forceinline__ R dcentral_tile(int order, int per, int n, int m, Ld f)
+{
+    if (per) {
+        if (order == 8)
+            return ((R)(672.0 / 840.0)) * (f(m + 1) - f(m - 1)) + ((R)(-168.0 / 840.0)) * (f(m + 2) - f(m - 2)) +
+                   ((R)(32.0 / 840.0)) * (f(m + 3) - f(m - 3)) + ((R)(-3.0 / 840.0)) * (f(m + 4) - f(m - 4));
+        return ((R)(45.0 / 60.0)) * (f(m + 1) - f(m - 1)) + ((R)(-9.0 / 60.0)) * (f(m + 2) - f(m - 2)) +
+               ((R)(1.0 / 60.0)) * (f(m + 3) - f(m - 3));
+    }
+    return dcentral<R>(order, 0, n, m, f);
+}
+
 // ---------------------------------------------------------------------------
 // viscous fluxes at nodes (Eqs. 9-15 with readings R13-R15)
 // ---------------------------------------------------------------------------
-template <class R>
-__device__ __forceinline__ R viscosity(const Phys& ph, R T)
+__device__ __forceinline__ double viscosity(const Phys& ph, double T)
 {
-    if (ph.visc_law == 1) return (R)pow((double)T, ph.omega);
-    R s = (R)ph.suth_s;
-    return T * sqrt(T) * ((R)1 + s) / (T + s);
+    if (ph.visc_law == 1) return pow(T, ph.omega);
+    double s = ph.suth_s;
+    return T * sqrt(T) * (1.0 + s) / (T + s);
+}
+
+__device__ __forceinline__ float viscosity(const Phys& ph, float T)
+{
+    if (ph.visc_law == 1) return powf(T, ph.omegaf);
+    float s = ph.suth_sf;
+    return T * sqrtf(T) * (1.0f + s) / (T + s);
 }
 
 template <class R>
@@ -385,31 +534,35 @@ __global__ void __launch_bounds__(256) k_visc_flux(Geo g, Phys ph, const R* __re
     const long long N = g.N;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int ord = ph.vorder;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(n % nx);
-        int j = (int)((n / nx) % ny);
-        int k = (int)(n / ((long long)nx * ny));
-        const long long st[3] = {1, nx, (long long)nx * ny};
+    NODE_IJK(g);
+    {
+        const int st[3] = {1, nx, nx * ny};
         const int pos[3] = {i, j, k};
         const int nd[3] = {nx, ny, nz};
+        // element offsets of the line positions m-4..m+4 in each direction,
+        // computed once and shared by the four fields (periodic lines wrap)
+        int off[3][9];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int t = 0; t < 9; ++t)
+                off[d][t] = g.per[d] ? (wrapi(pos[d] + t - 4, nd[d]) - pos[d]) * st[d] : (t - 4) * st[d];
         // dq[var][d]: var = u, v, w, T (P rows 1, 2, 3, 5)
         R dq[4][3];
 #pragma unroll
         for (int var = 0; var < 4; ++var) {
-            const R* f = P + (long long)(var < 3 ? var + 1 : 5) * N;
+            const R* f = P + (long long)(var < 3 ? var + 1 : 5) * N + n;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const long long base = n - (long long)pos[d] * st[d];
-                const long long s = st[d];
-                dq[var][d] = dcentral<R>(ord, g.per[d], nd[d], pos[d],
-                                         [&](int m) { return __ldg(f + base + (long long)m * s); });
+                const int m = pos[d];
+                dq[var][d] = dcentral_tile<R>(ord, g.per[d], nd[d], m,
+                                              [&](int mm) { return __ldg(f + off[d][mm - m + 4]); });
             }
         }
         const long long mi = midx(g, i, j, n);
         R mraw[9];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) mraw[e] = (R)metv(g, M_RAW + e, mi);
+        for (int e = 0; e < 9; ++e) mraw[e] = metr<R>(g, M_RAW + e, mi);
         R gr[4][3];
 #pragma unroll
         for (int var = 0; var < 4; ++var)
@@ -417,8 +570,8 @@ __global__ void __launch_bounds__(256) k_visc_flux(Geo g, Phys ph, const R* __re
             for (int x = 0; x < 3; ++x)
                 gr[var][x] = mraw[x] * dq[var][0] + mraw[3 + x] * dq[var][1] + mraw[6 + x] * dq[var][2];
         R T = P[5 * N + n];
-        R mu = viscosity<R>(ph, T);
-        R mr = mu * (R)ph.invRe;
+        R mu = viscosity(ph, T);
+        R mr = mu * pk<R>(ph.invRe, ph.invRef);
         R div = gr[0][0] + gr[1][1] + gr[2][2];
         R tau[3][3];
 #pragma unroll
@@ -426,15 +579,15 @@ __global__ void __launch_bounds__(256) k_visc_flux(Geo g, Phys ph, const R* __re
 #pragma unroll
             for (int b = 0; b < 3; ++b)
                 tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? ((R)(2.0 / 3.0)) * div : (R)0));
-        R kc = mu * (R)ph.kcoef;
+        R kc = mu * pk<R>(ph.kcoef, ph.kcoeff);
         R u = P[N + n], v = P[2 * N + n], w = P[3 * N + n];
         R Th[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) Th[a] = u * tau[a][0] + v * tau[a][1] + w * tau[a][2] + kc * gr[3][a];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            R a0 = (R)metv(g, M_ALPHA + 3 * d, mi), a1 = (R)metv(g, M_ALPHA + 3 * d + 1, mi),
-              a2 = (R)metv(g, M_ALPHA + 3 * d + 2, mi);
+            R a0 = metr<R>(g, M_ALPHA + 3 * d, mi), a1 = metr<R>(g, M_ALPHA + 3 * d + 1, mi),
+              a2 = metr<R>(g, M_ALPHA + 3 * d + 2, mi);
 #pragma unroll
             for (int row = 0; row < 3; ++row)
                 Fv[(long long)(4 * d + row) * N + n] = a0 * tau[0][row] + a1 * tau[1][row] + a2 * tau[2][row];
@@ -520,8 +673,8 @@ __device__ __forceinline__ void node_split(const SweepArgs& A, int d, long long 
     const long long N = A.g.N;
     const long long mi = midx(A.g, i, j, n);
     R rho = P[n], u = P[N + n], v = P[2 * N + n], w = P[3 * N + n], c = P[6 * N + n];
-    R k1 = (R)metv(A.g, M_K + 3 * d, mi), k2 = (R)metv(A.g, M_K + 3 * d + 1, mi),
-      k3 = (R)metv(A.g, M_K + 3 * d + 2, mi), sg = (R)metv(A.g, M_SIG + d, mi);
+    R k1 = metr<R>(A.g, M_K + 3 * d, mi), k2 = metr<R>(A.g, M_K + 3 * d + 1, mi),
+      k3 = metr<R>(A.g, M_K + 3 * d + 2, mi), sg = metr<R>(A.g, M_SIG + d, mi);
     sw_split<R>(A.ph, rho, u, v, w, c, k1, k2, k3, sg, fp, fm);
 }
 
@@ -531,6 +684,7 @@ __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
 {
     __shared__ R sf[10][BX + 8];
     __shared__ R sh[5][BX + 1];
+    __shared__ R sv[4][BX + 8];
     __shared__ uint8_t sc[BX + 8];
     const Geo& g = A.g;
     const int n = g.nx;
@@ -549,9 +703,17 @@ __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
             int ii = per ? wrapi(i, n) : i;
             node_split<R>(A, 0, row + ii, ii, j, fp, fm);
             if (A.cls) c = A.cls[row + ii];
+            if (A.Fv) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) sv[r][s] = ((const R*)A.Fv)[(long long)r * g.N + row + ii];
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < 5; ++q) fp[q] = fm[q] = (R)0;
+            if (A.Fv) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) sv[r][s] = (R)0;
+            }
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
@@ -581,7 +743,7 @@ __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
                 p8[o] = sf[q][s0 + o];
                 m8[o] = sf[5 + q][s0 + o];
             }
-            sh[q][slot] = face_flux<R>(use, p8, m8, (R)A.ph.eps, mp, mm);
+            sh[q][slot] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mp, mm);
         }
     }
     __syncthreads();
@@ -592,7 +754,11 @@ __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
         R val[5];
 #pragma unroll
         for (int q = 0; q < 5; ++q) val[q] = -(sh[q][t + 1] - sh[q][t]);
-        if (A.Fv) visc_div<R>(A, 0, row, 1, n, i, val);
+        if (A.Fv) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                val[r + 1] += dcentral_tile<R>(A.ph.vorder, per, n, i, [&](int mm) { return sv[r][mm - (i0 - 4)]; });
+        }
         epilogue<R, EP>(A, nn, i, j, k, val);
     }
     // zero the non-periodic boundary nodes of the accumulator
@@ -678,7 +844,7 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
                     p8[b] = ring[(sl * 10 + q) * 32 + lane];
                     m8[b] = ring[(sl * 10 + 5 + q) * 32 + lane];
                 }
-                fh[q] = face_flux<R>(use, p8, m8, (R)A.ph.eps, mp, mm);
+                fh[q] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mp, mm);
             }
             if (s >= 8 && lane_ok) {
                 const int mn = m - 4;  // node
@@ -697,6 +863,134 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
             for (int q = 0; q < 5; ++q) fprev[q] = fh[q];
         }
     }
+}
+
+// eta / zeta sweep on tiles: 32 consecutive x (lanes) by TL nodes along the
+// sweep line plus a 4-node halo on each side.  The split fluxes and the
+// viscous fluxes of the tile are staged in shared memory by all 8 warps at
+// once (many loads in flight), faces are computed from shared memory, then
+// differenced.  The halo costs 8/TL extra splits -- cheap in FP32, where the
+// streaming form is latency-bound instead.
+template <class R, int DIR, int EP, int TL>
+__global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A)
+{
+    constexpr int ROWS = TL + 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sf = reinterpret_cast<R*>(smem_raw);                      // [ROWS][10][32]
+    R* sv = sf + (size_t)ROWS * 10 * 32;                          // [ROWS][4][32]
+    uint8_t* sc = reinterpret_cast<uint8_t*>(sv + (size_t)ROWS * 4 * 32);  // [ROWS][32]
+    const Geo& g = A.g;
+    const int lane = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int nx = g.nx;
+    const int n = DIR == 1 ? g.ny : g.nz;
+    const long long stride = DIR == 1 ? (long long)nx : (long long)nx * g.ny;
+    const int per = g.per[DIR];
+    const int lo = per ? 0 : 1, hi = per ? n : n - 1;
+    const int i = blockIdx.x * 32 + lane;
+    const bool lane_ok = i < nx;
+    const int o = blockIdx.y;
+    const int m0 = lo + blockIdx.z * TL;
+    const long long base = DIR == 1 ? (long long)i + (long long)nx * g.ny * o : (long long)i + (long long)nx * o;
+    const long long N = g.N;
+    const R* Fv = (const R*)A.Fv;
+    // 1. split fluxes, classes and viscous fluxes of the tile rows
+    for (int r = ty; r < ROWS; r += 8) {
+        const int m = m0 - 4 + r;
+        R fp[5], fm[5];
+        uint8_t c = 0;
+        const bool ok = lane_ok && (per || (m >= 0 && m < n));
+        if (ok) {
+            const int mm = per ? wrapi(m, n) : m;
+            const long long nn = base + (long long)mm * stride;
+            const int jj = DIR == 1 ? mm : o;
+            node_split<R>(A, DIR, nn, i, jj, fp, fm);
+            if (A.cls) c = A.cls[nn];
+            if (Fv) {
+#pragma unroll
+                for (int row = 0; row < 4; ++row) sv[(r * 4 + row) * 32 + lane] = Fv[(long long)(4 * DIR + row) * N + nn];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) fp[q] = fm[q] = (R)0;
+            if (Fv) {
+#pragma unroll
+                for (int row = 0; row < 4; ++row) sv[(r * 4 + row) * 32 + lane] = (R)0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            sf[(r * 10 + q) * 32 + lane] = fp[q];
+            sf[(r * 10 + 5 + q) * 32 + lane] = fm[q];
+        }
+        sc[r * 32 + lane] = c;
+    }
+    __syncthreads();
+    // 2. faces (m0-1+f)+1/2, f = 0..TL, from rows f..f+7; kept in registers
+    constexpr int FPT = (TL + 1 + 7) / 8;
+    R fh[FPT][5];
+#pragma unroll
+    for (int t = 0; t < FPT; ++t) {
+        const int f = ty + 8 * t;
+        if (f > TL) break;
+        const int jf = m0 - 1 + f;
+        const bool need = per || (jf >= 0 && jf <= n - 2);
+        if (!need) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) fh[t][q] = (R)0;
+            continue;
+        }
+        int cm = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) cm = max(cm, (int)sc[(f + b) * 32 + lane]);
+        int mp, mmk;
+        const int use = face_use(A.ph, per, n, jf, cm, &mp, &mmk);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            R p8[8], m8[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                p8[b] = sf[((f + b) * 10 + q) * 32 + lane];
+                m8[b] = sf[((f + b) * 10 + 5 + q) * 32 + lane];
+            }
+            fh[t][q] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mp, mmk);
+        }
+    }
+    __syncthreads();
+    R* sh = sf;  // faces reuse the split-flux buffer: [TL+1][5][32]
+#pragma unroll
+    for (int t = 0; t < FPT; ++t) {
+        const int f = ty + 8 * t;
+        if (f > TL) break;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) sh[(f * 5 + q) * 32 + lane] = fh[t][q];
+    }
+    __syncthreads();
+    // 3. difference, viscous divergence and the epilogue
+    if (!lane_ok) return;
+    for (int r = ty; r < TL; r += 8) {
+        const int m = m0 + r;
+        if (m >= hi) break;
+        R val[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) val[q] = -(sh[((r + 1) * 5 + q) * 32 + lane] - sh[(r * 5 + q) * 32 + lane]);
+        if (Fv) {
+            const int rowbase = m0 - 4;  // line position of tile row 0
+#pragma unroll
+            for (int row = 0; row < 4; ++row)
+                val[row + 1] += dcentral_tile<R>(A.ph.vorder, per, n, m,
+                                                 [&](int mm) { return sv[((mm - rowbase) * 4 + row) * 32 + lane]; });
+        }
+        const int mm = per ? wrapi(m, n) : m;
+        const long long nn = base + (long long)mm * stride;
+        const int jj = DIR == 1 ? mm : o, kk = DIR == 1 ? o : mm;
+        epilogue<R, EP>(A, nn, i, jj, kk, val);
+    }
+}
+
+template <class R, int TL>
+constexpr size_t tile_smem_bytes()
+{
+    return (size_t)(TL + 8) * 32 * (10 + 4) * sizeof(R) + (size_t)(TL + 8) * 32;
 }
 
 // ---------------------------------------------------------------------------

@@ -115,6 +115,14 @@ class Solver:
         names = ["prim", "sensor", "visc_flux", "sweep_xi", "sweep_eta", "sweep_zeta"]
         return dict(zip(names, list(ms)))
 
+    def set_sweep_variant(self, dir, kind, param):
+        L.check(L.lib().cfd_set_sweep_variant(self.ctx, dir, kind, param), self.ctx)
+
+    def sweep_variant(self, dir):
+        k, p = C.c_int(), C.c_int()
+        L.check(L.lib().cfd_get_sweep_variant(self.ctx, dir, C.byref(k), C.byref(p)), self.ctx)
+        return k.value, p.value
+
     def launches(self):
         return L.lib().cfd_launch_count(self.ctx)
 

@@ -243,3 +243,30 @@ def test_device_pointers_and_stream(orc):
         c = orc.Case(n, n, n, Re=400.0, Ma=0.5, scheme=0)
         Lo = orc.rhs(c, cases.expand_metrics(_box((n, n, n)), (n, n, n)), U)
         assert field_rel_err(Ld.cpu().numpy(), Lo) <= TOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sweep_variants_bit_identical(orc, precision):
+    """The streaming and tiled eta/zeta sweeps (any segment / tile length)
+    give identical bits; the autotuner only changes speed."""
+    from paper_2209_15333_gb300.solver import Solver
+    sh = (37, 21, 26)
+    bc = dict(bc_lo=(0, 3, 0), bc_hi=(0, 3, 0))   # one non-periodic direction too
+    met = cases.uniform_metrics(*sh)
+    U = turbulence_field(sh, 61)
+    outs = []
+    for kind, param in ((0, 128), (0, 5), (1, 32), (1, 16)):
+        with Solver(sh, met, precision=precision, scheme=3, Re=150.0, theta1=0.004, theta2=0.012, **bc) as s:
+            s.set_state(U)
+            for d in (1, 2):
+                s.set_sweep_variant(d, kind, param)
+            L = s.rhs()
+            s.step(1e-3, 2)
+            outs.append((L, s.get_state()))
+    for L, V in outs[1:]:
+        assert np.array_equal(L, outs[0][0])
+        assert np.array_equal(V, outs[0][1])
+    if precision == 0:
+        c = orc.Case(*sh, Re=150.0, Ma=0.5, scheme=3, theta1=0.004, theta2=0.012, **bc)
+        Lo = orc.rhs(c, cases.expand_metrics(met, sh[::-1]), orc.apply_bc(c, cases.expand_metrics(met, sh[::-1]), U))
+        assert field_rel_err(outs[0][0], Lo) <= TOL
