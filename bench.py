@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="one profiled stage per precision (ncu runs)")
+    ap.add_argument("--variants", default="", help="pin kernel variants, e.g. 0:2,1:1:16,2:1:16 (dir:kind[:param])")
     return ap.parse_args()
 
 
@@ -224,6 +225,9 @@ def run_precision(args, prec, U, met, params, world, local, dt):
     s = Solver((n, n, n), met, stream=stream, precision=1 if prec == "mixed" else 0, **params)
     Ud = torch.tensor(U, device="cuda")
     s.set_state(Ud)
+    for item in filter(None, args.variants.split(",")):
+        f = [int(x) for x in item.split(":")]
+        s.set_sweep_variant(f[0], f[1], f[2] if len(f) > 2 else 0)
     if args.profile_only:
         s.profile_stage(1)
         s.close()
@@ -276,9 +280,10 @@ def run_precision(args, prec, U, met, params, world, local, dt):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
     prof = s.profile_stage(3)
+    variants = {"visc": s.sweep_variant(0), "eta": s.sweep_variant(1), "zeta": s.sweep_variant(2)}
     s.close()
     return dict(value=value, ms=ms, launches=launches, clocks=clk, class_fraction=[float(x) for x in frac],
-                e2e=world * N * 3 * args.steps / e2e_s, prof=prof, U1=U1)
+                e2e=world * N * 3 * args.steps / e2e_s, prof=prof, U1=U1, variants=variants)
 
 
 def roofline(prec, r, N, peaks, fma, src_hash):
@@ -347,7 +352,7 @@ def main():
                                  "frac": alg_b * r["value"] / world / 1e9 / peaks["hbm_gbs"]},
              "err_vs_oracle_1step": field_rel_err(r["U1"], U1o) if U1o is not None else None,
              "class_fraction": r["class_fraction"], "gpu_launches": r["launches"], "clocks": r["clocks"],
-             "e2e": r["e2e"]}
+             "e2e": r["e2e"], "kernel_variants": r["variants"]}
         if p == "fp64":
             d["fp64_alu_frac_whole_step"] = sum(FP64_FLOPS.values()) * r["value"] / world / 1e12 / fma["fp64"]
         return d
@@ -370,6 +375,7 @@ def main():
         "hbm_algorithmic": dict(h["hbm_algorithmic"], peak_gbs=peaks["hbm_gbs"], peak_source=peak_kind),
         "err_vs_oracle_1step": h["err_vs_oracle_1step"],
         "class_fraction": h["class_fraction"],
+        "kernel_variants": h["kernel_variants"],
         "fma_peak_tflops": fma,
         "kernel_src": src_hash,
         "cpu_baseline": cpu,

@@ -209,7 +209,10 @@ cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const
    parallelism; best when latency binds).  By default the context times all
    four on its first cfd_rhs / cfd_step and keeps the fastest (cached per
    process by precision, grid and scheme); cfd_set_sweep_variant fixes one
-   and turns the tuning off. */
+   and turns the tuning off.  dir 0 selects the viscous node-flux kernel the
+   same way: kind 0 one thread per node reading its neighbours, kind 1 / 2 a
+   32 x 8 tile streaming along zeta in segments of 64 / 32 planes with a
+   9-plane shared ring (param ignored). */
 cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param);
 cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param);
 

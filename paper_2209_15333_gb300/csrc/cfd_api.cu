@@ -46,6 +46,7 @@ struct cfd_ctx {
     float* metf = nullptr;          // [31][M] float mirror
     int sweep_kind[3] = {0, 0, 0};  // eta/zeta: 0 streaming, 1 tile (chosen by the autotuner)
     int sweep_param[3] = {0, 128, 128};
+    int visc_kind = 0;              // 0 node-parallel, 1 2.5-D TZ 64, 2 2.5-D TZ 32 (autotuned)
     bool tuned = false;
     int* err = nullptr;             // device non-physical flag
     double* dt = nullptr;           // device scalars
@@ -271,6 +272,10 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     CU((set_sweep_attrs<float, 1, EP_ACCUM>()));
     CU((set_sweep_attrs<float, 2, EP_FINAL_RHS>()));
     CU((set_sweep_attrs<float, 2, EP_FINAL_RK>()));
+    CU(cudaFuncSetAttribute(k_visc_flux25<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)visc25_smem_bytes<float>()));
+    CU(cudaFuncSetAttribute(k_visc_flux25<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)visc25_smem_bytes<float>()));
+    CU(cudaFuncSetAttribute(k_visc_flux25<double, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)visc25_smem_bytes<double>()));
+    CU(cudaFuncSetAttribute(k_visc_flux25<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)visc25_smem_bytes<double>()));
     if (p.precision == CFD_FP32_BULK) CU(cudaMemsetAsync(ctx->b.cls, 2, N, ctx->stream));
     ctx->bx = g.nx <= 32 ? 32 : (g.nx <= 64 ? 64 : 128);
     CU(cudaStreamSynchronize(ctx->stream));
@@ -330,6 +335,27 @@ static cfd_status launch_bc(cfd_ctx* ctx, double* U, double tfrac, bool use_dt)
                                                                   use_dt ? ctx->dt : nullptr, tfrac);
         LAUNCH_CHECK();
     }
+    return CFD_OK;
+}
+
+template <class R>
+static cfd_status launch_visc(cfd_ctx* ctx, int kind)
+{
+    const Geo& g = ctx->g;
+    if (kind == 0) {
+        const NodeLaunch nl = node_launch(g);
+        k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P, (R*)ctx->b.Fv);
+    } else {
+        const int tz = kind == 1 ? 64 : 32;
+        dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + tz - 1) / tz);
+        if (kind == 1)
+            k_visc_flux25<R, 64><<<grid, 256, visc25_smem_bytes<R>(), ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P,
+                                                                                   (R*)ctx->b.Fv);
+        else
+            k_visc_flux25<R, 32><<<grid, 256, visc25_smem_bytes<R>(), ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P,
+                                                                                   (R*)ctx->b.Fv);
+    }
+    LAUNCH_CHECK();
     return CFD_OK;
 }
 
@@ -440,8 +466,8 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
     }
     if (ev) cudaEventRecord(ev[2], ctx->stream);
     if (ctx->ph.viscous) {
-        k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P, (R*)ctx->b.Fv);
-        LAUNCH_CHECK();
+        cfd_status st = launch_visc<R>(ctx, ctx->visc_kind);
+        if (st != CFD_OK) return st;
     }
     SweepArgs A = make_args(ctx, Uin, Un, Uout, Lout, a, b);
     if (ev) cudaEventRecord(ev[3], ctx->stream);
@@ -510,6 +536,23 @@ static cfd_status autotune_t(cfd_ctx* ctx)
             }
         }
     }
+    if (ctx->ph.viscous) {
+        float best = 1e30f;
+        for (int kind = 0; kind < 3 && st == CFD_OK; ++kind) {
+            for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, ctx->stream);
+                st = launch_visc<R>(ctx, kind);
+            }
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, CFD_ECUDA, "autotune timing");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == CFD_OK && ms < best) {
+                best = ms;
+                ctx->visc_kind = kind;
+            }
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
@@ -527,6 +570,7 @@ static cfd_status autotune(cfd_ctx* ctx)
                     ctx->sweep_kind[d] = kv.second[2 * d - 2];
                     ctx->sweep_param[d] = kv.second[2 * d - 1];
                 }
+                ctx->visc_kind = kv.second[4];
                 ctx->tuned = true;
                 return CFD_OK;
             }
@@ -536,14 +580,22 @@ static cfd_status autotune(cfd_ctx* ctx)
     ctx->tuned = true;
     ctx->graph_valid = false;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache.push_back({key, {ctx->sweep_kind[1], ctx->sweep_param[1], ctx->sweep_kind[2], ctx->sweep_param[2]}});
+    g_tune_cache.push_back(
+        {key, {ctx->sweep_kind[1], ctx->sweep_param[1], ctx->sweep_kind[2], ctx->sweep_param[2], ctx->visc_kind}});
     return CFD_OK;
 }
 
 extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param)
 {
     if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
-    if (dir < 1 || dir > 2 || kind < 0 || kind > 1) return fail(ctx, CFD_EINVAL, "dir must be 1 or 2, kind 0 or 1");
+    if (dir == 0) {
+        if (kind < 0 || kind > 2) return fail(ctx, CFD_EINVAL, "viscous kernel kind must be 0, 1 or 2");
+        ctx->visc_kind = kind;
+        ctx->tuned = true;
+        ctx->graph_valid = false;
+        return CFD_OK;
+    }
+    if (dir < 1 || dir > 2 || kind < 0 || kind > 1) return fail(ctx, CFD_EINVAL, "dir must be 0, 1 or 2");
     if (kind == 1 && param != 16 && param != 32) return fail(ctx, CFD_EINVAL, "tile length must be 16 or 32");
     if (kind == 0 && (param < 1 || param > 65535)) return fail(ctx, CFD_EINVAL, "segment length out of range");
     ctx->sweep_kind[dir] = kind;
@@ -555,7 +607,12 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
 
 extern "C" cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param)
 {
-    if (!ctx || !kind || !param || dir < 1 || dir > 2) return fail(ctx, CFD_EINVAL, "bad argument");
+    if (!ctx || !kind || !param || dir < 0 || dir > 2) return fail(ctx, CFD_EINVAL, "bad argument");
+    if (dir == 0) {
+        *kind = ctx->visc_kind;
+        *param = ctx->visc_kind == 1 ? 64 : (ctx->visc_kind == 2 ? 32 : 0);
+        return CFD_OK;
+    }
     *kind = ctx->sweep_kind[dir];
     *param = ctx->sweep_param[dir];
     return CFD_OK;

@@ -596,6 +596,114 @@ __global__ void __launch_bounds__(256) k_visc_flux(Geo g, Phys ph, const R* __re
     }
 }
 
+// Viscous node fluxes, 2.5-D form: a CTA owns 32 x 8 nodes of an (x, y) tile
+// and walks along zeta over a segment of TZ planes.  Each plane of u, v, w, T
+// with a 4-node x/y halo is staged once in a 9-plane shared ring; the x and y
+// derivatives of the centre plane and the zeta derivatives all come from
+// shared memory, so every value is read from L2/HBM about 2.5 times instead of
+// once per stencil use.  Same operations, in the same order, as k_visc_flux.
+template <class R>
+__device__ __forceinline__ void visc_node_flux(const Geo& g, const Phys& ph, long long n, int i, int j, const R dq[4][3],
+                                               R T, R u, R v, R w, R* __restrict__ Fv)
+{
+    const long long N = g.N;
+    const long long mi = midx(g, i, j, n);
+    R mraw[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) mraw[e] = metr<R>(g, M_RAW + e, mi);
+    R gr[4][3];
+#pragma unroll
+    for (int var = 0; var < 4; ++var)
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+            gr[var][x] = mraw[x] * dq[var][0] + mraw[3 + x] * dq[var][1] + mraw[6 + x] * dq[var][2];
+    R mu = viscosity(ph, T);
+    R mr = mu * pk<R>(ph.invRe, ph.invRef);
+    R div = gr[0][0] + gr[1][1] + gr[2][2];
+    R tau[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? ((R)(2.0 / 3.0)) * div : (R)0));
+    R kc = mu * pk<R>(ph.kcoef, ph.kcoeff);
+    R Th[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Th[a] = u * tau[a][0] + v * tau[a][1] + w * tau[a][2] + kc * gr[3][a];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        R a0 = metr<R>(g, M_ALPHA + 3 * d, mi), a1 = metr<R>(g, M_ALPHA + 3 * d + 1, mi),
+          a2 = metr<R>(g, M_ALPHA + 3 * d + 2, mi);
+#pragma unroll
+        for (int row = 0; row < 3; ++row)
+            Fv[(long long)(4 * d + row) * N + n] = a0 * tau[0][row] + a1 * tau[1][row] + a2 * tau[2][row];
+        Fv[(long long)(4 * d + 3) * N + n] = a0 * Th[0] + a1 * Th[1] + a2 * Th[2];
+    }
+}
+
+template <class R>
+constexpr size_t visc25_smem_bytes()
+{
+    return (size_t)9 * 4 * 16 * 40 * sizeof(R);
+}
+
+template <class R, int TZ>
+__global__ void __launch_bounds__(256) k_visc_flux25(Geo g, Phys ph, const R* __restrict__ P, R* __restrict__ Fv)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* ring = reinterpret_cast<R*>(smem_raw);  // [9][4][16][40]
+    constexpr int PL = 4 * 16 * 40;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long N = g.N;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+    const int zlo = blockIdx.z * TZ, zhi = min(zlo + TZ, nz);
+    const int i = x0 + tx, j = y0 + ty;
+    const bool own = i < nx && j < ny;
+    const int ord = ph.vorder;
+    const R* fld[4] = {P + N, P + 2 * N, P + 3 * N, P + 5 * N};
+    for (int z = zlo - 4; z < zhi + 4; ++z) {
+        // stage plane z (with its x/y halo) into ring slot z mod 9
+        const int slot = ((z % 9) + 9) % 9;
+        R* pl = ring + (size_t)slot * PL;
+        const bool zin = g.per[2] || (z >= 0 && z < nz);
+        const int zz = g.per[2] ? wrapi(z, nz) : z;
+        for (int t = threadIdx.x; t < 16 * 40; t += 256) {
+            const int hy = t / 40, hx = t - hy * 40;
+            int gx = x0 - 4 + hx, gy = y0 - 4 + hy;
+            bool ok = zin;
+            if (g.per[0]) gx = wrapi(gx, nx);
+            else ok = ok && gx >= 0 && gx < nx;
+            if (g.per[1]) gy = wrapi(gy, ny);
+            else ok = ok && gy >= 0 && gy < ny;
+            const long long nn = ok ? (long long)gx + (long long)nx * ((long long)gy + (long long)ny * zz) : 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) pl[f * 640 + t] = ok ? __ldg(fld[f] + nn) : (R)0;
+        }
+        __syncthreads();
+        const int zc = z - 4;  // output plane: its +-4 neighbours are all staged now
+        if (zc >= zlo && own) {
+            const R* c = ring + (size_t)(((zc % 9) + 9) % 9) * PL;
+            const int hx = tx + 4, hy = ty + 4;
+            R dq[4][3];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const R* cf = c + f * 640;
+                dq[f][0] = dcentral_tile<R>(ord, g.per[0], nx, i, [&](int mm) { return cf[hy * 40 + hx + (mm - i)]; });
+                dq[f][1] = dcentral_tile<R>(ord, g.per[1], ny, j, [&](int mm) { return cf[(hy + (mm - j)) * 40 + hx]; });
+                dq[f][2] = dcentral_tile<R>(ord, g.per[2], nz, zc, [&](int mm) {
+                    return ring[(size_t)(((mm % 9) + 9) % 9) * PL + f * 640 + hy * 40 + hx];
+                });
+            }
+            const long long n = (long long)i + (long long)nx * ((long long)j + (long long)ny * zc);
+            const R* cu = c;
+            visc_node_flux<R>(g, ph, n, i, j, dq, P[5 * N + n], cu[hy * 40 + hx], cu[640 + hy * 40 + hx],
+                              cu[1280 + hy * 40 + hx], Fv);
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the directional sweeps
 // ---------------------------------------------------------------------------
@@ -682,10 +790,10 @@ __device__ __forceinline__ void node_split(const SweepArgs& A, int d, long long 
 template <class R, int BX, int EP>
 __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
 {
-    __shared__ R sf[10][BX + 8];
+    __shared__ __align__(16) R sf[10][BX + 12];  // rows padded so a 12-value window never leaves a row
     __shared__ R sh[5][BX + 1];
     __shared__ R sv[4][BX + 8];
-    __shared__ uint8_t sc[BX + 8];
+    __shared__ uint8_t sc[BX + 12];
     const Geo& g = A.g;
     const int n = g.nx;
     const int per = g.per[0];
@@ -722,26 +830,50 @@ __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
         }
         sc[s] = c;
     }
+    if (t < 4) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) sf[q][BX + 8 + t] = (R)0;
+        sc[BX + 8 + t] = 0;
+    }
     __syncthreads();
-    // faces: thread t -> face (i0+t)+1/2 stored at sh[.][t+1]; face (i0-1)+1/2 at sh[.][0]
-    for (int f = t; f < BX + 1; f += BX) {
-        int slot = f == BX ? 0 : f + 1;
-        int jf = i0 - 1 + slot;  // face jf + 1/2
-        int s0 = slot;           // smem index of node jf-3
-        bool need = per ? true : (jf >= 0 && jf <= n - 2);
-        if (!need || jf - (i0 - 1) > min(BX, (per ? n : n - 1) - i0)) continue;
-        int cm = 0;
+    // faces: slot f <-> face (i0-1+f)+1/2 (stencil rows f..f+7), f = 0..BX.
+    // A job is 4 consecutive faces of one component, computed from one
+    // 12-value window per side (vector shared-memory loads).
+    constexpr int NG = (BX + 1 + 3) / 4;
+    const int flim = min(BX, (per ? n : n - 1) - i0);  // last slot needed
+    for (int job = t; job < 5 * NG; job += BX) {
+        const int q = job / NG, f0 = 4 * (job - q * NG);
+        if (f0 > flim) continue;
+        R pv[12], mv[12];
 #pragma unroll
-        for (int o = 0; o < 8; ++o) cm = max(cm, (int)sc[s0 + o]);
-        int mp, mm;
-        int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+        for (int b = 0; b < 12; b += 16 / (int)sizeof(R)) {
+            if constexpr (sizeof(R) == 4) {
+                const float4 a = *reinterpret_cast<const float4*>(&sf[q][f0 + b]);
+                const float4 c = *reinterpret_cast<const float4*>(&sf[5 + q][f0 + b]);
+                pv[b] = (R)a.x; pv[b + 1] = (R)a.y; pv[b + 2] = (R)a.z; pv[b + 3] = (R)a.w;
+                mv[b] = (R)c.x; mv[b + 1] = (R)c.y; mv[b + 2] = (R)c.z; mv[b + 3] = (R)c.w;
+            } else {
+                const double2 a = *reinterpret_cast<const double2*>(&sf[q][f0 + b]);
+                const double2 c = *reinterpret_cast<const double2*>(&sf[5 + q][f0 + b]);
+                pv[b] = (R)a.x; pv[b + 1] = (R)a.y;
+                mv[b] = (R)c.x; mv[b + 1] = (R)c.y;
+            }
+        }
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
+        for (int u = 0; u < 4; ++u) {
+            const int slot = f0 + u;
+            const int jf = i0 - 1 + slot;
+            if (slot > flim || (!per && jf < 0)) continue;
+            int cm = 0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) cm = max(cm, (int)sc[slot + o]);
+            int mp, mm;
+            const int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
             R p8[8], m8[8];
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
-                p8[o] = sf[q][s0 + o];
-                m8[o] = sf[5 + q][s0 + o];
+                p8[o] = pv[u + o];
+                m8[o] = mv[u + o];
             }
             sh[q][slot] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mp, mm);
         }
@@ -925,44 +1057,57 @@ __global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A)
         sc[r * 32 + lane] = c;
     }
     __syncthreads();
-    // 2. faces (m0-1+f)+1/2, f = 0..TL, from rows f..f+7; kept in registers
+    // 2. faces (m0-1+f)+1/2, f = 0..TL, from rows f..f+7.  Thread row ty
+    //    owns FPT consecutive faces and reads their FPT+7 rows once per
+    //    component; results stay in registers until the buffer is reused.
     constexpr int FPT = (TL + 1 + 7) / 8;
+    constexpr int WIN = FPT + 7;
+    const int fbase = ty * FPT;
     R fh[FPT][5];
+    int usev[FPT], mpv[FPT], mmv[FPT];
 #pragma unroll
-    for (int t = 0; t < FPT; ++t) {
-        const int f = ty + 8 * t;
-        if (f > TL) break;
+    for (int u = 0; u < FPT; ++u) {
+        const int f = fbase + u;
         const int jf = m0 - 1 + f;
-        const bool need = per || (jf >= 0 && jf <= n - 2);
-        if (!need) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) fh[t][q] = (R)0;
-            continue;
-        }
+        usev[u] = -1;
+        if (f > TL || !(per || (jf >= 0 && jf <= n - 2))) continue;
         int cm = 0;
 #pragma unroll
         for (int b = 0; b < 8; ++b) cm = max(cm, (int)sc[(f + b) * 32 + lane]);
-        int mp, mmk;
-        const int use = face_use(A.ph, per, n, jf, cm, &mp, &mmk);
+        usev[u] = face_use(A.ph, per, n, jf, cm, &mpv[u], &mmv[u]);
+    }
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < 5; ++q) {
+        R pv[WIN], mv[WIN];
+#pragma unroll
+        for (int b = 0; b < WIN; ++b) {
+            const int r = min(fbase + b, ROWS - 1);
+            pv[b] = sf[(r * 10 + q) * 32 + lane];
+            mv[b] = sf[(r * 10 + 5 + q) * 32 + lane];
+        }
+#pragma unroll
+        for (int u = 0; u < FPT; ++u) {
+            if (usev[u] < 0) {
+                fh[u][q] = (R)0;
+                continue;
+            }
             R p8[8], m8[8];
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
-                p8[b] = sf[((f + b) * 10 + q) * 32 + lane];
-                m8[b] = sf[((f + b) * 10 + 5 + q) * 32 + lane];
+                p8[b] = pv[u + b];
+                m8[b] = mv[u + b];
             }
-            fh[t][q] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mp, mmk);
+            fh[u][q] = face_flux<R>(usev[u], p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mpv[u], mmv[u]);
         }
     }
     __syncthreads();
     R* sh = sf;  // faces reuse the split-flux buffer: [TL+1][5][32]
 #pragma unroll
-    for (int t = 0; t < FPT; ++t) {
-        const int f = ty + 8 * t;
+    for (int u = 0; u < FPT; ++u) {
+        const int f = fbase + u;
         if (f > TL) break;
 #pragma unroll
-        for (int q = 0; q < 5; ++q) sh[(f * 5 + q) * 32 + lane] = fh[t][q];
+        for (int q = 0; q < 5; ++q) sh[(f * 5 + q) * 32 + lane] = fh[u][q];
     }
     __syncthreads();
     // 3. difference, viscous divergence and the epilogue
