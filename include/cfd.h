@@ -104,6 +104,22 @@ void cfd_default_params(cfd_params* p);
 cfd_status cfd_create(cfd_ctx** out, const cfd_grid* grid, const double* metrics,
                       int metrics_on_device, const cfd_params* params, void* stream);
 
+/*
+ * Ensemble of nblocks independent blocks of uneven sizes (grids[b],
+ * metrics[b], params[b] for b < nblocks; every block may have its own gas
+ * parameters, e.g. Ma and Re, but all share precision, scheme, viscous or
+ * inviscid, visc_order and sensor).  cfd_step advances every block with one
+ * persistent launch per kernel kind and stage (CTAs walk a work list of the
+ * tiles of all blocks), captured with the boundary conditions as one CUDA
+ * graph per RK3 step.  Per-block calls (cfd_set_state, cfd_get_state,
+ * cfd_rhs, cfd_cfl_dt, cfd_get_flags) take the block index.  Not a step of
+ * the paper itself: the single-GPU form of running many blocks at once.
+ * Errors as cfd_create; CFD_EINVAL if the blocks disagree on shared settings.
+ */
+cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_grid* grids,
+                            const double* const* metrics, int metrics_on_device,
+                            const cfd_params* params, void* stream);
+
 /* Inflow profile for CFD_BC_INFLOW on the xi-low face: prim[5][ny] =
    rho, u, v, w, p per eta index, the same for every zeta (host memory). */
 cfd_status cfd_set_inflow(cfd_ctx* ctx, const double* prim);

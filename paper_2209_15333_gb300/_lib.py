@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "CFD_OK", -1: "CFD_EINVAL", -2: "CFD_ENOMEM", -3: "CFD_ECUDA"
                 -5: "CFD_ETIMEOUT", -6: "CFD_EUNSUPPORTED"}
 
 # every entry point declared in include/cfd.h
-EXPORTS = ["cfd_default_params", "cfd_create", "cfd_set_inflow", "cfd_set_blowing", "cfd_set_state",
+EXPORTS = ["cfd_default_params", "cfd_create", "cfd_create_batch", "cfd_set_inflow", "cfd_set_blowing", "cfd_set_state",
            "cfd_get_state", "cfd_rhs", "cfd_step", "cfd_cfl_dt", "cfd_get_flags", "cfd_force_flags",
            "cfd_get_time", "cfd_set_time", "cfd_sync", "cfd_last_error", "cfd_launch_count", "cfd_fma_peak",
            "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
@@ -63,6 +63,8 @@ def lib():
         L.cfd_default_params.argtypes = [C.POINTER(CfdParams)]
         L.cfd_default_params.restype = None
         L.cfd_create.argtypes = [C.POINTER(vp), C.POINTER(CfdGrid), vp, C.c_int, C.POINTER(CfdParams), vp]
+        L.cfd_create_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(CfdGrid), C.POINTER(vp), C.c_int,
+                                       C.POINTER(CfdParams), vp]
         L.cfd_set_inflow.argtypes = [vp, vp]
         L.cfd_set_blowing.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
                                       C.c_double, vp, vp]

@@ -28,6 +28,7 @@ struct Bufs {
     void* Fv = nullptr;       // [12][N] viscous fluxes
     void* R = nullptr;        // [5][N] accumulator
     uint8_t* cls = nullptr;   // [N]
+    uint8_t* cls_tune = nullptr;  // [N] class buffer of the autotuner's trial runs
 };
 
 }  // namespace
@@ -48,6 +49,13 @@ struct cfd_ctx {
     int sweep_param[3] = {0, 128, 128};
     int visc_kind = 0;              // 0 node-parallel, 1 2.5-D TZ 64, 2 2.5-D TZ 32 (autotuned)
     bool tuned = false;
+    // ensemble of blocks (cfd_create_batch): one single-block context per block
+    // plus the tables that drive one persistent launch per kernel kind
+    std::vector<cfd_ctx*> sub;
+    SweepArgs* d_tbl[3] = {nullptr, nullptr, nullptr};  // per stage, [nb]
+    int* d_maps = nullptr;                              // all prefix / gdim arrays
+    BatchMap maps[3][5];                                // [stage][kind]
+    int map_grid[5] = {0, 0, 0, 0, 0};                  // persistent grid per kind
     int* err = nullptr;             // device non-physical flag
     double* dt = nullptr;           // device scalars
     double* t = nullptr;
@@ -183,8 +191,16 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
 
 static void free_all(cfd_ctx* c)
 {
+    for (cfd_ctx* b : c->sub) {
+        free_all(b);
+        delete b;
+    }
+    c->sub.clear();
+    for (int s = 0; s < 3; ++s)
+        if (c->d_tbl[s]) cudaFree(c->d_tbl[s]);
+    if (c->d_maps) cudaFree(c->d_maps);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void* ptrs[] = {c->b.U, c->b.Uk, c->b.P, c->b.Fv, c->b.R, c->b.cls, c->met, c->metf, c->err, c->dt, c->t,
+    void* ptrs[] = {c->b.U, c->b.Uk, c->b.P, c->b.Fv, c->b.R, c->b.cls, c->b.cls_tune, c->met, c->metf, c->err, c->dt, c->t,
                     c->cflmax, c->inflow, c->wall_x, c->wall_z};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -247,6 +263,7 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     CU(cudaMalloc(&ctx->b.R, 5 * N * rs));
     CU(cudaMalloc(&ctx->b.cls, N));
     CU(cudaMemsetAsync(ctx->b.cls, 0, N, ctx->stream));
+    CU(cudaMalloc(&ctx->b.cls_tune, N));
     if (ph.viscous) CU(cudaMalloc(&ctx->b.Fv, 12 * N * rs));
     CU(cudaMalloc(&ctx->met, (size_t)M_COUNT * g.M * sizeof(double)));
     CU(cudaMalloc(&ctx->err, sizeof(int)));
@@ -318,9 +335,24 @@ extern "C" long long cfd_launch_count(const cfd_ctx* ctx) { return ctx ? ctx->la
 static cfd_status check_block(cfd_ctx* ctx, int block)
 {
     if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
-    if (block != 0) return fail(ctx, CFD_EINVAL, "block index out of range");
+    const int nb = ctx->sub.empty() ? 1 : (int)ctx->sub.size();
+    if (block < 0 || block >= nb) return fail(ctx, CFD_EINVAL, "block index out of range");
     return CFD_OK;
 }
+
+// the context that holds block `block` (itself for single-block contexts)
+static cfd_ctx* blk(cfd_ctx* ctx, int block) { return ctx->sub.empty() ? ctx : ctx->sub[block]; }
+
+// run a per-block call on the block's context and copy its error message up
+#define DELEGATE(call_on_sub)                                                                         \
+    do {                                                                                              \
+        if (!ctx->sub.empty()) {                                                                      \
+            cfd_ctx* b_ = ctx->sub[block];                                                            \
+            cfd_status s_ = call_on_sub;                                                              \
+            if (s_ != CFD_OK) ctx->msg = b_->msg;                                                     \
+            return s_;                                                                                \
+        }                                                                                             \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // launches
@@ -339,21 +371,19 @@ static cfd_status launch_bc(cfd_ctx* ctx, double* U, double tfrac, bool use_dt)
 }
 
 template <class R>
-static cfd_status launch_visc(cfd_ctx* ctx, int kind)
+static cfd_status launch_visc(cfd_ctx* ctx, const SweepArgs& A, int kind)
 {
     const Geo& g = ctx->g;
     if (kind == 0) {
         const NodeLaunch nl = node_launch(g);
-        k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P, (R*)ctx->b.Fv);
+        k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
     } else {
         const int tz = kind == 1 ? 64 : 32;
         dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + tz - 1) / tz);
         if (kind == 1)
-            k_visc_flux25<R, 64><<<grid, 256, visc25_smem_bytes<R>(), ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P,
-                                                                                   (R*)ctx->b.Fv);
+            k_visc_flux25<R, 64><<<grid, 256, visc25_smem_bytes<R>(), ctx->stream>>>(A);
         else
-            k_visc_flux25<R, 32><<<grid, 256, visc25_smem_bytes<R>(), ctx->stream>>>(g, ctx->ph, (const R*)ctx->b.P,
-                                                                                   (R*)ctx->b.Fv);
+            k_visc_flux25<R, 32><<<grid, 256, visc25_smem_bytes<R>(), ctx->stream>>>(A);
     }
     LAUNCH_CHECK();
     return CFD_OK;
@@ -428,8 +458,10 @@ static SweepArgs make_args(cfd_ctx* ctx, const double* Uin, const double* Un, do
     A.ph = ctx->ph;
     A.P = ctx->b.P;
     A.cls = ctx->prm.scheme == CFD_HYBRID ? ctx->b.cls : nullptr;
+    A.cls_io = ctx->b.cls;
     A.Fv = ctx->ph.viscous ? ctx->b.Fv : nullptr;
     A.R = ctx->b.R;
+    A.err = ctx->err;
     A.U = Uin;
     A.Un = Un;
     A.Uout = Uout;
@@ -447,29 +479,28 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
                               double a, double b, cudaEvent_t* ev)
 {
     const Geo& g = ctx->g;
-    const long long N = g.N;
     const bool mixed = sizeof(R) == sizeof(float);
+    SweepArgs A = make_args(ctx, Uin, Un, Uout, Lout, a, b);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
     const NodeLaunch nl = node_launch(g);
     if (mixed)
-        k_prim_mixed<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, Uin, (float*)ctx->b.P, ctx->b.cls, ctx->err);
+        k_prim_mixed<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
     else
-        k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, Uin, (double*)ctx->b.P, ctx->err);
+        k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
     LAUNCH_CHECK();
     if (ev) cudaEventRecord(ev[1], ctx->stream);
     if (!ctx->forced && (mixed || ctx->prm.scheme == CFD_HYBRID)) {
         if (mixed)
-            k_sensor32<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const float*)ctx->b.P + 4 * N, ctx->b.cls);
+            k_sensor32<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
         else
-            k_sensor<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, (const double*)ctx->b.P + 4 * N, ctx->b.cls);
+            k_sensor<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
         LAUNCH_CHECK();
     }
     if (ev) cudaEventRecord(ev[2], ctx->stream);
     if (ctx->ph.viscous) {
-        cfd_status st = launch_visc<R>(ctx, ctx->visc_kind);
+        cfd_status st = launch_visc<R>(ctx, A, ctx->visc_kind);
         if (st != CFD_OK) return st;
     }
-    SweepArgs A = make_args(ctx, Uin, Un, Uout, Lout, a, b);
     if (ev) cudaEventRecord(ev[3], ctx->stream);
     return launch_sweeps<R, EPF>(ctx, A, ev ? ev + 3 : nullptr);
 }
@@ -541,7 +572,7 @@ static cfd_status autotune_t(cfd_ctx* ctx)
         for (int kind = 0; kind < 3 && st == CFD_OK; ++kind) {
             for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, ctx->stream);
-                st = launch_visc<R>(ctx, kind);
+                st = launch_visc<R>(ctx, A, kind);
             }
             cudaEventRecord(e1, ctx->stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, CFD_ECUDA, "autotune timing");
@@ -575,7 +606,12 @@ static cfd_status autotune(cfd_ctx* ctx)
                 return CFD_OK;
             }
     }
+    // trial runs work on a copy of the classes: the sensor they run must not
+    // change what the next real evaluation sees (the mixed recovery reads it)
+    CU(cudaMemcpyAsync(ctx->b.cls_tune, ctx->b.cls, ctx->g.N, cudaMemcpyDeviceToDevice, ctx->stream));
+    std::swap(ctx->b.cls, ctx->b.cls_tune);
     cfd_status st = ctx->prm.precision == CFD_FP32_BULK ? autotune_t<float>(ctx) : autotune_t<double>(ctx);
+    std::swap(ctx->b.cls, ctx->b.cls_tune);
     if (st != CFD_OK) return st;
     ctx->tuned = true;
     ctx->graph_valid = false;
@@ -637,6 +673,7 @@ static cfd_status read_err(cfd_ctx* ctx)
 extern "C" cfd_status cfd_set_inflow(cfd_ctx* ctx, const double* prim)
 {
     if (!ctx || !prim) return fail(ctx, CFD_EINVAL, "null argument");
+    if (!ctx->sub.empty()) return fail(ctx, CFD_EUNSUPPORTED, "inflow profiles are per single-block context");
     const int ny = ctx->g.ny;
     if (!ctx->inflow) CU(cudaMalloc(&ctx->inflow, 5 * ny * sizeof(double)));
     CU(cudaMemcpyAsync(ctx->inflow, prim, 5 * ny * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
@@ -650,6 +687,7 @@ extern "C" cfd_status cfd_set_blowing(cfd_ctx* ctx, double amp, double x0, doubl
                                       const double* wall_x, const double* wall_z)
 {
     if (!ctx || !wall_x || !wall_z) return fail(ctx, CFD_EINVAL, "null argument");
+    if (!ctx->sub.empty()) return fail(ctx, CFD_EUNSUPPORTED, "blowing is per single-block context");
     if (!(x1 > x0) || !(Lz > 0.0)) return fail(ctx, CFD_EINVAL, "blowing strip needs x1 > x0 and Lz > 0");
     if (!ctx->wall_x) CU(cudaMalloc(&ctx->wall_x, ctx->g.nx * sizeof(double)));
     if (!ctx->wall_z) CU(cudaMalloc(&ctx->wall_z, ctx->g.nz * sizeof(double)));
@@ -673,6 +711,7 @@ extern "C" cfd_status cfd_set_state(cfd_ctx* ctx, int block, const double* U, in
 {
     cfd_status st = check_block(ctx, block);
     if (st != CFD_OK) return st;
+    DELEGATE(cfd_set_state(b_, 0, U, on_device));
     if (!U) return fail(ctx, CFD_EINVAL, "null state");
     const long long N = ctx->g.N;
     CU(cudaMemcpyAsync(ctx->b.U, U, 5 * N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -688,6 +727,7 @@ extern "C" cfd_status cfd_get_state(cfd_ctx* ctx, int block, double* U, int on_d
 {
     cfd_status st = check_block(ctx, block);
     if (st != CFD_OK) return st;
+    DELEGATE(cfd_get_state(b_, 0, U, on_device));
     if (!U) return fail(ctx, CFD_EINVAL, "null output");
     const long long N = ctx->g.N;
     CU(cudaMemcpyAsync(U, ctx->b.U, 5 * N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -699,6 +739,7 @@ extern "C" cfd_status cfd_rhs(cfd_ctx* ctx, int block, double* dUdt, int on_devi
 {
     cfd_status st = check_block(ctx, block);
     if (st != CFD_OK) return st;
+    DELEGATE(cfd_rhs(b_, 0, dUdt, on_device));
     if (!dUdt) return fail(ctx, CFD_EINVAL, "null output");
     const long long N = ctx->g.N;
     st = autotune(ctx);
@@ -711,8 +752,239 @@ extern "C" cfd_status cfd_rhs(cfd_ctx* ctx, int block, double* dUdt, int on_devi
     return read_err(ctx);
 }
 
+
+// ---------------------------------------------------------------------------
+// ensembles of uneven blocks (cfd_create_batch): persistent batched launches
+// ---------------------------------------------------------------------------
+enum { MK_NODE = 0, MK_VISC = 1, MK_SX = 2, MK_T1 = 3, MK_T2 = 4, MK_COUNT = 5 };
+constexpr int kBatchBX = 64, kBatchTL = 16, kBatchTZ = 32;
+
+static void batch_tiles(const Geo& g, int kind, int out[3])
+{
+    auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
+    auto span = [&](int d) {
+        const int n = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+        return g.per[d] ? n : n - 2;
+    };
+    switch (kind) {
+    case MK_NODE: out[0] = cdiv(g.nx, 128); out[1] = g.ny; out[2] = g.nz; break;
+    case MK_VISC: out[0] = cdiv(g.nx, 32); out[1] = cdiv(g.ny, 8); out[2] = cdiv(g.nz, kBatchTZ); break;
+    case MK_SX: out[0] = cdiv(span(0), kBatchBX); out[1] = g.ny; out[2] = g.nz; break;
+    case MK_T1: out[0] = cdiv(g.nx, 32); out[1] = g.nz; out[2] = cdiv(span(1), kBatchTL); break;
+    default: out[0] = cdiv(g.nx, 32); out[1] = g.ny; out[2] = cdiv(span(2), kBatchTL); break;
+    }
+}
+
+template <class R>
+static cudaError_t batch_kernel_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(kb_visc_flux25<R, kBatchTZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)visc25_smem_bytes<R>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, kBatchTL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<R, kBatchTL>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<R, kBatchTL>());
+    return e;
+}
+
+// persistent grid: every SM filled to its occupancy, never more CTAs than items
+template <class K>
+static int persistent_grid(K kernel, int threads, size_t smem, int items)
+{
+    int per_sm = 1, dev = 0, sms = kSMs;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    return std::max(1, std::min(items, std::max(1, per_sm) * sms));
+}
+
+template <class R>
+static void batch_grids(cfd_ctx* ctx, const int totals[MK_COUNT])
+{
+    const bool mixed = sizeof(R) == sizeof(float);
+    ctx->map_grid[MK_NODE] = mixed ? persistent_grid(kb_prim_mixed, 128, 0, totals[MK_NODE])
+                                   : persistent_grid(kb_prim<double>, 128, 0, totals[MK_NODE]);
+    ctx->map_grid[MK_VISC] = persistent_grid(kb_visc_flux25<R, kBatchTZ>, 256, visc25_smem_bytes<R>(), totals[MK_VISC]);
+    ctx->map_grid[MK_SX] = persistent_grid(kb_sweep_x<R, kBatchBX, EP_STORE>, kBatchBX, 0, totals[MK_SX]);
+    ctx->map_grid[MK_T1] = persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, kBatchTL>, 256, tile_smem_bytes<R, kBatchTL>(),
+                                           totals[MK_T1]);
+    ctx->map_grid[MK_T2] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL>, 256,
+                                           tile_smem_bytes<R, kBatchTL>(), totals[MK_T2]);
+}
+
+static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids, const double* const* metrics,
+                                     int metrics_on_device, const cfd_params* params, void* stream)
+{
+    ctx->grid = grids[0];
+    ctx->prm = params[0];
+    CU(cudaGetDevice(&ctx->dev));
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    CU(cudaMalloc(&ctx->err, sizeof(int)));
+    CU(cudaMalloc(&ctx->dt, sizeof(double)));
+    CU(cudaMalloc(&ctx->t, sizeof(double)));
+    CU(cudaMallocHost(&ctx->h_pinned, 8 * sizeof(double)));
+    CU(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+    CU(cudaMemsetAsync(ctx->t, 0, sizeof(double), ctx->stream));
+    ctx->ph = Phys{};
+    ctx->ph.viscous = params[0].Re > 0.0;
+    for (int b = 0; b < nb; ++b) {
+        cfd_ctx* sb = new (std::nothrow) cfd_ctx();
+        if (!sb) return fail(ctx, CFD_ENOMEM, "host allocation");
+        ctx->sub.push_back(sb);
+        cfd_status st = create_inner(sb, &grids[b], metrics[b], metrics_on_device, &params[b], ctx->stream);
+        if (st != CFD_OK) {
+            ctx->msg = "block " + std::to_string(b) + ": " + sb->msg;
+            return st;
+        }
+    }
+    // per-stage argument tables (stage 1: Uk = U + dt L(U); 2: Uk = 3/4 U + 1/4(Uk + dt L);
+    // 3: U = 1/3 U + 2/3 (Uk + dt L)), sharing the ensemble's dt
+    const double ra[3] = {0.0, 0.75, 1.0 / 3.0}, rb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int s = 0; s < 3; ++s) {
+        std::vector<SweepArgs> tbl(nb);
+        for (int b = 0; b < nb; ++b) {
+            cfd_ctx* sb = ctx->sub[b];
+            const double* Uin = s == 0 ? sb->b.U : sb->b.Uk;
+            double* Uout = s == 2 ? sb->b.U : sb->b.Uk;
+            tbl[b] = make_args(sb, Uin, sb->b.U, Uout, nullptr, ra[s], rb[s]);
+            tbl[b].dt = ctx->dt;
+        }
+        CU(cudaMalloc(&ctx->d_tbl[s], nb * sizeof(SweepArgs)));
+        CU(cudaMemcpyAsync(ctx->d_tbl[s], tbl.data(), nb * sizeof(SweepArgs), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    // work-list maps: prefix sums of tiles and per-block tile grids per kernel kind
+    const int per_kind = (nb + 1) + 3 * nb;
+    std::vector<int> h((size_t)MK_COUNT * per_kind);
+    int totals[MK_COUNT];
+    for (int k = 0; k < MK_COUNT; ++k) {
+        int* pre = h.data() + (size_t)k * per_kind;
+        int* gd = pre + nb + 1;
+        pre[0] = 0;
+        for (int b = 0; b < nb; ++b) {
+            batch_tiles(ctx->sub[b]->g, k, gd + 3 * b);
+            pre[b + 1] = pre[b] + gd[3 * b] * gd[3 * b + 1] * gd[3 * b + 2];
+        }
+        totals[k] = pre[nb];
+    }
+    CU(cudaMalloc(&ctx->d_maps, h.size() * sizeof(int)));
+    CU(cudaMemcpyAsync(ctx->d_maps, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    for (int s = 0; s < 3; ++s)
+        for (int k = 0; k < MK_COUNT; ++k) {
+            int* pre = ctx->d_maps + (size_t)k * per_kind;
+            ctx->maps[s][k] = BatchMap{ctx->d_tbl[s], pre, pre + nb + 1, nb};
+        }
+    if (params[0].precision == CFD_FP32_BULK) {
+        CU((batch_kernel_attrs<float>()));
+        batch_grids<float>(ctx, totals);
+    } else {
+        CU((batch_kernel_attrs<double>()));
+        batch_grids<double>(ctx, totals);
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return CFD_OK;
+}
+
+extern "C" cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_grid* grids,
+                                       const double* const* metrics, int metrics_on_device, const cfd_params* params,
+                                       void* stream)
+{
+    if (!out || !grids || !metrics || !params || nblocks < 1)
+        return fail(nullptr, CFD_EINVAL, "bad argument to cfd_create_batch");
+    *out = nullptr;
+    for (int b = 0; b < nblocks; ++b) {
+        if (!metrics[b]) return fail(nullptr, CFD_EINVAL, "null metrics for a block");
+        cfd_status st = validate(nullptr, &grids[b], &params[b]);
+        if (st != CFD_OK) return st;
+        const cfd_params &p = params[b], &p0 = params[0];
+        if (p.precision != p0.precision || p.scheme != p0.scheme || (p.Re > 0.0) != (p0.Re > 0.0) ||
+            p.visc_order != p0.visc_order || p.metric_mode != p0.metric_mode || p.sensor != p0.sensor)
+            return fail(nullptr, CFD_EINVAL,
+                        "all blocks of a batch share precision, scheme, viscous/inviscid, visc_order and sensor");
+    }
+    cfd_ctx* ctx = new (std::nothrow) cfd_ctx();
+    if (!ctx) return fail(nullptr, CFD_ENOMEM, "host allocation");
+    cfd_status st = create_batch_inner(ctx, nblocks, grids, metrics, metrics_on_device, params, stream);
+    if (st != CFD_OK) {
+        g_static_msg = ctx->msg;
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+        free_all(ctx);
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return CFD_OK;
+}
+
+template <class R>
+static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
+{
+    const bool mixed = sizeof(R) == sizeof(float);
+    const cudaStream_t st = ctx->stream;
+    const BatchMap* m = ctx->maps[s];
+    if (ev) cudaEventRecord(ev[0], st);
+    if (mixed) kb_prim_mixed<<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
+    else kb_prim<double><<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
+    LAUNCH_CHECK();
+    if (ev) cudaEventRecord(ev[1], st);
+    if (mixed || ctx->prm.scheme == CFD_HYBRID) {
+        if (mixed) kb_sensor32<<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
+        else kb_sensor<<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
+        LAUNCH_CHECK();
+    }
+    if (ev) cudaEventRecord(ev[2], st);
+    if (ctx->ph.viscous) {
+        kb_visc_flux25<R, kBatchTZ><<<ctx->map_grid[MK_VISC], 256, visc25_smem_bytes<R>(), st>>>(m[MK_VISC]);
+        LAUNCH_CHECK();
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    kb_sweep_x<R, kBatchBX, EP_STORE><<<ctx->map_grid[MK_SX], kBatchBX, 0, st>>>(m[MK_SX]);
+    LAUNCH_CHECK();
+    if (ev) cudaEventRecord(ev[4], st);
+    kb_sweep_t<R, 1, EP_ACCUM, kBatchTL><<<ctx->map_grid[MK_T1], 256, tile_smem_bytes<R, kBatchTL>(), st>>>(m[MK_T1]);
+    LAUNCH_CHECK();
+    if (ev) cudaEventRecord(ev[5], st);
+    kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL><<<ctx->map_grid[MK_T2], 256, tile_smem_bytes<R, kBatchTL>(), st>>>(
+        m[MK_T2]);
+    LAUNCH_CHECK();
+    if (ev) cudaEventRecord(ev[6], st);
+    // boundary conditions of blocks with non-periodic faces, at the stage time
+    const double tfrac[3] = {1.0, 0.5, 1.0};
+    for (cfd_ctx* sb : ctx->sub) {
+        double* Uout = s == 2 ? sb->b.U : sb->b.Uk;
+        for (int d = 0; d < 3; ++d) {
+            if (sb->g.per[d]) continue;
+            const Geo& g = sb->g;
+            long long nface = d == 0 ? (long long)g.ny * g.nz : (d == 1 ? (long long)g.nx * g.nz : (long long)g.nx * g.ny);
+            k_bc<<<grid_for(2 * nface, 256), 256, 0, st>>>(g, sb->ph, sb->bc, Uout, d, ctx->t, ctx->dt, tfrac[s]);
+            LAUNCH_CHECK();
+        }
+    }
+    return CFD_OK;
+}
+
+static cfd_status enqueue_batch_step(cfd_ctx* ctx)
+{
+    for (int s = 0; s < 3; ++s) {
+        cfd_status st = ctx->prm.precision == CFD_FP32_BULK ? enqueue_batch_stage<float>(ctx, s, nullptr)
+                                                            : enqueue_batch_stage<double>(ctx, s, nullptr);
+        if (st != CFD_OK) return st;
+    }
+    k_advance_time<<<1, 32, 0, ctx->stream>>>(ctx->t, ctx->dt);
+    LAUNCH_CHECK();
+    return CFD_OK;
+}
+
 static cfd_status enqueue_step(cfd_ctx* ctx)
 {
+    if (!ctx->sub.empty()) return enqueue_batch_step(ctx);
     cfd_status st;
     // stage 1: Uk = U + dt L(U)
     st = run_stage<EP_FINAL_RK>(ctx, ctx->b.U, ctx->b.U, ctx->b.Uk, nullptr, 0.0, 1.0);
@@ -760,6 +1032,13 @@ static cfd_status build_graph(cfd_ctx* ctx)
 
 static long long launches_per_step(const cfd_ctx* ctx)
 {
+    if (!ctx->sub.empty()) {
+        const bool sensor = ctx->prm.scheme == CFD_HYBRID || ctx->prm.precision == CFD_FP32_BULK;
+        long long per_stage = 1 + 3 + (sensor ? 1 : 0) + (ctx->ph.viscous ? 1 : 0);
+        for (const cfd_ctx* sb : ctx->sub)
+            for (int d = 0; d < 3; ++d) per_stage += sb->g.per[d] ? 0 : 1;
+        return 3 * per_stage + 1;
+    }
     const bool sensor = !ctx->forced && (ctx->prm.scheme == CFD_HYBRID || ctx->prm.precision == CFD_FP32_BULK);
     long long per_stage = 1 + 3 + (sensor ? 1 : 0) + (ctx->ph.viscous ? 1 : 0);
     long long bc = 0;
@@ -774,7 +1053,7 @@ extern "C" cfd_status cfd_step(cfd_ctx* ctx, double dt, int nsteps)
     if (nsteps == 0) return CFD_OK;
     k_set_scalar<<<1, 32, 0, ctx->stream>>>(ctx->dt, dt);
     LAUNCH_CHECK();
-    {
+    if (ctx->sub.empty()) {
         cfd_status st = autotune(ctx);
         if (st != CFD_OK) return st;
     }
@@ -793,14 +1072,16 @@ extern "C" cfd_status cfd_cfl_dt(cfd_ctx* ctx, int block, double cfl, double* dt
 {
     cfd_status st = check_block(ctx, block);
     if (st != CFD_OK) return st;
+    DELEGATE(cfd_cfl_dt(b_, 0, cfl, dt));
     if (!dt || !(cfl > 0.0)) return fail(ctx, CFD_EINVAL, "bad cfl or null output");
     const Geo& g = ctx->g;
     const bool mixed = ctx->prm.precision == CFD_FP32_BULK;
     const NodeLaunch nl = node_launch(g);
+    const SweepArgs A = make_args(ctx, ctx->b.U, nullptr, nullptr, nullptr, 0.0, 1.0);
     if (mixed)
-        k_prim_mixed<<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, ctx->b.U, (float*)ctx->b.P, ctx->b.cls, ctx->err);
+        k_prim_mixed<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
     else
-        k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(g, ctx->ph, ctx->b.U, (double*)ctx->b.P, ctx->err);
+        k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
     LAUNCH_CHECK();
     CU(cudaMemsetAsync(ctx->cflmax, 0, sizeof(unsigned long long), ctx->stream));
     if (mixed)
@@ -822,6 +1103,7 @@ extern "C" cfd_status cfd_get_flags(cfd_ctx* ctx, int block, unsigned char* cls,
 {
     cfd_status st = check_block(ctx, block);
     if (st != CFD_OK) return st;
+    DELEGATE(cfd_get_flags(b_, 0, cls, on_device));
     if (!cls) return fail(ctx, CFD_EINVAL, "null output");
     CU(cudaMemcpyAsync(cls, ctx->b.cls, ctx->g.N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -833,6 +1115,7 @@ extern "C" cfd_status cfd_force_flags(cfd_ctx* ctx, int block, const unsigned ch
 {
     cfd_status st = check_block(ctx, block);
     if (st != CFD_OK) return st;
+    if (!ctx->sub.empty()) return fail(ctx, CFD_EUNSUPPORTED, "forced classes are per single-block context");
     if (!cls) {
         ctx->forced = false;
     } else {
@@ -860,6 +1143,10 @@ extern "C" cfd_status cfd_set_time(cfd_ctx* ctx, double t)
     ctx->h_pinned[3] = t;
     CU(cudaMemcpyAsync(ctx->t, ctx->h_pinned + 3, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    for (cfd_ctx* b : ctx->sub) {
+        cfd_status st = cfd_set_time(b, t);
+        if (st != CFD_OK) return st;
+    }
     return CFD_OK;
 }
 
@@ -874,6 +1161,13 @@ extern "C" cfd_status cfd_sync(cfd_ctx* ctx, double timeout_s)
         double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el >= timeout_s) return fail(ctx, CFD_ETIMEOUT, "cfd_sync timed out; work still running");
         std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    for (cfd_ctx* b : ctx->sub) {
+        cfd_status st = read_err(b);
+        if (st != CFD_OK) {
+            ctx->msg = b->msg;
+            return st;
+        }
     }
     return read_err(ctx);
 }
@@ -921,6 +1215,28 @@ extern "C" cfd_status cfd_fma_peak(int precision, double* tflops)
 extern "C" cfd_status cfd_profile_stage(cfd_ctx* ctx, int reps, double* ms)
 {
     if (!ctx || !ms || reps < 1) return fail(ctx, CFD_EINVAL, "bad argument to cfd_profile_stage");
+    if (!ctx->sub.empty()) {
+        // ensemble: time the persistent launches of one stage-1 evaluation
+        // (it writes the stage buffers only); [3] is the xi sweep, [4] eta, [5] zeta
+        cudaEvent_t ev[7];
+        for (int i = 0; i < 7; ++i) CU(cudaEventCreate(&ev[i]));
+        for (int i = 0; i < CFD_PROFILE_KERNELS; ++i) ms[i] = 0.0;
+        const int order[6] = {0, 1, 2, 3, 4, 5};
+        cfd_status st = CFD_OK;
+        for (int r = 0; r < reps && st == CFD_OK; ++r) {
+            st = ctx->prm.precision == CFD_FP32_BULK ? enqueue_batch_stage<float>(ctx, 0, ev)
+                                                     : enqueue_batch_stage<double>(ctx, 0, ev);
+            if (st != CFD_OK) break;
+            CU(cudaEventSynchronize(ev[6]));
+            for (int i = 0; i < 6; ++i) {
+                float t = 0.0f;
+                CU(cudaEventElapsedTime(&t, ev[order[i]], ev[order[i] + 1]));
+                ms[i] += t / reps;
+            }
+        }
+        for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+        return st;
+    }
     {
         cfd_status st0 = autotune(ctx);
         if (st0 != CFD_OK) return st0;
@@ -1070,27 +1386,30 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
     // the only value that must start at zero; every other array is fully
     // written before it is read
     NA_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
-    const NodeLaunch nl = node_launch(g);
-    k_prim<double><<<nl.grid, nl.block, 0, s>>>(g, ph, U, (double*)P, err);
-    NA_CHECK(cudaGetLastError());
-    if (params->scheme == CFD_HYBRID) {
-        k_sensor<<<nl.grid, nl.block, 0, s>>>(g, ph, (const double*)P + 4 * N, cls);
-        NA_CHECK(cudaGetLastError());
-    }
-    if (ph.viscous) {
-        k_visc_flux<double><<<nl.grid, nl.block, 0, s>>>(g, ph, (const double*)P, (double*)Fv);
-        NA_CHECK(cudaGetLastError());
-    }
     SweepArgs A{};
     A.g = g;
     A.ph = ph;
     A.P = P;
     A.cls = params->scheme == CFD_HYBRID ? cls : nullptr;
+    A.cls_io = cls;
     A.Fv = ph.viscous ? Fv : nullptr;
     A.R = R;
+    A.err = err;
+    A.U = U;
     A.Lout = dUdt;
     A.rk_b = 1.0;
     A.seg_len = 128;
+    const NodeLaunch nl = node_launch(g);
+    k_prim<double><<<nl.grid, nl.block, 0, s>>>(A);
+    NA_CHECK(cudaGetLastError());
+    if (params->scheme == CFD_HYBRID) {
+        k_sensor<<<nl.grid, nl.block, 0, s>>>(A);
+        NA_CHECK(cudaGetLastError());
+    }
+    if (ph.viscous) {
+        k_visc_flux<double><<<nl.grid, nl.block, 0, s>>>(A);
+        NA_CHECK(cudaGetLastError());
+    }
     {
         const int lo = g.per[0] ? 0 : 1, hi = g.per[0] ? g.nx : g.nx - 1;
         const int nb = g.nx <= 32 ? 32 : (g.nx <= 64 ? 64 : 128);

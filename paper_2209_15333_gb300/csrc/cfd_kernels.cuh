@@ -91,12 +91,13 @@ __device__ __forceinline__ float metr<float>(const Geo& g, int e, long long mi)
     return __ldg(g.metf + (long long)e * g.M + mi);
 }
 
-// node (i, j, k) of a node-parallel kernel launched on a (x-chunks, ny, nz) grid
+// node (i, j, k) of a node-parallel kernel on a (x-chunks, ny, nz) grid of
+// (virtual) blocks vb; the body that follows runs only when i < nx
 #define NODE_IJK(g)                                                                                   \
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;                                              \
-    if (i >= (g).nx) return;                                                                          \
-    const int j = blockIdx.y, k = blockIdx.z;                                                         \
-    const long long n = (long long)i + (long long)(g).nx * ((long long)j + (long long)(g).ny * k)
+    const int i = vb.x * blockDim.x + threadIdx.x;                                                    \
+    const int j = vb.y, k = vb.z;                                                                     \
+    const long long n = (long long)i + (long long)(g).nx * ((long long)j + (long long)(g).ny * k);     \
+    if (i < (g).nx)
 
 __device__ __forceinline__ bool is_bnd(const Geo& g, int i, int j, int k)
 {
@@ -132,19 +133,42 @@ __global__ void k_metric_derive(double* met, long long M)
     }
 }
 
+// Everything a kernel of one stage needs about one block: geometry, gas,
+// buffers and the RK3 epilogue.  Single-block launches pass it by value;
+// batched launches read one per block from a device table.
+struct SweepArgs {
+    Geo g;
+    Phys ph;
+    void* P;               // [7][N] real primitives
+    const uint8_t* cls;    // [N] classes read by the sweeps (null unless hybrid)
+    uint8_t* cls_io;       // [N] classes written by the sensor / read by the mixed recovery
+    void* Fv;              // [12][N] real or null (inviscid)
+    void* R;               // [5][N] real accumulator
+    int* err;              // non-physical flag
+    const double* U;       // stage state  U^(k)
+    const double* Un;      // step state   U^n
+    double* Uout;          // RK output (may alias U or Un)
+    double* Lout;          // L(U) output (rhs mode) or null
+    const double* dt;      // device scalar
+    double rk_a, rk_b;     // U_out = a Un + b (U + dt L)
+    int seg_len;           // streaming segment length
+};
+
 // ---------------------------------------------------------------------------
 // primitive recovery (Eq. 5, 8, 16, 17).  The operation order matches the
 // oracle's (no contraction), so that p -- and with it the sensor's class
 // decisions -- are bit-identical to a plain IEEE evaluation.
 // ---------------------------------------------------------------------------
 template <class RT>
-__global__ void k_prim(Geo g, Phys ph, const double* __restrict__ U, RT* __restrict__ P,
-                       int* __restrict__ err)
+__device__ __forceinline__ void prim_body(const SweepArgs& A, uint3 vb)
 {
+    const Geo& g = A.g;
+    const Phys& ph = A.ph;
+    const double* __restrict__ U = A.U;
+    RT* __restrict__ P = (RT*)A.P;
+    int* err = A.err;
     const long long N = g.N;
-    NODE_IJK(g);
-    (void)j;
-    (void)k;
+    NODE_IJK(g)
     {
         double rho = U[n];
         double u = __ddiv_rn(U[N + n], rho);
@@ -183,11 +207,16 @@ __device__ __forceinline__ bool near_wall(const Geo& g, int i, int j, int k)
     return false;
 }
 
-__global__ void k_prim_mixed(Geo g, Phys ph, const double* __restrict__ U, float* __restrict__ P,
-                             const uint8_t* __restrict__ cls_prev, int* __restrict__ err)
+__device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
 {
+    const Geo& g = A.g;
+    const Phys& ph = A.ph;
+    const double* __restrict__ U = A.U;
+    float* __restrict__ P = (float*)A.P;
+    const uint8_t* __restrict__ cls_prev = A.cls_io;
+    int* err = A.err;
     const long long N = g.N;
-    NODE_IJK(g);
+    NODE_IJK(g)
     {
         float rho, u, v, w, p, T, c;
         if (cls_prev[n] != 0 || near_wall(g, i, j, k)) {
@@ -230,10 +259,14 @@ __device__ __forceinline__ double sensor_phi(double pm, double p0, double pp)
     return __ddiv_rn(num, den);
 }
 
-__global__ void k_sensor(Geo g, Phys ph, const double* __restrict__ p, uint8_t* __restrict__ cls)
+__device__ __forceinline__ void sensor_body(const SweepArgs& A, uint3 vb)
 {
+    const Geo& g = A.g;
+    const Phys& ph = A.ph;
+    const double* __restrict__ p = (const double*)A.P + 4 * g.N;
+    uint8_t* __restrict__ cls = A.cls_io;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    NODE_IJK(g);
+    NODE_IJK(g)
     {
         double p0 = p[n];
         double phi[3];
@@ -257,11 +290,15 @@ __global__ void k_sensor(Geo g, Phys ph, const double* __restrict__ p, uint8_t* 
 }
 
 // the same sensor in FP32 arithmetic on FP32 pressures (mixed precision)
-__global__ void k_sensor32(Geo g, Phys ph, const float* __restrict__ p, uint8_t* __restrict__ cls)
+__device__ __forceinline__ void sensor32_body(const SweepArgs& A, uint3 vb)
 {
+    const Geo& g = A.g;
+    const Phys& ph = A.ph;
+    const float* __restrict__ p = (const float*)A.P + 4 * g.N;
+    uint8_t* __restrict__ cls = A.cls_io;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const float th1 = ph.th1f, th2 = ph.th2f;
-    NODE_IJK(g);
+    NODE_IJK(g)
     {
         float p0 = p[n];
         const int pos[3] = {i, j, k};
@@ -529,12 +566,16 @@ __device__ __forceinline__ float viscosity(const Phys& ph, float T)
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_visc_flux(Geo g, Phys ph, const R* __restrict__ P, R* __restrict__ Fv)
+__device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
 {
+    const Geo& g = A.g;
+    const Phys& ph = A.ph;
+    const R* __restrict__ P = (const R*)A.P;
+    R* __restrict__ Fv = (R*)A.Fv;
     const long long N = g.N;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int ord = ph.vorder;
-    NODE_IJK(g);
+    NODE_IJK(g)
     {
         const int st[3] = {1, nx, nx * ny};
         const int pos[3] = {i, j, k};
@@ -648,16 +689,20 @@ constexpr size_t visc25_smem_bytes()
 }
 
 template <class R, int TZ>
-__global__ void __launch_bounds__(256) k_visc_flux25(Geo g, Phys ph, const R* __restrict__ P, R* __restrict__ Fv)
+__device__ __forceinline__ void visc25_body(const SweepArgs& A, uint3 vb)
 {
+    const Geo& g = A.g;
+    const Phys& ph = A.ph;
+    const R* __restrict__ P = (const R*)A.P;
+    R* __restrict__ Fv = (R*)A.Fv;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* ring = reinterpret_cast<R*>(smem_raw);  // [9][4][16][40]
     constexpr int PL = 4 * 16 * 40;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const long long N = g.N;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
-    const int zlo = blockIdx.z * TZ, zhi = min(zlo + TZ, nz);
+    const int x0 = vb.x * 32, y0 = vb.y * 8;
+    const int zlo = vb.z * TZ, zhi = min(zlo + TZ, nz);
     const int i = x0 + tx, j = y0 + ty;
     const bool own = i < nx && j < ny;
     const int ord = ph.vorder;
@@ -707,23 +752,6 @@ __global__ void __launch_bounds__(256) k_visc_flux25(Geo g, Phys ph, const R* __
 // ---------------------------------------------------------------------------
 // the directional sweeps
 // ---------------------------------------------------------------------------
-struct SweepArgs {
-    Geo g;
-    Phys ph;
-    const void* P;         // [7][N] real
-    const uint8_t* cls;    // [N] or null (non-hybrid)
-    const void* Fv;        // [12][N] real or null (inviscid)
-    void* R;               // [5][N] real accumulator
-    // epilogue of the last sweep
-    const double* U;       // stage state  U^(k)
-    const double* Un;      // step state   U^n
-    double* Uout;          // RK output (may alias U or Un)
-    double* Lout;          // L(U) output (rhs mode) or null
-    const double* dt;      // device scalar
-    double rk_a, rk_b;     // U_out = a Un + b (U + dt L)
-    int seg_len;           // streaming segment length
-};
-
 // epilogue modes
 enum { EP_STORE = 0, EP_ACCUM = 1, EP_FINAL_RHS = 2, EP_FINAL_RK = 3 };
 
@@ -788,7 +816,7 @@ __device__ __forceinline__ void node_split(const SweepArgs& A, int d, long long 
 
 // xi sweep: one CTA per segment of BX nodes of one x-line, halo of 4 nodes.
 template <class R, int BX, int EP>
-__global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
+__device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
 {
     __shared__ __align__(16) R sf[10][BX + 12];  // rows padded so a 12-value window never leaves a row
     __shared__ R sh[5][BX + 1];
@@ -797,9 +825,9 @@ __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
     const Geo& g = A.g;
     const int n = g.nx;
     const int per = g.per[0];
-    const int j = blockIdx.y, k = blockIdx.z;
+    const int j = vb.y, k = vb.z;
     const int lo = per ? 0 : 1;                 // first node that gets a right-hand side
-    const int i0 = lo + blockIdx.x * BX;
+    const int i0 = lo + vb.x * BX;
     const long long row = (long long)n * (j + (long long)g.ny * k);
     const int t = threadIdx.x;
     for (int s = t; s < BX + 8; s += BX) {
@@ -894,7 +922,7 @@ __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A)
         epilogue<R, EP>(A, nn, i, j, k, val);
     }
     // zero the non-periodic boundary nodes of the accumulator
-    if (EP == EP_STORE && !per && blockIdx.x == 0 && t < 2) {
+    if (EP == EP_STORE && !per && vb.x == 0 && t < 2) {
         int ib = t == 0 ? 0 : n - 1;
         R* Racc = (R*)A.R;
 #pragma unroll
@@ -1004,7 +1032,7 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
 // differenced.  The halo costs 8/TL extra splits -- cheap in FP32, where the
 // streaming form is latency-bound instead.
 template <class R, int DIR, int EP, int TL>
-__global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A)
+__device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
 {
     constexpr int ROWS = TL + 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1018,10 +1046,10 @@ __global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A)
     const long long stride = DIR == 1 ? (long long)nx : (long long)nx * g.ny;
     const int per = g.per[DIR];
     const int lo = per ? 0 : 1, hi = per ? n : n - 1;
-    const int i = blockIdx.x * 32 + lane;
+    const int i = vb.x * 32 + lane;
     const bool lane_ok = i < nx;
-    const int o = blockIdx.y;
-    const int m0 = lo + blockIdx.z * TL;
+    const int o = vb.y;
+    const int m0 = lo + vb.z * TL;
     const long long base = DIR == 1 ? (long long)i + (long long)nx * g.ny * o : (long long)i + (long long)nx * o;
     const long long N = g.N;
     const R* Fv = (const R*)A.Fv;
@@ -1111,8 +1139,7 @@ __global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A)
     }
     __syncthreads();
     // 3. difference, viscous divergence and the epilogue
-    if (!lane_ok) return;
-    for (int r = ty; r < TL; r += 8) {
+    for (int r = ty; r < TL && lane_ok; r += 8) {
         const int m = m0 + r;
         if (m >= hi) break;
         R val[5];
@@ -1269,5 +1296,72 @@ __global__ void k_advance_time(double* t, const double* dt)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *t += *dt;
 }
+
+// ---------------------------------------------------------------------------
+// kernels: single-block launches (grid = the block's tiles) ...
+// ---------------------------------------------------------------------------
+template <class RT>
+__global__ void k_prim(SweepArgs A) { prim_body<RT>(A, blockIdx); }
+__global__ void k_prim_mixed(SweepArgs A) { prim_mixed_body(A, blockIdx); }
+__global__ void k_sensor(SweepArgs A) { sensor_body(A, blockIdx); }
+__global__ void k_sensor32(SweepArgs A) { sensor32_body(A, blockIdx); }
+template <class R>
+__global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R>(A, blockIdx); }
+template <class R, int TZ>
+__global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<R, TZ>(A, blockIdx); }
+template <class R, int BX, int EP>
+__global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A) { sweep_x_body<R, BX, EP>(A, blockIdx); }
+template <class R, int DIR, int EP, int TL>
+__global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A) { sweep_t_body<R, DIR, EP, TL>(A, blockIdx); }
+
+// ---------------------------------------------------------------------------
+// ... and persistent batched launches over an ensemble of uneven blocks: one
+// launch per kernel kind covers the tiles of every block; CTAs walk a work
+// list (item -> block by binary search over the per-block tile prefix sums,
+// then the block-local tile coordinates) with a grid-size stride.
+// ---------------------------------------------------------------------------
+struct BatchMap {
+    const SweepArgs* tbl;  // [nb] per-block arguments of this stage
+    const int* prefix;     // [nb+1] tile prefix sums for this kernel kind
+    const int* gdim;       // [nb][3] per-block tile grid of this kernel kind
+    int nb;
+};
+
+__device__ __forceinline__ int batch_find(const BatchMap& m, int item, uint3* v)
+{
+    int lo = 0, hi = m.nb;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(m.prefix + mid) <= item) lo = mid;
+        else hi = mid;
+    }
+    const int local = item - __ldg(m.prefix + lo);
+    const int gx = __ldg(m.gdim + 3 * lo), gy = __ldg(m.gdim + 3 * lo + 1);
+    v->x = local % gx;
+    v->y = (local / gx) % gy;
+    v->z = local / (gx * gy);
+    return lo;
+}
+
+#define BATCH_LOOP(BODY, SYNC)                                                                        \
+    const int total = __ldg(m.prefix + m.nb);                                                         \
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {                                    \
+        uint3 v;                                                                                      \
+        const int b = batch_find(m, item, &v);                                                        \
+        BODY(m.tbl[b], v);                                                                            \
+        if (SYNC) __syncthreads();                                                                    \
+    }
+
+template <class RT>
+__global__ void kb_prim(BatchMap m) { BATCH_LOOP(prim_body<RT>, false) }
+__global__ void kb_prim_mixed(BatchMap m) { BATCH_LOOP(prim_mixed_body, false) }
+__global__ void kb_sensor(BatchMap m) { BATCH_LOOP(sensor_body, false) }
+__global__ void kb_sensor32(BatchMap m) { BATCH_LOOP(sensor32_body, false) }
+template <class R, int TZ>
+__global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((visc25_body<R, TZ>), true) }
+template <class R, int BX, int EP>
+__global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m) { BATCH_LOOP((sweep_x_body<R, BX, EP>), true) }
+template <class R, int DIR, int EP, int TL>
+__global__ void __launch_bounds__(256) kb_sweep_t(BatchMap m) { BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true) }
 
 }  // namespace cfdk

@@ -142,3 +142,56 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class BatchSolver(Solver):
+    """Ensemble of independent blocks of uneven sizes (cfd_create_batch).
+
+    shapes: list of (nx, ny, nz); metrics: list of metric arrays; params: list
+    of keyword dicts (one per block); bcs: optional list of (bc_lo, bc_hi).
+    """
+
+    def __init__(self, shapes, metrics, params, *, bcs=None, stream=None):
+        nb = len(shapes)
+        self.shapes = [(nz, ny, nx) for (nx, ny, nz) in shapes]
+        self.shape = self.shapes[0]
+        grids = (L.CfdGrid * nb)()
+        prms = (L.CfdParams * nb)()
+        self._metrics = []
+        mptrs = (C.c_void_p * nb)()
+        dev_flags = set()
+        for b in range(nb):
+            nx, ny, nz = shapes[b]
+            m = metrics[b]
+            ndim = m.dim() if _is_torch(m) else np.asarray(m).ndim
+            layout = {1: L.METRICS_UNIFORM, 3: L.METRICS_2D, 4: L.METRICS_3D}[ndim]
+            if not _is_torch(m):
+                m = np.ascontiguousarray(m, dtype=np.float64)
+            self._metrics.append(m)
+            lo, hi = bcs[b] if bcs else ((0, 0, 0), (0, 0, 0))
+            grids[b] = L.make_grid(nx, ny, nz, lo, hi, layout)
+            prms[b] = L.default_params(**params[b])
+            p, dev = _ptr(m)
+            mptrs[b] = p
+            dev_flags.add(dev)
+        if len(dev_flags) != 1:
+            raise ValueError("metrics must be all on the host or all on the device")
+        self.ctx = C.c_void_p()
+        stream_ptr = None if stream is None else C.c_void_p(getattr(stream, "cuda_stream", stream))
+        L.check(L.lib().cfd_create_batch(C.byref(self.ctx), nb, grids, mptrs, dev_flags.pop(), prms, stream_ptr))
+        self.nblocks = nb
+
+    def get_state(self, out=None, block=0):
+        if out is None:
+            out = np.empty((5,) + self.shapes[block])
+        return super().get_state(out, block)
+
+    def rhs(self, out=None, block=0):
+        if out is None:
+            out = np.empty((5,) + self.shapes[block])
+        return super().rhs(out, block)
+
+    def flags(self, block=0):
+        out = np.empty(self.shapes[block], dtype=np.uint8)
+        L.check(L.lib().cfd_get_flags(self.ctx, block, C.c_void_p(out.ctypes.data), 0), self.ctx)
+        return out
