@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="one profiled stage per precision (ncu runs)")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-block ensemble measurement")
     ap.add_argument("--variants", default="", help="pin kernel variants, e.g. 0:2,1:1:16,2:1:16 (dir:kind[:param])")
     return ap.parse_args()
 
@@ -286,6 +287,47 @@ def run_precision(args, prec, U, met, params, world, local, dt):
                 e2e=world * N * 3 * args.steps / e2e_s, prof=prof, U1=U1, variants=variants)
 
 
+def run_ensemble(args, world):
+    """Batched ensemble: 48 periodic isotropic-turbulence blocks with dims
+    drawn from {32,48,64,96,128} per axis and Mt in [0.3, 0.7], FP32 bulk /
+    FP64 state, one persistent launch per kernel kind per stage."""
+    import torch
+    from paper_2209_15333_gb300 import cases
+    from paper_2209_15333_gb300.solver import BatchSolver
+    blocks = cases.ensemble_blocks(48, SEED)
+    nodes = sum(int(np.prod(b["shape"])) for b in blocks)
+    params = [dict(gamma=GAMMA, Re=b["Re"], Ma=b["Mt"], Pr=0.72, visc_law=1, visc_omega=0.76, scheme=3,
+                   theta1=0.02, theta2=0.1, visc_order=8, precision=1) for b in blocks]
+    stream = torch.cuda.Stream()
+    bs = BatchSolver([b["shape"] for b in blocks], [b["metrics"] for b in blocks], params, stream=stream)
+    for i, b in enumerate(blocks):
+        bs.set_state(b["U"], block=i)
+    dt = min(bs.cfl_dt(0.5, block=i) for i in range(len(blocks)))
+    for _ in range(args.warmup):
+        bs.step(dt, 1)
+    bs.sync(600.0)
+    l0 = bs.launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bs.step(dt, args.steps)
+    e1.record(stream)
+    bs.sync(600.0)
+    ms = e0.elapsed_time(e1)
+    launches = bs.launches() - l0
+    prof = bs.profile_stage(3)
+    bs.close()
+    names = {"sweep_xi": "sweep_xi", "sweep_eta": "sweep_eta", "sweep_zeta": "sweep_zeta"}
+    return {"workload": "48 periodic isotropic-turbulence blocks, dims i.i.d. from {32,48,64,96,128}, "
+                        "Mt in [0.3,0.7], hybrid, viscous, FP32 bulk / FP64 state",
+            "nodes": nodes, "value": world * nodes * 3 * args.steps / (ms * 1e-3), "unit": "point-stage/s",
+            "ms_per_step": ms / args.steps, "gpu_launches": launches,
+            "launches_per_step": launches / max(1, args.steps), "kernel_ms": prof}
+
+
 def roofline(prec, r, N, peaks, fma, src_hash):
     prof = r["prof"]
     dom = max(prof, key=prof.get)
@@ -329,6 +371,7 @@ def main():
     res = {p: run_precision(args, p, U, met, params, world, local, dt) for p in precs}
     if args.profile_only:
         return
+    ens = None if args.no_ensemble else run_ensemble(args, world)
     fma = fma_peaks()
     peaks, peak_kind = measured_peaks()
     src_hash = kernel_src_hash()
@@ -382,6 +425,8 @@ def main():
     }
     if head == "mixed" and "fp64" in res:
         line["fp64"] = summary("fp64")
+    if ens is not None:
+        line["ensemble"] = ens
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

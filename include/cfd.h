@@ -130,6 +130,33 @@ cfd_status cfd_set_inflow(cfd_ctx* ctx, const double* prim);
 cfd_status cfd_set_blowing(cfd_ctx* ctx, double amp, double x0, double x1, double omega, int m,
                            double Lz, const double* wall_x, const double* wall_z);
 
+/*
+ * Learned shock sensor (not in the paper: it stands in for the sensor of
+ * Eq. 42-43).  A 42 -> 32 -> 32 -> 3 MLP with ReLU, BF16 weights and FP32
+ * accumulation on the tensor cores classifies every node (0 UD7, 1 WENO7,
+ * 2 WENO5) from normalised stencil differences of p and rho (see
+ * cfd_sensor_features); the interface rule (largest class over m-3..m+4)
+ * applies as for the plain sensor.  A node whose largest softmax
+ * probability is below conf_min, or whose features are not finite, takes
+ * the plain sensor's class.  weights_bf16: W1[32][42], W2[32][32],
+ * W3[3][32] (row = output), as consecutive bf16 (uint16) arrays; biases:
+ * b1[32], b2[32], b3[3] float.  NULL weights switch back to the plain
+ * sensor.  Single-block contexts only (CFD_EUNSUPPORTED for ensembles).
+ */
+cfd_status cfd_set_sensor_mlp(cfd_ctx* ctx, const void* weights_bf16, const float* biases,
+                              float conf_min);
+
+/* The 42 sensor features of every node of the current state, float
+   [42][nz][ny][nx]: for each direction d (xi, eta, zeta) and field q (p,
+   rho), over line positions m-3..m+3 (periodic lines wrap, others clamp),
+   (q_{m+t+1} - q_{m+t})/q_m for t = -3..2 and
+   (q_{m-1} - 2 q_m + q_{m+1})/(q_{m-1} + 2 q_m + q_{m+1}); feature index
+   (2 d + field) * 7 + t.  For training the learned sensor. */
+cfd_status cfd_sensor_features(cfd_ctx* ctx, int block, float* out, int on_device);
+
+/* Nodes that fell back to the plain sensor since the last call (reset). */
+cfd_status cfd_sensor_fallbacks(cfd_ctx* ctx, unsigned long long* count);
+
 /* Copy U [5][nz][ny][nx] into the context and apply the boundary
    conditions at the context time.  block: 0 (single-block contexts). */
 cfd_status cfd_set_state(cfd_ctx* ctx, int block, const double* U, int on_device);

@@ -27,6 +27,7 @@ EXPORTS = ["cfd_default_params", "cfd_create", "cfd_create_batch", "cfd_set_infl
            "cfd_get_state", "cfd_rhs", "cfd_step", "cfd_cfl_dt", "cfd_get_flags", "cfd_force_flags",
            "cfd_get_time", "cfd_set_time", "cfd_sync", "cfd_last_error", "cfd_launch_count", "cfd_fma_peak",
            "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
+           "cfd_set_sensor_mlp", "cfd_sensor_features", "cfd_sensor_fallbacks",
            "cfd_destroy"]
 
 
@@ -84,6 +85,9 @@ def lib():
         L.cfd_launch_count.restype = C.c_longlong
         L.cfd_fma_peak.argtypes = [C.c_int, dp]
         L.cfd_profile_stage.argtypes = [vp, C.c_int, dp]
+        L.cfd_set_sensor_mlp.argtypes = [vp, vp, vp, C.c_float]
+        L.cfd_sensor_features.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.cfd_sensor_fallbacks.argtypes = [vp, C.POINTER(C.c_ulonglong)]
         L.cfd_set_sweep_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.cfd_get_sweep_variant.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cfd_rhs_noalloc.argtypes = [C.POINTER(CfdGrid), C.POINTER(CfdParams), vp, vp, vp, vp]

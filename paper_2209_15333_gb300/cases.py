@@ -82,7 +82,7 @@ def taylor_green(n, Ma=0.5, gamma=1.4):
 
 
 def isotropic_turbulence(n, seed, Mt=0.5, gamma=1.4, k0=4.0, Re_lambda=72.0, visc_mu1=1.0):
-    """Decaying isotropic turbulence initial field on [0, 2 pi)^3.
+    """Decaying isotropic turbulence initial field on [0, 2 pi)^3 (n^3 nodes).
 
     Random-phase solenoidal velocity with E(k) ~ k^4 exp(-2 (k/k0)^2),
     scaled to <u_i u_i> = 1, uniform rho = T = 1, so the turbulent Mach
@@ -90,27 +90,34 @@ def isotropic_turbulence(n, seed, Mt=0.5, gamma=1.4, k0=4.0, Re_lambda=72.0, vis
     Re_lambda = u' lambda Re / mu(1), u' = 1/sqrt(3),
     lambda = u' / <(du/dx)^2>^(1/2) measured on the generated field.
     """
+    return isotropic_turbulence_box(n, n, n, seed, Mt, gamma, k0, Re_lambda, visc_mu1)
+
+
+def isotropic_turbulence_box(nx, ny, nz, seed, Mt=0.5, gamma=1.4, k0=4.0, Re_lambda=72.0, visc_mu1=1.0):
+    """The same recipe on an nx x ny x nz box of [0, 2 pi)^3 (uneven
+    resolutions per axis; integer wavenumbers, each axis up to its Nyquist)."""
     rng = np.random.default_rng(seed)
-    k1 = np.fft.fftfreq(n, d=1.0 / n)
-    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")
+    kz1 = np.fft.fftfreq(nz, d=1.0 / nz)
+    ky1 = np.fft.fftfreq(ny, d=1.0 / ny)
+    kx1 = np.fft.fftfreq(nx, d=1.0 / nx)
+    KZ, KY, KX = np.meshgrid(kz1, ky1, kx1, indexing="ij")
     K2 = KX * KX + KY * KY + KZ * KZ
     K = np.sqrt(K2)
     Ek = K ** 4 * np.exp(-2.0 * (K / k0) ** 2)
     with np.errstate(divide="ignore", invalid="ignore"):
         amp = np.where(K > 0, np.sqrt(Ek / (4.0 * np.pi * np.maximum(K2, 1e-300))), 0.0)
-    comps = []
-    for _ in range(3):
-        ph = rng.uniform(0.0, TWO_PI, size=K.shape)
-        comps.append(amp * np.exp(1j * ph))
-    c = np.stack(comps)
+    c = [amp * np.exp(1j * rng.uniform(0.0, TWO_PI, size=K.shape)) for _ in range(3)]
     # solenoidal projection: c <- c - k (k.c)/|k|^2
     with np.errstate(divide="ignore", invalid="ignore"):
         kdotc = (KX * c[0] + KY * c[1] + KZ * c[2]) / np.where(K2 > 0, K2, 1.0)
     c[0] -= KX * kdotc
     c[1] -= KY * kdotc
     c[2] -= KZ * kdotc
-    vel = np.stack([np.real(np.fft.ifftn(c[i])) for i in range(3)])
-    # Nyquist planes make the real part slightly divergent for even n: remove them
+    vel = np.empty((3,) + K.shape)
+    for i in range(3):
+        vel[i] = np.real(np.fft.ifftn(c[i]))
+    del c
+    # Nyquist planes make the real part slightly divergent for even n: remove the mean
     vel -= vel.mean(axis=(1, 2, 3), keepdims=True)
     scale = 1.0 / math.sqrt(float(np.mean(np.sum(vel * vel, axis=0))))
     vel *= scale
@@ -119,10 +126,26 @@ def isotropic_turbulence(n, seed, Mt=0.5, gamma=1.4, k0=4.0, Re_lambda=72.0, vis
     uprime = 1.0 / math.sqrt(3.0)
     lam = uprime / math.sqrt(float(np.mean(dudx * dudx)))
     Re = Re_lambda * visc_mu1 / (uprime * lam)
-    rho = np.ones((n, n, n))
-    p = np.full((n, n, n), 1.0 / (gamma * Mt * Mt))
+    shp = (nz, ny, nx)
+    rho = np.ones(shp)
+    p = np.full(shp, 1.0 / (gamma * Mt * Mt))
     U = conserved(rho, vel[0], vel[1], vel[2], p, gamma)
     return U, Re
+
+
+def ensemble_blocks(nblocks=48, seed=20220930, sizes=(32, 48, 64, 96, 128), mt_range=(0.3, 0.7)):
+    """Batched-ensemble workload: block dims drawn i.i.d. per axis from
+    `sizes`, block b seeded with seed + b and a turbulent Mach number drawn
+    uniformly in mt_range.  Returns a list of dicts (shape (nx, ny, nz), U,
+    Re, Mt, metrics)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(nblocks):
+        nx, ny, nz = (int(x) for x in rng.choice(sizes, size=3))
+        mt = float(rng.uniform(*mt_range))
+        U, Re = isotropic_turbulence_box(nx, ny, nz, seed + b, Mt=mt)
+        out.append(dict(shape=(nx, ny, nz), U=U, Re=Re, Mt=mt, metrics=uniform_metrics(nx, ny, nz)))
+    return out
 
 
 def isentropic_vortex(n, nz=8, gamma=1.4, beta=5.0, L=20.0, t=0.0, mean=(1.0, 1.0)):

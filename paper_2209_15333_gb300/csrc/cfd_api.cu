@@ -47,7 +47,11 @@ struct cfd_ctx {
     float* metf = nullptr;          // [31][M] float mirror
     int sweep_kind[3] = {0, 0, 0};  // eta/zeta: 0 streaming, 1 tile (chosen by the autotuner)
     int sweep_param[3] = {0, 128, 128};
-    int visc_kind = 0;              // 0 node-parallel, 1 2.5-D TZ 64, 2 2.5-D TZ 32 (autotuned)
+    int visc_kind = 0;
+    // learned sensor
+    void* mlp_buf = nullptr;                    // w1, w2, w3 (bf16), b1, b2, b3 (f32), fallback counter
+    MlpArgs mlp{};
+    bool mlp_on = false;              // 0 node-parallel, 1 2.5-D TZ 64, 2 2.5-D TZ 32 (autotuned)
     bool tuned = false;
     // ensemble of blocks (cfd_create_batch): one single-block context per block
     // plus the tables that drive one persistent launch per kernel kind
@@ -181,7 +185,7 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
     if (!(p->weno_eps > 0.0)) return fail(ctx, CFD_EINVAL, "weno_eps must be > 0");
     if (p->metric_mode != CFD_METRIC_NODAL) return fail(ctx, CFD_EUNSUPPORTED, "only the nodal metric mode");
     if (p->precision != CFD_FP64 && p->precision != CFD_FP32_BULK) return fail(ctx, CFD_EINVAL, "unknown precision");
-    if (p->sensor != CFD_SENSOR_PLAIN) return fail(ctx, CFD_EUNSUPPORTED, "only the plain sensor");
+    if (p->sensor != CFD_SENSOR_PLAIN && p->sensor != CFD_SENSOR_MLP) return fail(ctx, CFD_EINVAL, "unknown sensor");
     if (p->scheme == CFD_HYBRID && !(p->theta1 <= p->theta2)) return fail(ctx, CFD_EINVAL, "theta1 > theta2");
     bool wall = false;
     for (int d = 0; d < 3; ++d) wall |= gr->bc_lo[d] == CFD_BC_WALL_ISOTHERMAL || gr->bc_hi[d] == CFD_BC_WALL_ISOTHERMAL;
@@ -201,6 +205,7 @@ static void free_all(cfd_ctx* c)
     if (c->d_maps) cudaFree(c->d_maps);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void* ptrs[] = {c->b.U, c->b.Uk, c->b.P, c->b.Fv, c->b.R, c->b.cls, c->b.cls_tune, c->met, c->metf, c->err, c->dt, c->t,
+                    c->mlp_buf,
                     c->cflmax, c->inflow, c->wall_x, c->wall_z};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -339,9 +344,6 @@ static cfd_status check_block(cfd_ctx* ctx, int block)
     if (block < 0 || block >= nb) return fail(ctx, CFD_EINVAL, "block index out of range");
     return CFD_OK;
 }
-
-// the context that holds block `block` (itself for single-block contexts)
-static cfd_ctx* blk(cfd_ctx* ctx, int block) { return ctx->sub.empty() ? ctx : ctx->sub[block]; }
 
 // run a per-block call on the block's context and copy its error message up
 #define DELEGATE(call_on_sub)                                                                         \
@@ -490,10 +492,15 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
     LAUNCH_CHECK();
     if (ev) cudaEventRecord(ev[1], ctx->stream);
     if (!ctx->forced && (mixed || ctx->prm.scheme == CFD_HYBRID)) {
-        if (mixed)
+        if (ctx->prm.sensor == CFD_SENSOR_MLP) {
+            if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
+            dim3 grid((g.nx + 127) / 128, g.ny, g.nz);
+            k_sensor_mlp<R><<<grid, 128, 0, ctx->stream>>>(A, ctx->mlp);
+        } else if (mixed) {
             k_sensor32<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
-        else
+        } else {
             k_sensor<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+        }
         LAUNCH_CHECK();
     }
     if (ev) cudaEventRecord(ev[2], ctx->stream);
@@ -1435,5 +1442,98 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
         NA_CHECK(cudaGetLastError());
     }
 #undef NA_CHECK
+    return CFD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned sensor: weights, features, fallback statistics
+// ---------------------------------------------------------------------------
+extern "C" cfd_status cfd_set_sensor_mlp(cfd_ctx* ctx, const void* weights_bf16, const float* biases, float conf_min)
+{
+    if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
+    if (!ctx->sub.empty()) return fail(ctx, CFD_EUNSUPPORTED, "the learned sensor is per single-block context");
+    if (!weights_bf16 || !biases) {
+        ctx->mlp_on = false;
+        ctx->prm.sensor = CFD_SENSOR_PLAIN;
+        ctx->graph_valid = false;
+        return CFD_OK;
+    }
+    if (!(conf_min >= 0.0f && conf_min <= 1.0f)) return fail(ctx, CFD_EINVAL, "conf_min must be in [0, 1]");
+    // padded layouts: w1 [32][48], w2 [32][32], w3 [8][32]; biases b1[32], b2[32], b3[8]
+    const size_t n1 = 32 * MLP_KP, n2 = 32 * 32, n3 = 8 * 32;
+    std::vector<uint16_t> hw(n1 + n2 + n3, 0);
+    const uint16_t* src = (const uint16_t*)weights_bf16;
+    for (int o = 0; o < 32; ++o)
+        for (int i = 0; i < MLP_IN; ++i) hw[o * MLP_KP + i] = src[o * MLP_IN + i];
+    src += 32 * MLP_IN;
+    for (int o = 0; o < 32; ++o)
+        for (int i = 0; i < 32; ++i) hw[n1 + o * 32 + i] = src[o * 32 + i];
+    src += 32 * 32;
+    for (int o = 0; o < MLP_OUT; ++o)
+        for (int i = 0; i < 32; ++i) hw[n1 + n2 + o * 32 + i] = src[o * 32 + i];
+    std::vector<float> hb(72, 0.0f);
+    for (int e = 0; e < 32; ++e) hb[e] = biases[e];
+    for (int e = 0; e < 32; ++e) hb[32 + e] = biases[32 + e];
+    for (int e = 0; e < MLP_OUT; ++e) hb[64 + e] = biases[64 + e];
+    const size_t wbytes = hw.size() * sizeof(uint16_t), bbytes = hb.size() * sizeof(float);
+    if (!ctx->mlp_buf) CU(cudaMalloc(&ctx->mlp_buf, wbytes + bbytes + 64));
+    char* base = (char*)ctx->mlp_buf;
+    CU(cudaMemcpyAsync(base, hw.data(), wbytes, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(base + wbytes, hb.data(), bbytes, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(base + wbytes + bbytes, 0, 8, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const uint16_t* dw = (const uint16_t*)base;
+    const float* db = (const float*)(base + wbytes);
+    ctx->mlp = MlpArgs{dw, dw + n1, dw + n1 + n2, db, db + 32, db + 64, conf_min,
+                       (unsigned long long*)(base + wbytes + bbytes)};
+    ctx->mlp_on = true;
+    ctx->prm.sensor = CFD_SENSOR_MLP;
+    ctx->graph_valid = false;
+    return CFD_OK;
+}
+
+extern "C" cfd_status cfd_sensor_features(cfd_ctx* ctx, int block, float* out, int on_device)
+{
+    cfd_status st = check_block(ctx, block);
+    if (st != CFD_OK) return st;
+    if (!out) return fail(ctx, CFD_EINVAL, "null output");
+    DELEGATE(cfd_sensor_features(b_, 0, out, on_device));
+    const Geo& g = ctx->g;
+    const long long bytes = (long long)MLP_IN * g.N * sizeof(float);
+    float* dev = nullptr;
+    if (on_device) {
+        dev = out;
+    } else {
+        CU(cudaMalloc(&dev, bytes));
+    }
+    const NodeLaunch nl = node_launch(g);
+    const SweepArgs A = make_args(ctx, ctx->b.U, nullptr, nullptr, nullptr, 0.0, 1.0);
+    if (ctx->prm.precision == CFD_FP32_BULK)
+        k_prim_mixed<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+    else
+        k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+    LAUNCH_CHECK();
+    if (ctx->prm.precision == CFD_FP32_BULK)
+        k_mlp_features<float><<<nl.grid, nl.block, 0, ctx->stream>>>(A, dev);
+    else
+        k_mlp_features<double><<<nl.grid, nl.block, 0, ctx->stream>>>(A, dev);
+    LAUNCH_CHECK();
+    if (!on_device) {
+        CU(cudaMemcpyAsync(out, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        cudaFree(dev);
+    }
+    return read_err(ctx);
+}
+
+extern "C" cfd_status cfd_sensor_fallbacks(cfd_ctx* ctx, unsigned long long* count)
+{
+    if (!ctx || !count) return fail(ctx, CFD_EINVAL, "null argument");
+    *count = 0;
+    if (!ctx->mlp_on) return CFD_OK;
+    CU(cudaMemcpyAsync(ctx->h_pinned + 5, ctx->mlp.fallbacks, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp.fallbacks, 0, 8, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(count, ctx->h_pinned + 5, 8);
     return CFD_OK;
 }

@@ -318,6 +318,271 @@ __device__ __forceinline__ void sensor32_body(const SweepArgs& A, uint3 vb)
 }
 
 // ---------------------------------------------------------------------------
+// learned shock sensor: 42 normalised stencil differences of p and rho ->
+// 32 -> 32 -> 3 MLP (BF16 weights, FP32 accumulation on the tensor cores
+// with mma.sync m16n8k16), falling back to the plain sensor (Eq. 42-43) when
+// the largest softmax probability is below conf_min or an input is not finite.
+// Features, for each direction d and field q in (p, rho), over the line
+// positions m-3..m+3 (periodic lines wrap, others clamp at the ends):
+//   (q_{m+t+1} - q_{m+t}) / q_m for t = -3..2, and
+//   (q_{m-1} - 2 q_m + q_{m+1}) / (q_{m-1} + 2 q_m + q_{m+1});
+// feature index (2 d + field) * 7 + t.
+// ---------------------------------------------------------------------------
+enum { MLP_IN = 42, MLP_H = 32, MLP_OUT = 3, MLP_KP = 48, MLP_NP = 8 };
+
+struct MlpArgs {
+    const uint16_t* w1;  // [32][48] bf16, in padded with zeros
+    const uint16_t* w2;  // [32][32] bf16
+    const uint16_t* w3;  // [8][32] bf16, rows 3..7 zero
+    const float* b1;     // [32]
+    const float* b2;     // [32]
+    const float* b3;     // [8]
+    float conf_min;
+    unsigned long long* fallbacks;  // count of nodes that fell back to the plain sensor
+};
+
+template <class RT>
+__device__ __forceinline__ void mlp_features(const SweepArgs& A, int i, int j, int k, long long n, float f[MLP_IN])
+{
+    const Geo& g = A.g;
+    const RT* P = (const RT*)A.P;
+    const long long N = g.N;
+    const int pos[3] = {i, j, k};
+    const int nd[3] = {g.nx, g.ny, g.nz};
+    const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int m = pos[d];
+        long long off[7];
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+            int mm = m + t - 3;
+            if (g.per[d]) mm = wrapi(mm, nd[d]);
+            else mm = mm < 0 ? 0 : (mm >= nd[d] ? nd[d] - 1 : mm);
+            off[t] = (long long)(mm - m) * st[d];
+        }
+#pragma unroll
+        for (int fld = 0; fld < 2; ++fld) {
+            const RT* q = P + (fld == 0 ? 4 * N : 0) + n;
+            float v[7];
+#pragma unroll
+            for (int t = 0; t < 7; ++t) v[t] = (float)q[off[t]];
+            const float inv = 1.0f / v[3];
+            float* o = f + (2 * d + fld) * 7;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) o[t] = (v[t + 1] - v[t]) * inv;
+            o[6] = (v[2] - 2.0f * v[3] + v[4]) / (v[2] + 2.0f * v[3] + v[4]);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const uint32_t a = __float_as_uint(lo), b = __float_as_uint(hi);
+    // round to nearest even
+    const uint32_t ra = (a + 0x7FFFu + ((a >> 16) & 1u)) >> 16;
+    const uint32_t rb = (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
+    return ra | (rb << 16);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// plain-sensor class of one node in the kernel's precision (the fallback)
+template <class RT>
+__device__ __forceinline__ int plain_class(const SweepArgs& A, int i, int j, int k, long long n)
+{
+    const Geo& g = A.g;
+    const RT* p = (const RT*)A.P + 4 * g.N;
+    const int pos[3] = {i, j, k};
+    const int nd[3] = {g.nx, g.ny, g.nz};
+    const long long st[3] = {1, g.nx, (long long)g.nx * g.ny};
+    RT th = (RT)0;
+    for (int d = 0; d < 3; ++d) {
+        const int m = pos[d];
+        if (!g.per[d] && (m == 0 || m == nd[d] - 1)) continue;
+        const RT pm = p[n + (long long)(wrapi(m - 1, nd[d]) - m) * st[d]];
+        const RT pp = p[n + (long long)(wrapi(m + 1, nd[d]) - m) * st[d]];
+        const RT p0 = p[n];
+        th += fabs(-pm + (RT)2 * p0 - pp) / (pm + (RT)2 * p0 + pp);
+    }
+    return th <= (RT)A.ph.th1 ? 0 : (th <= (RT)A.ph.th2 ? 1 : 2);
+}
+
+constexpr int MLP_ROW = 56;  // bf16 row stride of the feature tile (conflict-free fragment loads)
+
+// 128 nodes along x per CTA (4 warps x 32 rows); grid (x-chunks of 128, ny, nz)
+template <class RT>
+__global__ void __launch_bounds__(128) k_sensor_mlp(SweepArgs A, MlpArgs W)
+{
+    __shared__ __align__(16) uint16_t sx[128 * MLP_ROW];
+    __shared__ __align__(16) uint16_t sw1[32 * MLP_ROW];
+    __shared__ __align__(16) uint16_t sw2[32 * 40];
+    __shared__ __align__(16) uint16_t sw3[8 * 40];
+    __shared__ float sb[32 + 32 + 8];
+    __shared__ unsigned char sbad[128];
+    const Geo& g = A.g;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int i = blockIdx.x * 128 + t, j = blockIdx.y, k = blockIdx.z;
+    const long long n = (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
+    const bool own = i < g.nx;
+    // weights and biases to shared memory
+    for (int e = t; e < 32 * MLP_KP; e += 128) sw1[(e / MLP_KP) * MLP_ROW + e % MLP_KP] = W.w1[e];
+    for (int e = t; e < 32 * 32; e += 128) sw2[(e / 32) * 40 + e % 32] = W.w2[e];
+    for (int e = t; e < 8 * 32; e += 128) sw3[(e / 32) * 40 + e % 32] = W.w3[e];
+    for (int e = t; e < 72; e += 128) sb[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
+    // features of this thread's node
+    {
+        float f[MLP_IN];
+        bool bad = !own;
+        if (own) {
+            mlp_features<RT>(A, i, j, k, n, f);
+#pragma unroll
+            for (int e = 0; e < MLP_IN; ++e) bad |= !isfinite(f[e]);
+        }
+        uint32_t* row = reinterpret_cast<uint32_t*>(sx + t * MLP_ROW);
+#pragma unroll
+        for (int e = 0; e < MLP_KP; e += 2) {
+            const float a = (!bad && e < MLP_IN) ? f[e] : 0.0f;
+            const float b = (!bad && e + 1 < MLP_IN) ? f[e + 1] : 0.0f;
+            row[e / 2] = pack_bf16x2(a, b);
+        }
+        sbad[t] = bad;
+    }
+    __syncthreads();
+    const int gid = lane >> 2, tig = lane & 3;
+    int cls_row[2][2];  // [m-tile][row half] class (-1: use the plain sensor)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = warp * 32 + mt * 16 + gid;  // rows r0 and r0 + 8
+        // layer 1: [16 x 48] x [48 x 32]
+        float h1[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) h1[nt][e] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 3; ++ks) {
+            uint32_t a[4];
+            const int c = ks * 16 + tig * 2;
+            a[0] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c);
+            a[1] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c);
+            a[2] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c + 8);
+            a[3] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c + 8);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                uint32_t b[2];
+                const int nn = nt * 8 + gid;
+                b[0] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c);
+                b[1] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c + 8);
+                mma_bf16_16816(h1[nt], a, b);
+            }
+        }
+        // bias + ReLU, and the accumulator layout becomes the next A operand
+        uint32_t a2[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const float bb0 = sb[nt * 8 + tig * 2], bb1 = sb[nt * 8 + tig * 2 + 1];
+            const uint32_t lo = pack_bf16x2(fmaxf(h1[nt][0] + bb0, 0.0f), fmaxf(h1[nt][1] + bb1, 0.0f));
+            const uint32_t hi = pack_bf16x2(fmaxf(h1[nt][2] + bb0, 0.0f), fmaxf(h1[nt][3] + bb1, 0.0f));
+            a2[nt >> 1][(nt & 1) * 2 + 0] = lo;
+            a2[nt >> 1][(nt & 1) * 2 + 1] = hi;
+        }
+        // layer 2: [16 x 32] x [32 x 32]
+        float h2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) h2[nt][e] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int c = ks * 16 + tig * 2;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                uint32_t b[2];
+                const int nn = nt * 8 + gid;
+                b[0] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c);
+                b[1] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c + 8);
+                mma_bf16_16816(h2[nt], a2[ks], b);
+            }
+        }
+        uint32_t a3[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const float bb0 = sb[32 + nt * 8 + tig * 2], bb1 = sb[32 + nt * 8 + tig * 2 + 1];
+            const uint32_t lo = pack_bf16x2(fmaxf(h2[nt][0] + bb0, 0.0f), fmaxf(h2[nt][1] + bb1, 0.0f));
+            const uint32_t hi = pack_bf16x2(fmaxf(h2[nt][2] + bb0, 0.0f), fmaxf(h2[nt][3] + bb1, 0.0f));
+            a3[nt >> 1][(nt & 1) * 2 + 0] = lo;
+            a3[nt >> 1][(nt & 1) * 2 + 1] = hi;
+        }
+        // layer 3: [16 x 32] x [32 x 8] (3 logits used)
+        float lg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int c = ks * 16 + tig * 2;
+            uint32_t b[2];
+            b[0] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c);
+            b[1] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c + 8);
+            mma_bf16_16816(lg, a3[ks], b);
+        }
+        // logits of row r0 (lg[0..1]) and r0+8 (lg[2..3]) sit in columns 2 tig, 2 tig + 1:
+        // gather columns 0, 1, 2 at tig == 0
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const float c0 = __shfl_sync(0xffffffffu, lg[2 * half], lane & ~3);
+            const float c1 = __shfl_sync(0xffffffffu, lg[2 * half + 1], lane & ~3);
+            const float c2 = __shfl_sync(0xffffffffu, lg[2 * half], (lane & ~3) + 1);
+            const float l0 = c0 + sb[64], l1 = c1 + sb[65], l2 = c2 + sb[66];
+            const float mx = fmaxf(l0, fmaxf(l1, l2));
+            const float z = __expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx);
+            const int arg = l0 >= l1 ? (l0 >= l2 ? 0 : 2) : (l1 >= l2 ? 1 : 2);
+            cls_row[mt][half] = (1.0f / z >= W.conf_min && isfinite(z)) ? arg : -1;
+        }
+    }
+    __syncthreads();
+    // one writer per row: lane with tig == 0 owns rows r0 and r0 + 8 of each m-tile
+    __shared__ int scls[128];
+    if (tig == 0) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = warp * 32 + mt * 16 + gid;
+            scls[r0] = cls_row[mt][0];
+            scls[r0 + 8] = cls_row[mt][1];
+        }
+    }
+    __syncthreads();
+    if (own) {
+        int c = scls[t];
+        if (c < 0 || sbad[t]) {
+            c = plain_class<RT>(A, i, j, k, n);
+            if (W.fallbacks) atomicAdd(W.fallbacks, 1ull);
+        }
+        A.cls_io[n] = (uint8_t)c;
+    }
+}
+
+// the 42 features of every node (for training data and tests), [42][N] float
+template <class RT>
+__global__ void k_mlp_features(SweepArgs A, float* out)
+{
+    const Geo& g = A.g;
+    const uint3 vb = blockIdx;
+    NODE_IJK(g)
+    {
+        float f[MLP_IN];
+        mlp_features<RT>(A, i, j, k, n, f);
+#pragma unroll
+        for (int e = 0; e < MLP_IN; ++e) out[(long long)e * g.N + n] = f[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Steger-Warming split fluxes at one node (Eq. 20-30, Eq. 23 as corrected).
 // With s = l4 + l5 and dl = l5 - l4 the corrected Eq. 23 reads
 //   f0 = a (2(g-1) l1 + s),  f_i = u_i f0 + a c dl k_i,
@@ -1320,6 +1585,8 @@ __global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A) { sweep_t_body<R, 
 // list (item -> block by binary search over the per-block tile prefix sums,
 // then the block-local tile coordinates) with a grid-size stride.
 // ---------------------------------------------------------------------------
+static_assert(sizeof(SweepArgs) % sizeof(int) == 0, "argument record copied as words");
+
 struct BatchMap {
     const SweepArgs* tbl;  // [nb] per-block arguments of this stage
     const int* prefix;     // [nb+1] tile prefix sums for this kernel kind
@@ -1343,12 +1610,25 @@ __device__ __forceinline__ int batch_find(const BatchMap& m, int item, uint3* v)
     return lo;
 }
 
+// The block's argument record is copied to shared memory when a CTA moves to
+// a new block (consecutive items of a CTA mostly stay in one block), so the
+// bodies read it from shared memory instead of global memory.
 #define BATCH_LOOP(BODY, SYNC)                                                                        \
+    __shared__ __align__(16) SweepArgs sA;                                                            \
+    constexpr int AW = (int)(sizeof(SweepArgs) / sizeof(int));                                        \
+    int cached = -1;                                                                                  \
     const int total = __ldg(m.prefix + m.nb);                                                         \
     for (int item = blockIdx.x; item < total; item += gridDim.x) {                                    \
         uint3 v;                                                                                      \
         const int b = batch_find(m, item, &v);                                                        \
-        BODY(m.tbl[b], v);                                                                            \
+        if (b != cached) {                                                                            \
+            __syncthreads();                                                                          \
+            const int* src = reinterpret_cast<const int*>(m.tbl + b);                                 \
+            for (int w = threadIdx.x; w < AW; w += blockDim.x) reinterpret_cast<int*>(&sA)[w] = src[w];\
+            __syncthreads();                                                                          \
+            cached = b;                                                                               \
+        }                                                                                             \
+        BODY(sA, v);                                                                                  \
         if (SYNC) __syncthreads();                                                                    \
     }
 

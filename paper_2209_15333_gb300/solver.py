@@ -25,6 +25,17 @@ def _ptr(a):
     return C.c_void_p(a.ctypes.data), 0
 
 
+def to_bf16_bits(a):
+    """float32 -> bf16 bit patterns (uint16), round to nearest even."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+    return np.ascontiguousarray(r)
+
+
+def from_bf16_bits(b):
+    return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
 class Solver:
     def __init__(self, shape, metrics, *, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), stream=None, **params):
         """shape = (nx, ny, nz); metrics: numpy/torch (10,), (10, ny, nx) or (10, nz, ny, nx)."""
@@ -122,6 +133,29 @@ class Solver:
         k, p = C.c_int(), C.c_int()
         L.check(L.lib().cfd_get_sweep_variant(self.ctx, dir, C.byref(k), C.byref(p)), self.ctx)
         return k.value, p.value
+
+    def set_sensor_mlp(self, w1, w2, w3, b1, b2, b3, conf_min=0.0):
+        """Learned sensor weights (any float arrays; rounded to bf16 here):
+        w1 [32,42], w2 [32,32], w3 [3,32], biases [32], [32], [3]."""
+        if w1 is None:
+            L.check(L.lib().cfd_set_sensor_mlp(self.ctx, None, None, 0.0), self.ctx)
+            return
+        w = np.concatenate([np.asarray(a, np.float32).ravel() for a in (w1, w2, w3)])
+        self._mlp_w = to_bf16_bits(w)
+        self._mlp_b = np.concatenate([np.asarray(a, np.float32).ravel() for a in (b1, b2, b3)]).astype(np.float32)
+        L.check(L.lib().cfd_set_sensor_mlp(self.ctx, C.c_void_p(self._mlp_w.ctypes.data),
+                                           C.c_void_p(self._mlp_b.ctypes.data), float(conf_min)), self.ctx)
+
+    def sensor_features(self, block=0):
+        shp = self.shapes[block] if hasattr(self, "shapes") else self.shape
+        out = np.empty((42,) + shp, dtype=np.float32)
+        L.check(L.lib().cfd_sensor_features(self.ctx, block, C.c_void_p(out.ctypes.data), 0), self.ctx)
+        return out
+
+    def sensor_fallbacks(self):
+        c = C.c_ulonglong()
+        L.check(L.lib().cfd_sensor_fallbacks(self.ctx, C.byref(c)), self.ctx)
+        return c.value
 
     def launches(self):
         return L.lib().cfd_launch_count(self.ctx)

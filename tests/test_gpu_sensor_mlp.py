@@ -1,0 +1,123 @@
+"""Learned shock sensor: features, tensor-core MLP and plain-sensor fallback.
+
+The features are checked against a numpy evaluation of their definition; the
+MLP classes against a numpy forward pass with the same roundings (features
+and hidden activations to bf16, FP32 accumulation), on nodes whose logit
+margin exceeds the accumulation-order tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_2209_15333_gb300 import cases
+
+from gpu_helpers import turbulence_field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_15333_gb300 import build
+    build.build()
+
+
+def features_numpy(U, gamma, per):
+    """42 features per node from the definition (float64 here)."""
+    rho = U[0]
+    u, v, w = U[1] / rho, U[2] / rho, U[3] / rho
+    p = (gamma - 1.0) * (U[4] - 0.5 * rho * (u * u + v * v + w * w))
+    out = []
+    for d in range(3):
+        ax = 2 - d                      # arrays are [z][y][x]
+        n = p.shape[ax]
+        idx = np.arange(n)
+        for q in (p, rho):
+            vals = []
+            for t in range(7):
+                j = idx + t - 3
+                j = j % n if per[d] else np.clip(j, 0, n - 1)
+                vals.append(np.take(q, j, axis=ax))
+            for t in range(6):
+                out.append((vals[t + 1] - vals[t]) / vals[3])
+            out.append((vals[2] - 2 * vals[3] + vals[4]) / (vals[2] + 2 * vals[3] + vals[4]))
+    return np.stack(out)
+
+
+def bf16(a):
+    from paper_2209_15333_gb300.solver import from_bf16_bits, to_bf16_bits
+    return from_bf16_bits(to_bf16_bits(np.asarray(a, np.float32)))
+
+
+def mlp_numpy(F, W):
+    x = bf16(F.reshape(42, -1).T)
+    h = np.maximum(x @ bf16(W["w1"]).T + W["b1"], 0.0)
+    h = np.maximum(bf16(h) @ bf16(W["w2"]).T + W["b2"], 0.0)
+    return bf16(h) @ bf16(W["w3"]).T + W["b3"]
+
+
+def random_weights(seed, scale=10.0):
+    rng = np.random.default_rng(seed)
+    # features are O(0.01-0.3): a wide first layer makes several classes occur
+    return dict(w1=rng.normal(0, scale, (32, 42)), w2=rng.normal(0, 0.5, (32, 32)), w3=rng.normal(0, 0.5, (3, 32)),
+                b1=rng.normal(0, 0.1, 32), b2=rng.normal(0, 0.1, 32), b3=rng.normal(0, 0.1, 3))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_features_match_definition(precision):
+    from paper_2209_15333_gb300.solver import Solver
+    sh = (37, 19, 23)
+    U = turbulence_field(sh, 91)
+    bc = dict(bc_lo=(3, 0, 0), bc_hi=(3, 0, 0))
+    with Solver(sh, cases.uniform_metrics(*sh), precision=precision, scheme=3, Re=100.0, **bc) as s:
+        s.set_state(U)
+        Ub = s.get_state()
+        F = s.sensor_features()
+    ref = features_numpy(Ub, 1.4, (0, 1, 1))
+    tol = 1e-5 if precision else 1e-6
+    assert np.abs(F - ref).max() <= tol * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mlp_classes_match_numpy_forward_pass(precision):
+    from paper_2209_15333_gb300.solver import Solver
+    sh = (40, 24, 20)
+    U = turbulence_field(sh, 92)
+    W = random_weights(5)
+    with Solver(sh, cases.uniform_metrics(*sh), precision=precision, scheme=3, Re=100.0) as s:
+        s.set_state(U)
+        F = s.sensor_features()
+        s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=0.0)
+        s.rhs()
+        got = s.flags().ravel()
+        assert s.sensor_fallbacks() == 0
+    logits = mlp_numpy(F, W)
+    want = logits.argmax(axis=1)
+    srt = np.sort(logits, axis=1)
+    margin = srt[:, -1] - srt[:, -2]
+    sure = margin > 1e-2 * (1.0 + np.abs(logits).max(axis=1))
+    assert sure.mean() > 0.9
+    assert np.array_equal(got[sure], want[sure])
+    assert len(np.unique(want)) >= 2
+
+
+def test_mlp_fallback_to_plain_sensor():
+    from paper_2209_15333_gb300.solver import Solver
+    sh = (32, 16, 16)
+    U = turbulence_field(sh, 93)
+    kw = dict(scheme=3, Re=100.0, theta1=0.004, theta2=0.012)
+    with Solver(sh, cases.uniform_metrics(*sh), **kw) as s:
+        s.set_state(U)
+        s.rhs()
+        plain = s.flags()
+        W = random_weights(6, scale=0.5)
+        # small logits: no softmax probability rounds to 1, so every node falls back
+        s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=1.0)
+        s.rhs()
+        assert np.array_equal(s.flags(), plain)
+        assert s.sensor_fallbacks() == plain.size
+        s.set_sensor_mlp(None, None, None, None, None, None)
+        s.rhs()
+        assert np.array_equal(s.flags(), plain)
