@@ -248,7 +248,9 @@ typedef struct {
     int r;
     double c[4][4];      /* c[k][l]: q_k(1/2) = sum_l c[k][l] a[k+l] */
     double d[4];
-    double Q[4][4][4];   /* beta_k = sum_{l,m} Q[k][l][m] a[k+l] a[k+m] */
+    double P[4][4][4];   /* P[k][p][l]: coefficient of x^p of q_k = sum_l P[k][p][l] a[k+l] */
+    double B[4][4];      /* beta = sum_{p,q >= 1} B[p][q] coef_p coef_q */
+    double Q[4][4][4];   /* the same indicator as a quadratic form in a (exported for tests) */
     double cfull[7];
 } weno_tab;
 
@@ -325,7 +327,9 @@ static int build_tab(int r, weno_tab* T)
             for (int p = 0; p < r; ++p) s += pow(0.5, p) * C[p * r + l];
             T->c[k][l] = s;
         }
-        double B[4][4];
+        for (int p = 0; p < r; ++p)
+            for (int l = 0; l < r; ++l) T->P[k][p][l] = C[p * r + l];
+        double (*B)[4] = T->B;
         for (int p = 0; p < r; ++p)
             for (int q = 0; q < r; ++q) {
                 double s = 0.0;
@@ -386,14 +390,28 @@ int orc_weno_tables(int r, double* c, double* d, double* Q, double* cfull)
     return 0;
 }
 
+/* beta_k from its definition: the derivative coefficients of the
+   sub-stencil polynomial first, then the integrals of the squared
+   derivatives (a[0..r-1] are the sub-stencil values) */
+static double beta_of(const weno_tab* T, int k, const double* a)
+{
+    int r = T->r;
+    double co[4];
+    for (int p = 1; p < r; ++p) {
+        double s = 0.0;
+        for (int l = 0; l < r; ++l) s += T->P[k][p][l] * a[l];
+        co[p] = s;
+    }
+    double b = 0.0;
+    for (int p = 1; p < r; ++p)
+        for (int q = 1; q < r; ++q) b += T->B[p][q] * co[p] * co[q];
+    return b;
+}
+
 double orc_weno_beta(int r, int k, const double* a)
 {
     ensure_tabs();
-    const weno_tab* T = r == 3 ? &g_w5 : &g_w7;
-    double b = 0.0;
-    for (int l = 0; l < r; ++l)
-        for (int m = 0; m < r; ++m) b += T->Q[k][l][m] * a[l] * a[m];
-    return b;
+    return beta_of(r == 3 ? &g_w5 : &g_w7, k, a);
 }
 
 /* a[0..2r-2] = f_{j-r+1} .. f_{j+r-1}; value at j+1/2 */
@@ -406,9 +424,7 @@ double orc_weno(int r, const double* a, const int* mask, double eps, double* ome
         double s = 0.0;
         for (int l = 0; l < r; ++l) s += T->c[k][l] * a[k + l];
         q[k] = s;
-        double b = 0.0;
-        for (int l = 0; l < r; ++l)
-            for (int m = 0; m < r; ++m) b += T->Q[k][l][m] * a[k + l] * a[k + m];
+        double b = beta_of(T, k, a + k);
         alpha[k] = (mask && mask[k]) ? 0.0 : T->d[k] / ((eps + b) * (eps + b));
         sum += alpha[k];
     }
