@@ -414,8 +414,13 @@ double orc_weno_beta(int r, int k, const double* a)
     return beta_of(r == 3 ? &g_w5 : &g_w7, k, a);
 }
 
-/* a[0..2r-2] = f_{j-r+1} .. f_{j+r-1}; value at j+1/2 */
-double orc_weno(int r, const double* a, const int* mask, double eps, double* omega_out)
+/* a[0..2r-2] = f_{j-r+1} .. f_{j+r-1}; value at j+1/2.  Sec. 2.2.3:
+   candidates q_k, indicators beta_k, alpha_k = d_k/(eps + beta_k)^2,
+   omega_k = alpha_k / sum alpha.  The indicators are taken of a/s: beta is
+   quadratic in the values, so beta_k(a/s) = beta_k(a)/s^2 (reading R23: the
+   paper's fluxes carry the face area |grad d|/J, and eps is meant for the
+   flux per unit area, whose size does not depend on the grid's scaling). */
+double orc_weno(int r, const double* a, const int* mask, double eps, double fs, double* omega_out)
 {
     ensure_tabs();
     const weno_tab* T = r == 3 ? &g_w5 : &g_w7;
@@ -424,7 +429,7 @@ double orc_weno(int r, const double* a, const int* mask, double eps, double* ome
         double s = 0.0;
         for (int l = 0; l < r; ++l) s += T->c[k][l] * a[k + l];
         q[k] = s;
-        double b = beta_of(T, k, a + k);
+        double b = beta_of(T, k, a + k) / (fs * fs);
         alpha[k] = (mask && mask[k]) ? 0.0 : T->d[k] / ((eps + b) * (eps + b));
         sum += alpha[k];
     }
@@ -579,9 +584,10 @@ int orc_apply_bc(const orc_params* P, const double* metrics, double* U, double t
 /* ------------------------------------------------------------------ */
 
 /* inviscid flux at interface j+1/2 of one line (NODAL or FSP metrics) */
+/* fs: face-area scale sigma_{j+1/2} of the interface (R23) */
 static void interface_flux(const orc_params* P, int n, int periodic, int j,
                            const double* fp /* [n][5] */, const double* fm, const unsigned char* lcls,
-                           double out[5])
+                           double fs, double out[5])
 {
     int scheme = P->scheme;
     int masked_edge = !periodic && (j - 3 < 0 || j + 4 > n - 1);
@@ -617,8 +623,8 @@ static void interface_flux(const orc_params* P, int n, int periodic, int j,
             vp = orc_ud7(a);
             vm = orc_ud7(b);
         } else if (use == 1) {
-            vp = orc_weno(4, a, NULL, P->weno_eps, NULL);
-            vm = orc_weno(4, b, NULL, P->weno_eps, NULL);
+            vp = orc_weno(4, a, NULL, P->weno_eps, fs, NULL);
+            vm = orc_weno(4, b, NULL, P->weno_eps, fs, NULL);
         } else {
             int mp[3], mm[3];
             for (int k = 0; k < 3; ++k) {
@@ -629,8 +635,8 @@ static void interface_flux(const orc_params* P, int n, int periodic, int j,
                     if (!inrange_m[1 + k + l]) mm[k] = 1;
                 }
             }
-            vp = orc_weno(3, a + 1, mp, P->weno_eps, NULL);
-            vm = orc_weno(3, b + 1, mm, P->weno_eps, NULL);
+            vp = orc_weno(3, a + 1, mp, P->weno_eps, fs, NULL);
+            vm = orc_weno(3, b + 1, mm, P->weno_eps, fs, NULL);
         }
         out[q] = vp + vm;
     }
@@ -694,9 +700,16 @@ static void inviscid_direction(const orc_params* P, const double* met, const dou
                 }
                 /* local line of the 8 stencil nodes j-3..j+4: interface at local 3+1/2,
                    whose stencil stays inside the local line */
-                interface_flux(P, 8, 1, 3, lfp, lfm, lc, out);
+                double fs = sqrt(ai[0] * ai[0] + ai[1] * ai[1] + ai[2] * ai[2]);
+                interface_flux(P, 8, 1, 3, lfp, lfm, lc, fs, out);
             } else {
-                interface_flux(P, nd, periodic, periodic ? wrap(j, nd) : j, fp, fm, lcls, out);
+                /* R23: sigma_{j+1/2} = (sigma_j + sigma_{j+1})/2, sigma = |alpha| (Eq. 22) */
+                int ja = wrap(j, nd), jb = wrap(j + 1, nd);
+                double fs = 0.5 * (sqrt(alpha[3 * ja] * alpha[3 * ja] + alpha[3 * ja + 1] * alpha[3 * ja + 1] +
+                                        alpha[3 * ja + 2] * alpha[3 * ja + 2]) +
+                                   sqrt(alpha[3 * jb] * alpha[3 * jb] + alpha[3 * jb + 1] * alpha[3 * jb + 1] +
+                                        alpha[3 * jb + 2] * alpha[3 * jb + 2]));
+                interface_flux(P, nd, periodic, periodic ? wrap(j, nd) : j, fp, fm, lcls, fs, out);
             }
             for (int q = 0; q < NV; ++q) fh[NV * (j + 1) + q] = out[q];
         }

@@ -64,8 +64,12 @@ void orc_sw_split(double gamma, double rho, double u, double v, double w, double
 double orc_ud7(const double a[7]);
 int orc_weno_tables(int r, double* c /* [r][r] */, double* d /* [r] */, double* Q /* [r][r][r] */,
                     double* cfull /* [2r-1] */);
+/* WENO value at j+1/2 from a[0..2r-2] = f_{j-r+1..j+r-1}.  The
+   smoothness indicators are measured on a/s (s > 0: the face-area scale of
+   the flux, 1 for a plain function), so the weights do not depend on the
+   scaling of the flux. */
 double orc_weno(int r, const double* a /* [2r-1] */, const int* mask /* [r] or NULL */, double eps,
-                double* omega_out /* [r] or NULL */);
+                double s, double* omega_out /* [r] or NULL */);
 double orc_weno_beta(int r, int k, const double* a /* [r] */);
 int orc_central_deriv(int order, int n, int periodic, const double* g, double* dg);
 int orc_midpoint_weights(double* w /* [8] */);

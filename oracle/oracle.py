@@ -56,7 +56,7 @@ def lib():
         L.orc_ud7.argtypes = [_dp]
         L.orc_ud7.restype = C.c_double
         L.orc_weno_tables.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
-        L.orc_weno.argtypes = [C.c_int, _dp, C.POINTER(C.c_int), C.c_double, _dp]
+        L.orc_weno.argtypes = [C.c_int, _dp, C.POINTER(C.c_int), C.c_double, C.c_double, _dp]
         L.orc_weno.restype = C.c_double
         L.orc_weno_beta.argtypes = [C.c_int, C.c_int, _dp]
         L.orc_weno_beta.restype = C.c_double
@@ -196,7 +196,7 @@ def weno_tables(r):
     return c, d, Q, cf
 
 
-def weno(r, a, mask=None, eps=1e-6, return_omega=False):
+def weno(r, a, mask=None, eps=1e-6, return_omega=False, scale=1.0):
     a = _f64(a)
     assert a.size == 2 * r - 1
     om = np.empty(r)
@@ -204,7 +204,7 @@ def weno(r, a, mask=None, eps=1e-6, return_omega=False):
     if mask is not None:
         m = (C.c_int * r)(*[int(x) for x in mask])
         mptr = C.cast(m, C.POINTER(C.c_int))
-    v = lib().orc_weno(r, _ptr(a), mptr, eps, _ptr(om))
+    v = lib().orc_weno(r, _ptr(a), mptr, eps, scale, _ptr(om))
     return (v, om) if return_omega else v
 
 

@@ -102,10 +102,16 @@ def _vortex_dudt(n, nz):
     return (Us[0] - 8 * Us[1] + 8 * Us[2] - Us[3]) / (12 * d)
 
 
-@pytest.mark.parametrize("scheme,order", [("UD7", 7), ("WENO7", 7), ("WENO5", 5)])
-def test_isentropic_vortex_order(orc, scheme, order):
+# The WENO weights only approach the linear weights once the smoothness
+# indicators (measured on the flux per unit face area) fall well below
+# eps = 1e-6, so the WENO schemes reach their order on finer grids than UD7;
+# at the vortex's critical points Jiang-Shu weights converge slowly, so
+# WENO7 is held to order - 1.5 on its finest pair.
+@pytest.mark.parametrize("scheme,order,ns,slack", [("UD7", 7, (32, 64, 128), 1.2),
+                                                  ("WENO7", 7, (128, 256, 512), 1.5),
+                                                  ("WENO5", 5, (128, 256, 512), 1.2)])
+def test_isentropic_vortex_order(orc, scheme, order, ns, slack):
     errs = []
-    ns = (32, 64, 128)
     for n in ns:
         U, met, Ma, _, _ = cases.isentropic_vortex(n, nz=1, mean=VORTEX_MEAN, beta=VORTEX_BETA)
         prim = orc.primitives(orc.Case(n, n, 1, Ma=Ma), U)
@@ -115,7 +121,7 @@ def test_isentropic_vortex_order(orc, scheme, order):
         L = orc.rhs(c, M, U)
         errs.append(np.abs(L - _vortex_dudt(n, 1)).max())
     rates = [math.log(errs[i] / errs[i + 1], 2) for i in range(len(errs) - 1)]
-    assert rates[-1] > order - 1.2, (errs, rates)
+    assert rates[-1] > order - slack, (errs, rates)
 
 
 # ---- Sod shock tube against the exact Riemann solution ----
@@ -209,6 +215,29 @@ def test_sod_against_exact(orc, scheme):
         assert rho.max() <= 1.0 + 0.03 and rho.min() >= 0.125 - 0.03
     assert errs[0] > errs[1] > errs[2]
     assert math.log(errs[0] / errs[2], 4) > 0.6, errs
+
+
+@pytest.mark.parametrize("scheme", ["WENO5", "WENO7", "HYBRID"])
+def test_rhs_invariant_to_coordinate_scaling(orc, scheme):
+    """Reading R23: the same 1-D Sod state on grids whose transverse cell
+    sizes differ (J and the split fluxes scale with them) gives the same
+    L(U) = J R: the shock-capturing weights do not depend on the arbitrary
+    scaling of the computational coordinates."""
+    n = 101
+    U, met, Ma, x = cases.shock_tube(n)
+    Ls = []
+    for hy, hz in ((1.0, 1.0), (1e-3, 2e-2), (5e2, 1e-4)):
+        m = met.copy()
+        m[4], m[8] = 1.0 / hy, 1.0 / hz
+        m[9] = met[9] / (hy * hz)
+        M = cases.expand_metrics(m, (1, 1, n))
+        c = orc.Case(n, 1, 1, Re=0.0, Ma=Ma, gamma=G, scheme=getattr(orc, scheme),
+                     bc_lo=(orc.BC_OUTFLOW, 0, 0), bc_hi=(orc.BC_OUTFLOW, 0, 0))
+        Ls.append(orc.rhs(c, M, orc.apply_bc(c, M, U)))
+    scale = np.abs(Ls[0]).max()
+    assert scale > 1.0
+    for L in Ls[1:]:
+        assert np.abs(L - Ls[0]).max() < 1e-12 * scale
 
 
 def _kinetic_rate(U, L):

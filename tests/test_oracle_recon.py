@@ -164,3 +164,22 @@ def test_midpoint_weights(orc):
     x = np.arange(-3, 5, dtype=float)
     for deg in range(8):
         assert abs(w @ x ** deg - 0.5 ** deg) <= 1e-12
+
+
+@pytest.mark.parametrize("r", [3, 4])
+def test_weno_invariant_to_flux_scale(orc, r):
+    """Reading R23: the weights are measured on the flux per unit face area,
+    so scaling the values and the face scale together scales the result and
+    leaves the weights unchanged (the values straddle a jump, where the
+    weights are far from linear)."""
+    a = np.array([1.0, 1.02, 0.97, 1.1, 3.0, 3.05, 2.9])[:2 * r - 1]
+    v1, w1 = orc.weno(r, a, return_omega=True)
+    for lam in (1e-7, 1e-3, 1e4):
+        v2, w2 = orc.weno(r, lam * a, return_omega=True, scale=lam)
+        assert abs(v2 / lam - v1) < 1e-14 * abs(v1)
+        assert np.allclose(w2, w1, rtol=1e-13, atol=0)
+    # the unscaled call on tiny values degenerates to the linear weights
+    _, d, _, _ = orc.weno_tables(r)
+    _, w3 = orc.weno(r, 1e-7 * a, return_omega=True)
+    assert np.allclose(w3, d, atol=1e-3)
+    assert not np.allclose(w1, d, atol=1e-2)
