@@ -358,14 +358,69 @@ def ramp_inflow(y_rel, Ma, gamma=1.4, Tw=2.8, Pr=0.72, delta=1.0):
     return rho, ub, np.zeros_like(ub), np.zeros_like(ub), p
 
 
+def oblique_shock(Ma, angle_deg, gamma=1.4):
+    """Weak attached oblique shock from a wedge of the given angle in a
+    uniform stream (rho = T = U = 1, p = 1/(gamma Ma^2)): the theta-beta-Mach
+    relation solved by bisection for the weak shock angle beta, then the
+    normal-shock jump conditions on the normal Mach number M sin(beta).
+    Returns (beta, rho2, speed2, p2)."""
+    theta = math.radians(angle_deg)
+
+    def turn(b):
+        return math.atan(2.0 / math.tan(b) * (Ma * Ma * math.sin(b) ** 2 - 1.0)
+                         / (Ma * Ma * (gamma + math.cos(2.0 * b)) + 2.0))
+
+    lo, hi = math.asin(1.0 / Ma), 0.5 * math.pi
+    grid = np.linspace(lo, hi, 4001)[1:-1]
+    bmax = grid[int(np.argmax([turn(b) for b in grid]))]
+    if turn(bmax) < theta:
+        raise ValueError("detached shock: no weak solution for this angle and Mach number")
+    hi = bmax
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if turn(mid) < theta:
+            lo = mid
+        else:
+            hi = mid
+    beta = 0.5 * (lo + hi)
+    mn2 = (Ma * math.sin(beta)) ** 2
+    rho2 = (gamma + 1.0) * mn2 / ((gamma - 1.0) * mn2 + 2.0)
+    p2 = (1.0 + 2.0 * gamma / (gamma + 1.0) * (mn2 - 1.0)) / (gamma * Ma * Ma)
+    vt = math.cos(beta)
+    vn = math.sin(beta) / rho2
+    return beta, rho2, math.hypot(vt, vn), p2
+
+
 def ramp_case(nx, ny, nz, angle_deg, Ma, gamma=1.4, Tw=2.8, Pr=0.72):
-    """Ramp grid plus the profile initial condition and the inflow profile."""
+    """Ramp grid plus the initial condition and the inflow profile.
+
+    Initial field: the inviscid solution of the ramp (the free stream
+    upstream of the weak oblique shock from the corner, the uniform
+    post-shock state parallel to the ramp face below it) with a boundary
+    layer of the inflow profile's shape in the wall distance along each
+    vertical grid line: u/u_e = tanh(3 d), Crocco-Busemann temperature
+    between T_wall and the local edge state, uniform pressure across it.
+    Starting from the inviscid solution avoids the strong starting vortex
+    that an impulsive start into the ramp face produces at Mach 6."""
     met2, X2, Y2, z, wx = ramp_grid(nx, ny, nz, angle_deg)
     yw = Y2[0:1, :]
     yrel = Y2 - yw
-    rho, u, v, w, p = ramp_inflow(yrel, Ma, gamma, Tw, Pr)
+    beta, rho2, q2, p2 = oblique_shock(Ma, angle_deg, gamma)
+    pinf = 1.0 / (gamma * Ma * Ma)
+    behind = (X2 > 0.0) & (Y2 < X2 * math.tan(beta))
+    a = np.where(behind, math.radians(angle_deg), 0.0)
+    qe = np.where(behind, q2, 1.0)
+    pe = np.where(behind, p2, pinf)
+    Te = np.where(behind, gamma * Ma * Ma * p2 / rho2, 1.0)
+    Me2 = qe * qe * Ma * Ma / Te               # c^2 = T/Ma^2
+    r = Pr ** (1.0 / 3.0)
+    Tr = Te * (1.0 + r * (gamma - 1.0) / 2.0 * Me2)
+    f = np.tanh(3.0 * yrel)
+    T = Tw + (Tr - Tw) * f - (Tr - Te) * f * f
+    rho = gamma * Ma * Ma * pe / T
+    u, v = qe * f * np.cos(a), qe * f * np.sin(a)
     shp = (nz, ny, nx)
-    U = conserved(*(np.broadcast_to(a[None], shp) for a in (rho, u, v, w, p)), gamma)
+    U = conserved(*(np.broadcast_to(q[None], shp) for q in (rho, u, v, np.zeros_like(u), pe)), gamma)
     inflow = np.stack(ramp_inflow(yrel[:, 0], Ma, gamma, Tw, Pr))
     return dict(U=U, metrics2d=met2, inflow=np.ascontiguousarray(inflow), wall_x=wx, wall_z=z,
-                X=X2, Y=Y2)
+                X=X2, Y=Y2, shock_angle=beta)

@@ -401,7 +401,7 @@ static cfd_status launch_sweep_dir(cfd_ctx* ctx, SweepArgs& A, int kind, int par
         A.seg_len = param;
         const long long nseg = (hi - lo + param - 1) / param;
         const long long warps = (long long)((g.nx + 31) / 32) * nother * nseg;
-        k_sweep_s<R, DIR, EP><<<(unsigned)((warps + 3) / 4), 128, 4 * 80 * 32 * sizeof(R), ctx->stream>>>(A);
+        k_sweep_s<R, DIR, EP><<<(unsigned)((warps + 3) / 4), 128, stream_smem_bytes<R>(), ctx->stream>>>(A);
     } else {
         dim3 grid((g.nx + 31) / 32, nother, (hi - lo + param - 1) / param);
         if (param == 16)
@@ -442,7 +442,7 @@ template <class R, int DIR, int EP>
 static cudaError_t set_sweep_attrs()
 {
     cudaError_t e = cudaFuncSetAttribute(k_sweep_s<R, DIR, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(4 * 80 * 32 * sizeof(R)));
+                                         (int)stream_smem_bytes<R>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<R, 16>());
@@ -1301,7 +1301,7 @@ static cudaError_t setup(int dev, unsigned char** out)
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess) return e;
-        const int smem = 4 * 80 * 32 * (int)sizeof(double);
+        const int smem = (int)stream_smem_bytes<double>();
         e = cudaFuncSetAttribute(k_sweep_s<double, 1, EP_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_sweep_s<double, 2, EP_FINAL_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1426,7 +1426,7 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
         else k_sweep_x<double, 128, EP_STORE><<<gr, 128, 0, s>>>(A);
         NA_CHECK(cudaGetLastError());
     }
-    const size_t smem = 4 * 80 * 32 * sizeof(double);
+    const size_t smem = stream_smem_bytes<double>();
     {
         const int lo = g.per[1] ? 0 : 1, hi = g.per[1] ? g.ny : g.ny - 1;
         const long long nseg = (hi - lo + A.seg_len - 1) / A.seg_len;

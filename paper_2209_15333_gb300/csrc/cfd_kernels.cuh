@@ -663,9 +663,10 @@ __device__ __forceinline__ R beta_rows(const double (&S)[NS], const double (&SD)
 }
 
 // WENO7 (Balsara-Shu) on v[0..6]; one division (weights over a common
-// denominator, the division hoisting the paper describes).
+// denominator, the division hoisting the paper describes).  isc = 1/sigma^2
+// of the face: the indicators are measured on the flux per unit face area.
 template <class R>
-__device__ __forceinline__ R weno7(const R v[7], R eps)
+__device__ __forceinline__ R weno7(const R v[7], R eps, R isc)
 {
     constexpr double D[4] = W7_D;
     constexpr double SD[3] = W7_SD;
@@ -675,10 +676,10 @@ __device__ __forceinline__ R weno7(const R v[7], R eps)
     R q1 = (R)C1[0] * v[1] + (R)C1[1] * v[2] + (R)C1[2] * v[3] + (R)C1[3] * v[4];
     R q2 = (R)C2[0] * v[2] + (R)C2[1] * v[3] + (R)C2[2] * v[4] + (R)C2[3] * v[5];
     R q3 = (R)C3[0] * v[3] + (R)C3[1] * v[4] + (R)C3[2] * v[5] + (R)C3[3] * v[6];
-    R b0 = eps + beta_rows<R>(S0, SD, v + 0);
-    R b1 = eps + beta_rows<R>(S1, SD, v + 1);
-    R b2 = eps + beta_rows<R>(S2, SD, v + 2);
-    R b3 = eps + beta_rows<R>(S3, SD, v + 3);
+    R b0 = eps + isc * beta_rows<R>(S0, SD, v + 0);
+    R b1 = eps + isc * beta_rows<R>(S1, SD, v + 1);
+    R b2 = eps + isc * beta_rows<R>(S2, SD, v + 2);
+    R b3 = eps + isc * beta_rows<R>(S3, SD, v + 3);
     R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2, t3 = b3 * b3;
     R w0, w1, w2, w3;
     if (sizeof(R) == 8) {
@@ -696,7 +697,7 @@ __device__ __forceinline__ R weno7(const R v[7], R eps)
 // WENO5 (Jiang-Shu) on v[1..5] = f_{j-2..j+2}; mask bit k drops sub-stencil k
 // (the boundary closure of Section 2.2.4).
 template <class R>
-__device__ __forceinline__ R weno5(const R v[7], R eps, int mask)
+__device__ __forceinline__ R weno5(const R v[7], R eps, R isc, int mask)
 {
     constexpr double D[3] = W5_D;
     constexpr double SD[2] = W5_SD;
@@ -705,9 +706,9 @@ __device__ __forceinline__ R weno5(const R v[7], R eps, int mask)
     R q0 = (R)C0[0] * v[1] + (R)C0[1] * v[2] + (R)C0[2] * v[3];
     R q1 = (R)C1[0] * v[2] + (R)C1[1] * v[3] + (R)C1[2] * v[4];
     R q2 = (R)C2[0] * v[3] + (R)C2[1] * v[4] + (R)C2[2] * v[5];
-    R b0 = eps + beta_rows<R>(S0, SD, v + 1);
-    R b1 = eps + beta_rows<R>(S1, SD, v + 2);
-    R b2 = eps + beta_rows<R>(S2, SD, v + 3);
+    R b0 = eps + isc * beta_rows<R>(S0, SD, v + 1);
+    R b1 = eps + isc * beta_rows<R>(S1, SD, v + 2);
+    R b2 = eps + isc * beta_rows<R>(S2, SD, v + 3);
     R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2;
     R w0, w1, w2;
     if (sizeof(R) == 8) {
@@ -723,16 +724,26 @@ __device__ __forceinline__ R weno5(const R v[7], R eps, int mask)
 
 // one face value from upwind-ordered values; use: 0 UD7, 1 WENO7, 2 WENO5
 template <class R>
-__device__ __forceinline__ R recon(int use, const R v[7], R eps, int mask)
+__device__ __forceinline__ R recon(int use, const R v[7], R eps, R isc, int mask)
 {
     if (use == 0) return ud7<R>(v);
-    if (use == 1) return weno7<R>(v, eps);
-    return weno5<R>(v, eps, mask);
+    if (use == 1) return weno7<R>(v, eps, isc);
+    return weno5<R>(v, eps, isc, mask);
+}
+
+// 1/sigma_{j+1/2}^2 with sigma_{j+1/2} = (sigma_j + sigma_{j+1})/2, sigma =
+// |grad d|/J the face-area scale of the nodes' split fluxes (reading R23)
+template <class R>
+__device__ __forceinline__ R face_iscale(R sa, R sb)
+{
+    const R s = sa + sb;
+    return (R)4 / (s * s);
 }
 
 // Face flux at j+1/2 of component q from the 8 node values f_{j-3..j+4}.
 template <class R>
-__device__ __forceinline__ R face_flux(int use, const R fp8[8], const R fm8[8], R eps, int maskp, int maskm)
+__device__ __forceinline__ R face_flux(int use, const R fp8[8], const R fm8[8], R eps, R isc, int maskp,
+                                       int maskm)
 {
     R vp[7], vm[7];
 #pragma unroll
@@ -740,7 +751,7 @@ __device__ __forceinline__ R face_flux(int use, const R fp8[8], const R fm8[8], 
         vp[o] = fp8[o];
         vm[o] = fm8[7 - o];
     }
-    return recon<R>(use, vp, eps, maskp) + recon<R>(use, vm, eps, maskm);
+    return recon<R>(use, vp, eps, isc, maskp) + recon<R>(use, vm, eps, isc, maskm);
 }
 
 // scheme class of face j+1/2 (nodes j-3..j+4 of one line): returns use and masks.
@@ -1066,9 +1077,9 @@ __device__ __forceinline__ void visc_div(const SweepArgs& A, int d, long long ba
     }
 }
 
-// split fluxes of node (i, j, k) along direction d
+// split fluxes of node (i, j, k) along direction d; returns the node's sigma
 template <class R>
-__device__ __forceinline__ void node_split(const SweepArgs& A, int d, long long n, int i, int j, R fp[5], R fm[5])
+__device__ __forceinline__ R node_split(const SweepArgs& A, int d, long long n, int i, int j, R fp[5], R fm[5])
 {
     const R* P = (const R*)A.P;
     const long long N = A.g.N;
@@ -1077,6 +1088,7 @@ __device__ __forceinline__ void node_split(const SweepArgs& A, int d, long long 
     R k1 = metr<R>(A.g, M_K + 3 * d, mi), k2 = metr<R>(A.g, M_K + 3 * d + 1, mi),
       k3 = metr<R>(A.g, M_K + 3 * d + 2, mi), sg = metr<R>(A.g, M_SIG + d, mi);
     sw_split<R>(A.ph, rho, u, v, w, c, k1, k2, k3, sg, fp, fm);
+    return sg;
 }
 
 // xi sweep: one CTA per segment of BX nodes of one x-line, halo of 4 nodes.
@@ -1087,6 +1099,7 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
     __shared__ R sh[5][BX + 1];
     __shared__ R sv[4][BX + 8];
     __shared__ uint8_t sc[BX + 12];
+    __shared__ R ss[BX + 12];                    // sigma of the stencil nodes
     const Geo& g = A.g;
     const int n = g.nx;
     const int per = g.per[0];
@@ -1098,11 +1111,11 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
     for (int s = t; s < BX + 8; s += BX) {
         int i = i0 - 4 + s;
         bool ok = per || (i >= 0 && i < n);
-        R fp[5], fm[5];
+        R fp[5], fm[5], sg = (R)0;
         uint8_t c = 0;
         if (ok) {
             int ii = per ? wrapi(i, n) : i;
-            node_split<R>(A, 0, row + ii, ii, j, fp, fm);
+            sg = node_split<R>(A, 0, row + ii, ii, j, fp, fm);
             if (A.cls) c = A.cls[row + ii];
             if (A.Fv) {
 #pragma unroll
@@ -1122,11 +1135,13 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
             sf[5 + q][s] = fm[q];
         }
         sc[s] = c;
+        ss[s] = sg;
     }
     if (t < 4) {
 #pragma unroll
         for (int q = 0; q < 10; ++q) sf[q][BX + 8 + t] = (R)0;
         sc[BX + 8 + t] = 0;
+        ss[BX + 8 + t] = (R)0;
     }
     __syncthreads();
     // faces: slot f <-> face (i0-1+f)+1/2 (stencil rows f..f+7), f = 0..BX.
@@ -1162,13 +1177,14 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
             for (int o = 0; o < 8; ++o) cm = max(cm, (int)sc[slot + o]);
             int mp, mm;
             const int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+            const R isc = use ? face_iscale<R>(ss[slot + 3], ss[slot + 4]) : (R)0;
             R p8[8], m8[8];
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
                 p8[o] = pv[u + o];
                 m8[o] = mv[u + o];
             }
-            sh[q][slot] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mp, mm);
+            sh[q][slot] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), isc, mp, mm);
         }
     }
     __syncthreads();
@@ -1205,7 +1221,7 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo& g = A.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    R* ring = reinterpret_cast<R*>(smem_raw) + (size_t)warp * (8 * 10 * 32);
+    R* ring = reinterpret_cast<R*>(smem_raw) + (size_t)warp * (8 * 11 * 32);  // [8][f+, f-, sigma][32]
     const int nx = g.nx;
     const int n = DIR == 1 ? g.ny : g.nz;
     const int nother = DIR == 1 ? g.nz : g.ny;
@@ -1233,14 +1249,14 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
     for (int s = 0; s < nsteps; ++s) {
         const int m = m0 - 4 + s;
         const int slot = s & 7;
-        R fp[5], fm[5];
+        R fp[5], fm[5], sg = (R)0;
         uint8_t c = 0;
         bool ok = lane_ok && (per || (m >= 0 && m < n));
         if (ok) {
             int mm = per ? wrapi(m, n) : m;
             long long nn = base + (long long)mm * stride;
             int jj = DIR == 1 ? mm : o;
-            node_split<R>(A, DIR, nn, i, jj, fp, fm);
+            sg = node_split<R>(A, DIR, nn, i, jj, fp, fm);
             if (A.cls) c = A.cls[nn];
         } else {
 #pragma unroll
@@ -1248,9 +1264,10 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            ring[(slot * 10 + q) * 32 + lane] = fp[q];
-            ring[(slot * 10 + 5 + q) * 32 + lane] = fm[q];
+            ring[(slot * 11 + q) * 32 + lane] = fp[q];
+            ring[(slot * 11 + 5 + q) * 32 + lane] = fm[q];
         }
+        ring[(slot * 11 + 10) * 32 + lane] = sg;
         cwin = (cwin << 8) | c;
         if (s >= 7) {
             const int jf = m - 4;  // face jf + 1/2 with nodes m-7 .. m
@@ -1259,6 +1276,10 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
             for (int b = 0; b < 8; ++b) cm = max(cm, (int)((cwin >> (8 * b)) & 0xff));
             int mp, mm;
             int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+            // nodes jf and jf+1 sit at window positions 3 and 4
+            const R isc = use && lane_ok ? face_iscale<R>(ring[(((s - 4) & 7) * 11 + 10) * 32 + lane],
+                                               ring[(((s - 3) & 7) * 11 + 10) * 32 + lane])
+                              : (R)0;
             R fh[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
@@ -1266,10 +1287,10 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
 #pragma unroll
                 for (int b = 0; b < 8; ++b) {
                     int sl = (s - 7 + b) & 7;
-                    p8[b] = ring[(sl * 10 + q) * 32 + lane];
-                    m8[b] = ring[(sl * 10 + 5 + q) * 32 + lane];
+                    p8[b] = ring[(sl * 11 + q) * 32 + lane];
+                    m8[b] = ring[(sl * 11 + 5 + q) * 32 + lane];
                 }
-                fh[q] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mp, mm);
+                fh[q] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), isc, mp, mm);
             }
             if (s >= 8 && lane_ok) {
                 const int mn = m - 4;  // node
@@ -1356,18 +1377,26 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
     constexpr int FPT = (TL + 1 + 7) / 8;
     constexpr int WIN = FPT + 7;
     const int fbase = ty * FPT;
-    R fh[FPT][5];
+    R fh[FPT][5], iscv[FPT];
     int usev[FPT], mpv[FPT], mmv[FPT];
 #pragma unroll
     for (int u = 0; u < FPT; ++u) {
         const int f = fbase + u;
         const int jf = m0 - 1 + f;
         usev[u] = -1;
+        iscv[u] = (R)0;
         if (f > TL || !(per || (jf >= 0 && jf <= n - 2))) continue;
         int cm = 0;
 #pragma unroll
         for (int b = 0; b < 8; ++b) cm = max(cm, (int)sc[(f + b) * 32 + lane]);
         usev[u] = face_use(A.ph, per, n, jf, cm, &mpv[u], &mmv[u]);
+        if (usev[u] > 0 && lane_ok) {
+            // sigma of nodes jf and jf+1 from the metrics (WENO faces only)
+            const int ma = per ? wrapi(jf, n) : jf, mb = per ? wrapi(jf + 1, n) : jf + 1;
+            const long long na = base + (long long)ma * stride, nb = base + (long long)mb * stride;
+            iscv[u] = face_iscale<R>(metr<R>(g, M_SIG + DIR, midx(g, i, DIR == 1 ? ma : o, na)),
+                                     metr<R>(g, M_SIG + DIR, midx(g, i, DIR == 1 ? mb : o, nb)));
+        }
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -1390,7 +1419,7 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
                 p8[b] = pv[u + b];
                 m8[b] = mv[u + b];
             }
-            fh[u][q] = face_flux<R>(usev[u], p8, m8, pk<R>(A.ph.eps, A.ph.epsf), mpv[u], mmv[u]);
+            fh[u][q] = face_flux<R>(usev[u], p8, m8, pk<R>(A.ph.eps, A.ph.epsf), iscv[u], mpv[u], mmv[u]);
         }
     }
     __syncthreads();
@@ -1428,6 +1457,13 @@ template <class R, int TL>
 constexpr size_t tile_smem_bytes()
 {
     return (size_t)(TL + 8) * 32 * (10 + 4) * sizeof(R) + (size_t)(TL + 8) * 32;
+}
+
+// dynamic shared memory of k_sweep_s: 4 warps x 8 ring slots x 11 values x 32 lanes
+template <class R>
+constexpr size_t stream_smem_bytes()
+{
+    return (size_t)4 * 8 * 11 * 32 * sizeof(R);
 }
 
 // ---------------------------------------------------------------------------
