@@ -39,9 +39,14 @@ MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_
 # 160^3 stage, valid for the kernel source with this hash prefix; scaled to the full
 # launch by the node count (traffic grows with it: the arrays exceed L2).
 NCU_TRAFFIC = {
-    "fp64": {"src": "", "per_node": {"visc_flux": 185.4, "sweep_xi": 106.4, "sweep_eta": 153.5,
-                                      "sweep_zeta": 155.5}},
-    "mixed": {"src": "", "per_node": {}},
+    # DRAM read + write bytes per node of one launch, from the ncu --set full
+    # captures at 160^3 (the profiles directory), valid for the kernel
+    # sources with this hash and the variant each kernel ran in
+    "fp64": {"src": "2b744d3cad74", "per_node": {"visc_flux": 117.1, "sweep_xi": 106.4},
+             "variant": {"visc_flux": [0, 0], "sweep_xi": None}},
+    "mixed": {"src": "2b744d3cad74", "per_node": {"visc_flux": 51.9, "sweep_xi": 50.2, "sweep_eta": 72.5,
+                                                  "sweep_zeta": 90.7},
+              "variant": {"visc_flux": [0, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
 }
 
 
@@ -333,7 +338,10 @@ def roofline(prec, r, N, peaks, fma, src_hash):
     dom = max(prof, key=prof.get)
     tr = NCU_TRAFFIC[prec]
     traffic = None
-    if tr["src"] and tr["src"] == src_hash and dom in tr["per_node"]:
+    ran = {"visc_flux": r["variants"]["visc"], "sweep_eta": r["variants"]["eta"],
+           "sweep_zeta": r["variants"]["zeta"]}.get(dom)
+    if (tr["src"] and tr["src"] == src_hash and dom in tr["per_node"]
+            and (tr["variant"][dom] is None or list(tr["variant"][dom]) == list(ran))):
         traffic = tr["per_node"][dom] * N
     if prec == "fp64":
         achieved = FP64_FLOPS[dom] * N / (prof[dom] * 1e-3) / 1e12
