@@ -30,18 +30,16 @@ MT = 0.5
 GAMMA = 1.4
 KERNEL_NAMES = ["prim", "sensor", "visc_flux", "sweep_xi", "sweep_eta", "sweep_zeta"]
 
-# Algorithmic work per node of each kernel (stated in the design doc, section 5):
+# Algorithmic work per node of each kernel:
 # FP64 form: counted flops (FMA = 2; division, sqrt, pow = 1);
 # mixed form: compulsory bytes (inputs read once, outputs written once).
 FP64_FLOPS = {"prim": 25, "sensor": 20, "visc_flux": 305, "sweep_xi": 247, "sweep_eta": 252, "sweep_zeta": 277}
 MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_eta": 77, "sweep_zeta": 164}
-# DRAM bytes per node measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on a
-# 160^3 stage, valid for the kernel source with this hash prefix; scaled to the full
-# launch by the node count (traffic grows with it: the arrays exceed L2).
+# DRAM bytes per node measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on a 160^3 stage (the profiles directory), valid for the kernel sources with this
+# hash prefix and the variant each kernel ran in; scaled to the full launch by the
+# node count (traffic grows with it: the arrays exceed L2).
 NCU_TRAFFIC = {
-    # DRAM read + write bytes per node of one launch, from the ncu --set full
-    # captures at 160^3 (the profiles directory), valid for the kernel
-    # sources with this hash and the variant each kernel ran in
     "fp64": {"src": "2b744d3cad74", "per_node": {"visc_flux": 117.1, "sweep_xi": 106.4},
              "variant": {"visc_flux": [0, 0], "sweep_xi": None}},
     "mixed": {"src": "2b744d3cad74", "per_node": {"visc_flux": 51.9, "sweep_xi": 50.2, "sweep_eta": 72.5,
