@@ -1077,6 +1077,30 @@ __device__ __forceinline__ void visc_div(const SweepArgs& A, int d, long long ba
     }
 }
 
+// primitives a split needs (rho, u, v, w, c), loaded through the read-only path
+template <class R>
+struct NodePrim {
+    R rho, u, v, w, c;
+};
+
+template <class R>
+__device__ __forceinline__ NodePrim<R> load_prim(const SweepArgs& A, long long n)
+{
+    const R* __restrict__ P = (const R*)A.P;
+    const long long N = A.g.N;
+    return {__ldg(P + n), __ldg(P + N + n), __ldg(P + 2 * N + n), __ldg(P + 3 * N + n), __ldg(P + 6 * N + n)};
+}
+
+// split fluxes from loaded primitives along direction d; returns sigma
+template <class R>
+__device__ __forceinline__ R split_prim(const SweepArgs& A, int d, const NodePrim<R>& q, long long mi, R fp[5], R fm[5])
+{
+    R k1 = metr<R>(A.g, M_K + 3 * d, mi), k2 = metr<R>(A.g, M_K + 3 * d + 1, mi),
+      k3 = metr<R>(A.g, M_K + 3 * d + 2, mi), sg = metr<R>(A.g, M_SIG + d, mi);
+    sw_split<R>(A.ph, q.rho, q.u, q.v, q.w, q.c, k1, k2, k3, sg, fp, fm);
+    return sg;
+}
+
 // split fluxes of node (i, j, k) along direction d; returns the node's sigma
 template <class R>
 __device__ __forceinline__ R node_split(const SweepArgs& A, int d, long long n, int i, int j, R fp[5], R fm[5])
@@ -1100,6 +1124,8 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
     __shared__ R sv[4][BX + 8];
     __shared__ uint8_t sc[BX + 12];
     __shared__ R ss[BX + 12];                    // sigma of the stencil nodes
+    __shared__ uint8_t suse[BX + 1];             // per face: use | mask+ << 2 | mask- << 5 (0xff: none)
+    __shared__ R sisc[BX + 1];                   // per face: 1/sigma^2 (WENO faces)
     const Geo& g = A.g;
     const int n = g.nx;
     const int per = g.per[0];
@@ -1145,10 +1171,29 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
     }
     __syncthreads();
     // faces: slot f <-> face (i0-1+f)+1/2 (stencil rows f..f+7), f = 0..BX.
+    // The scheme of each face (interface class, closure masks, scale) is
+    // decided once here for all five components.
+    const int flim = min(BX, (per ? n : n - 1) - i0);  // last slot needed
+    for (int slot = t; slot <= BX; slot += BX) {
+        const int jf = i0 - 1 + slot;
+        uint8_t code = 0xff;
+        R isc = (R)0;
+        if (slot <= flim && (per || jf >= 0)) {
+            int cm = 0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) cm = max(cm, (int)sc[slot + o]);
+            int mp, mm;
+            const int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+            code = (uint8_t)(use | (mp << 2) | (mm << 5));
+            if (use) isc = face_iscale<R>(ss[slot + 3], ss[slot + 4]);
+        }
+        suse[slot] = code;
+        sisc[slot] = isc;
+    }
+    __syncthreads();
     // A job is 4 consecutive faces of one component, computed from one
     // 12-value window per side (vector shared-memory loads).
     constexpr int NG = (BX + 1 + 3) / 4;
-    const int flim = min(BX, (per ? n : n - 1) - i0);  // last slot needed
     for (int job = t; job < 5 * NG; job += BX) {
         const int q = job / NG, f0 = 4 * (job - q * NG);
         if (f0 > flim) continue;
@@ -1170,14 +1215,11 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int slot = f0 + u;
-            const int jf = i0 - 1 + slot;
-            if (slot > flim || (!per && jf < 0)) continue;
-            int cm = 0;
-#pragma unroll
-            for (int o = 0; o < 8; ++o) cm = max(cm, (int)sc[slot + o]);
-            int mp, mm;
-            const int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
-            const R isc = use ? face_iscale<R>(ss[slot + 3], ss[slot + 4]) : (R)0;
+            if (slot > BX) break;
+            const int code = suse[slot];
+            if (code == 0xff) continue;
+            const int use = code & 3, mp = (code >> 2) & 7, mm = code >> 5;
+            const R isc = sisc[slot];
             R p8[8], m8[8];
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
@@ -1339,36 +1381,55 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
     const long long base = DIR == 1 ? (long long)i + (long long)nx * g.ny * o : (long long)i + (long long)nx * o;
     const long long N = g.N;
     const R* Fv = (const R*)A.Fv;
-    // 1. split fluxes, classes and viscous fluxes of the tile rows
-    for (int r = ty; r < ROWS; r += 8) {
+    // 1. split fluxes, classes and viscous fluxes of the tile rows.  Every
+    //    thread first issues the loads of all its rows (NR per warp), then
+    //    splits: the loads of a tile are in flight together.
+    constexpr int NR = (ROWS + 7) / 8;
+    NodePrim<R> qv[NR];
+    R fvv[NR][4];
+    uint8_t cv[NR];
+    bool okv[NR];
+    long long miv[NR];
+#pragma unroll
+    for (int it = 0; it < NR; ++it) {
+        const int r = ty + 8 * it;
         const int m = m0 - 4 + r;
-        R fp[5], fm[5];
-        uint8_t c = 0;
-        const bool ok = lane_ok && (per || (m >= 0 && m < n));
-        if (ok) {
+        okv[it] = r < ROWS && lane_ok && (per || (m >= 0 && m < n));
+        cv[it] = 0;
+        miv[it] = 0;
+        if (okv[it]) {
             const int mm = per ? wrapi(m, n) : m;
             const long long nn = base + (long long)mm * stride;
-            const int jj = DIR == 1 ? mm : o;
-            node_split<R>(A, DIR, nn, i, jj, fp, fm);
-            if (A.cls) c = A.cls[nn];
+            miv[it] = midx(g, i, DIR == 1 ? mm : o, nn);
+            qv[it] = load_prim<R>(A, nn);
+            if (A.cls) cv[it] = __ldg(A.cls + nn);
             if (Fv) {
 #pragma unroll
-                for (int row = 0; row < 4; ++row) sv[(r * 4 + row) * 32 + lane] = Fv[(long long)(4 * DIR + row) * N + nn];
+                for (int row = 0; row < 4; ++row) fvv[it][row] = __ldg(Fv + (long long)(4 * DIR + row) * N + nn);
             }
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < NR; ++it) {
+        const int r = ty + 8 * it;
+        if (r >= ROWS) break;
+        R fp[5], fm[5];
+        if (okv[it]) {
+            split_prim<R>(A, DIR, qv[it], miv[it], fp, fm);
         } else {
 #pragma unroll
             for (int q = 0; q < 5; ++q) fp[q] = fm[q] = (R)0;
-            if (Fv) {
+        }
+        if (Fv) {
 #pragma unroll
-                for (int row = 0; row < 4; ++row) sv[(r * 4 + row) * 32 + lane] = (R)0;
-            }
+            for (int row = 0; row < 4; ++row) sv[(r * 4 + row) * 32 + lane] = okv[it] ? fvv[it][row] : (R)0;
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             sf[(r * 10 + q) * 32 + lane] = fp[q];
             sf[(r * 10 + 5 + q) * 32 + lane] = fm[q];
         }
-        sc[r * 32 + lane] = c;
+        sc[r * 32 + lane] = cv[it];
     }
     __syncthreads();
     // 2. faces (m0-1+f)+1/2, f = 0..TL, from rows f..f+7.  Thread row ty
@@ -1613,7 +1674,10 @@ __global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<
 template <class R, int BX, int EP>
 __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A) { sweep_x_body<R, BX, EP>(A, blockIdx); }
 template <class R, int DIR, int EP, int TL>
-__global__ void __launch_bounds__(256) k_sweep_t(SweepArgs A) { sweep_t_body<R, DIR, EP, TL>(A, blockIdx); }
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_sweep_t(SweepArgs A)
+{
+    sweep_t_body<R, DIR, EP, TL>(A, blockIdx);
+}
 
 // ---------------------------------------------------------------------------
 // ... and persistent batched launches over an ensemble of uneven blocks: one
@@ -1678,6 +1742,9 @@ __global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((
 template <class R, int BX, int EP>
 __global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m) { BATCH_LOOP((sweep_x_body<R, BX, EP>), true) }
 template <class R, int DIR, int EP, int TL>
-__global__ void __launch_bounds__(256) kb_sweep_t(BatchMap m) { BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true) }
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) kb_sweep_t(BatchMap m)
+{
+    BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true)
+}
 
 }  // namespace cfdk
