@@ -449,6 +449,14 @@ static cudaError_t set_sweep_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<R, 32>());
+    // tiles are latency-bound: let the shared-memory carveout admit every
+    // CTA the registers allow
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 32>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
@@ -793,6 +801,12 @@ static cudaError_t batch_kernel_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<R, kBatchTL>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, kBatchTL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     return e;
 }
 

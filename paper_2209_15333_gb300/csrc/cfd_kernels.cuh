@@ -860,10 +860,13 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
         // computed once and shared by the four fields (periodic lines wrap)
         int off[3][9];
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
+        for (int d = 0; d < 3; ++d) {
+            // only nodes within 4 of the ends of a periodic line need wrapping
+            const bool wrap = g.per[d] && (pos[d] < 4 || pos[d] + 4 >= nd[d]);
 #pragma unroll
             for (int t = 0; t < 9; ++t)
-                off[d][t] = g.per[d] ? (wrapi(pos[d] + t - 4, nd[d]) - pos[d]) * st[d] : (t - 4) * st[d];
+                off[d][t] = wrap ? (wrapi(pos[d] + t - 4, nd[d]) - pos[d]) * st[d] : (t - 4) * st[d];
+        }
         // dq[var][d]: var = u, v, w, T (P rows 1, 2, 3, 5)
         R dq[4][3];
 #pragma unroll
@@ -1674,7 +1677,7 @@ __global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<
 template <class R, int BX, int EP>
 __global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A) { sweep_x_body<R, BX, EP>(A, blockIdx); }
 template <class R, int DIR, int EP, int TL>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) k_sweep_t(SweepArgs A)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (TL == 16 ? 4 : 3) : 1) k_sweep_t(SweepArgs A)
 {
     sweep_t_body<R, DIR, EP, TL>(A, blockIdx);
 }
