@@ -584,10 +584,57 @@ int orc_apply_bc(const orc_params* P, const double* metrics, double* U, double t
 /* ------------------------------------------------------------------ */
 
 /* inviscid flux at interface j+1/2 of one line (NODAL or FSP metrics) */
+/* ------------------------------------------------------------------ */
+/* characteristic variables (Sec. 2.2.2, Eq. 31-40)                    */
+/* ------------------------------------------------------------------ */
+
+int orc_char_matrices(double gamma, const double U[5], const double n[3], double S[25], double Sinv[25])
+{
+    double rho = U[0];
+    if (!(rho > 0.0)) return -1;
+    double u = U[1] / rho, v = U[2] / rho, w = U[3] / rho;
+    double V = 0.5 * (u * u + v * v + w * w);                      /* Eq. 25 */
+    double p = (gamma - 1.0) * (U[4] - rho * V);
+    if (!(p > 0.0)) return -1;
+    double c2 = gamma * p / rho, c = sqrt(c2);
+    double H = V + c2 / (gamma - 1.0);                             /* Eq. 36 */
+    double kap = (gamma - 1.0) / c2, kap1 = 0.5 * kap, chi = 0.5 / c; /* Eq. 37 */
+    double n1 = n[0], n2 = n[1], n3 = n[2];
+    double l1, l2, l3;                                             /* Eq. 39 */
+    if (fabs(n3) <= fabs(n2)) {
+        double r = sqrt(n1 * n1 + n2 * n2);
+        l1 = -n2 / r; l2 = n1 / r; l3 = 0.0;
+    } else {
+        double r = sqrt(n1 * n1 + n3 * n3);
+        l1 = -n3 / r; l2 = 0.0; l3 = n1 / r;
+    }
+    double m1 = n2 * l3 - n3 * l2, m2 = n3 * l1 - n1 * l3, m3 = n1 * l2 - n2 * l1; /* Eq. 40 */
+    double un = u * n1 + v * n2 + w * n3;                          /* Eq. 38 */
+    double ul = u * l1 + v * l2 + w * l3;
+    double um = u * m1 + v * m2 + w * m3;
+    double Si[25] = {                                              /* Eq. 34 */
+        1.0, 0.0, 0.0, 1.0, 1.0,
+        u,   l1,  m1,  u - c * n1, u + c * n1,
+        v,   l2,  m2,  v - c * n2, v + c * n2,
+        w,   l3,  m3,  w - c * n3, w + c * n3,
+        V,   ul,  um,  H - c * un, H + c * un};
+    double Sl[25] = {                                              /* Eq. 35 */
+        1.0 - kap * V, kap * u, kap * v, kap * w, -kap,
+        -ul, l1, l2, l3, 0.0,
+        -um, m1, m2, m3, 0.0,
+        kap1 * V + chi * un, -chi * n1 - kap1 * u, -chi * n2 - kap1 * v, -chi * n3 - kap1 * w, kap1,
+        kap1 * V - chi * un, chi * n1 - kap1 * u, chi * n2 - kap1 * v, chi * n3 - kap1 * w, kap1};
+    memcpy(S, Sl, sizeof(Sl));
+    memcpy(Sinv, Si, sizeof(Si));
+    return 0;
+}
+
 /* fs: face-area scale sigma_{j+1/2} of the interface (R23) */
-static void interface_flux(const orc_params* P, int n, int periodic, int j,
-                           const double* fp /* [n][5] */, const double* fm, const unsigned char* lcls,
-                           double fs, double out[5])
+/* chU (U_j and U_{j+1}, [2][5]) and chn (unit normal of the interface):
+   characteristic reconstruction of the WENO faces (Sec. 2.2.2), or NULL */
+static int interface_flux(const orc_params* P, int n, int periodic, int j,
+                          const double* fp /* [n][5] */, const double* fm, const unsigned char* lcls,
+                          double fs, const double* chU, const double* chn, double out[5])
 {
     int scheme = P->scheme;
     int masked_edge = !periodic && (j - 3 < 0 || j + 4 > n - 1);
@@ -608,6 +655,17 @@ static void interface_flux(const orc_params* P, int n, int periodic, int j,
         }
         use = c;
     }
+    /* Eq. 31: with characteristic reconstruction the WENO faces work on
+       g = S f of every stencil node (UD7 is linear, so projecting would
+       not change it); the result is mapped back with S^-1 */
+    int chr = chU && use != 0;
+    double char_S[25], char_Sinv[25];
+    if (chr) {
+        double Uh[5];
+        for (int q = 0; q < NV; ++q) Uh[q] = 0.5 * (chU[q] + chU[NV + q]);   /* Eq. 32 */
+        if (orc_char_matrices(P->gamma, Uh, chn, char_S, char_Sinv) != 0) return -1;
+    }
+    double gout[5];
     for (int q = 0; q < NV; ++q) {
         double a[7], b[7];
         int inrange_p[7], inrange_m[7];
@@ -615,8 +673,17 @@ static void interface_flux(const orc_params* P, int n, int periodic, int j,
             int ip = j + o, im = j + 1 - o;
             inrange_p[o + 3] = periodic || (ip >= 0 && ip < n);
             inrange_m[o + 3] = periodic || (im >= 0 && im < n);
-            a[o + 3] = inrange_p[o + 3] ? fp[wrap(ip, n) * NV + q] : 0.0;
-            b[o + 3] = inrange_m[o + 3] ? fm[wrap(im, n) * NV + q] : 0.0;
+            a[o + 3] = 0.0;
+            b[o + 3] = 0.0;
+            if (chr) {
+                for (int e = 0; e < NV; ++e) {
+                    if (inrange_p[o + 3]) a[o + 3] += char_S[q * NV + e] * fp[wrap(ip, n) * NV + e];
+                    if (inrange_m[o + 3]) b[o + 3] += char_S[q * NV + e] * fm[wrap(im, n) * NV + e];
+                }
+            } else {
+                if (inrange_p[o + 3]) a[o + 3] = fp[wrap(ip, n) * NV + q];
+                if (inrange_m[o + 3]) b[o + 3] = fm[wrap(im, n) * NV + q];
+            }
         }
         double vp, vm;
         if (use == 0) {
@@ -638,16 +705,27 @@ static void interface_flux(const orc_params* P, int n, int periodic, int j,
             vp = orc_weno(3, a + 1, mp, P->weno_eps, fs, NULL);
             vm = orc_weno(3, b + 1, mm, P->weno_eps, fs, NULL);
         }
-        out[q] = vp + vm;
+        gout[q] = vp + vm;
     }
+    for (int q = 0; q < NV; ++q) {
+        if (!chr) {
+            out[q] = gout[q];
+            continue;
+        }
+        double s = 0.0;
+        for (int e = 0; e < NV; ++e) s += char_Sinv[q * NV + e] * gout[e];
+        out[q] = s;
+    }
+    return 0;
 }
 
 /* does node position m along a line receive a right-hand side */
 static int rhs_node(int periodic, int n, int m) { return periodic || (m > 0 && m < n - 1); }
 
-static void inviscid_direction(const orc_params* P, const double* met, const double* prim,
-                               const unsigned char* cls, double* R, int d)
+static int inviscid_direction(const orc_params* P, const double* met, const double* U, const double* prim,
+                              const unsigned char* cls, double* R, int d)
 {
+    int status = 0;
     long N = nnodes(P);
     int nd = dim_n(P, d);
     long s = dim_stride(P, d);
@@ -679,8 +757,18 @@ static void inviscid_direction(const orc_params* P, const double* met, const dou
         }
         /* interfaces j+1/2, j = -1 .. nd-1, stored at fh[j+1] */
         int jlo = periodic ? -1 : 0, jhi = periodic ? nd - 1 : nd - 2;
+        int chr = P->recon_vars == ORC_RECON_CHARACTERISTIC;
         for (int j = jlo; j <= jhi; ++j) {
             double out[5];
+            /* characteristic reconstruction: conserved states of the two
+               nodes of the interface (Eq. 32 averages them) */
+            double chU[10];
+            int ja = wrap(j, nd), jb = wrap(j + 1, nd);
+            for (int q = 0; q < NV; ++q) {
+                chU[q] = U[q * N + base + ja * s];
+                chU[NV + q] = U[q * N + base + jb * s];
+            }
+            int rc;
             if (P->metric_mode == ORC_METRIC_FSP) {
                 /* R17: interface metric, frozen over the stencil nodes j-3..j+4 */
                 double ai[3] = {0.0, 0.0, 0.0};
@@ -701,15 +789,28 @@ static void inviscid_direction(const orc_params* P, const double* met, const dou
                 /* local line of the 8 stencil nodes j-3..j+4: interface at local 3+1/2,
                    whose stencil stays inside the local line */
                 double fs = sqrt(ai[0] * ai[0] + ai[1] * ai[1] + ai[2] * ai[2]);
-                interface_flux(P, 8, 1, 3, lfp, lfm, lc, fs, out);
+                double nrm[3] = {ai[0] / fs, ai[1] / fs, ai[2] / fs};
+                rc = interface_flux(P, 8, 1, 3, lfp, lfm, lc, fs, chr ? chU : NULL, nrm, out);
             } else {
                 /* R23: sigma_{j+1/2} = (sigma_j + sigma_{j+1})/2, sigma = |alpha| (Eq. 22) */
-                int ja = wrap(j, nd), jb = wrap(j + 1, nd);
                 double fs = 0.5 * (sqrt(alpha[3 * ja] * alpha[3 * ja] + alpha[3 * ja + 1] * alpha[3 * ja + 1] +
                                         alpha[3 * ja + 2] * alpha[3 * ja + 2]) +
                                    sqrt(alpha[3 * jb] * alpha[3 * jb] + alpha[3 * jb + 1] * alpha[3 * jb + 1] +
                                         alpha[3 * jb + 2] * alpha[3 * jb + 2]));
-                interface_flux(P, nd, periodic, periodic ? wrap(j, nd) : j, fp, fm, lcls, fs, out);
+                /* R25: interface normal from the two nodes' metric vectors */
+                double sa[3], sn = 0.0;
+                for (int e = 0; e < 3; ++e) {
+                    sa[e] = alpha[3 * ja + e] + alpha[3 * jb + e];
+                    sn += sa[e] * sa[e];
+                }
+                sn = sqrt(sn);
+                double nrm[3] = {sa[0] / sn, sa[1] / sn, sa[2] / sn};
+                rc = interface_flux(P, nd, periodic, periodic ? wrap(j, nd) : j, fp, fm, lcls, fs,
+                                    chr ? chU : NULL, nrm, out);
+            }
+            if (rc != 0) {
+#pragma omp atomic write
+                status = -3;
             }
             for (int q = 0; q < NV; ++q) fh[NV * (j + 1) + q] = out[q];
         }
@@ -721,6 +822,7 @@ static void inviscid_direction(const orc_params* P, const double* met, const dou
         }
         free(fp); free(fm); free(fh); free(lcls); free(alpha);
     }
+    return status;
 }
 
 static void viscous_terms(const orc_params* P, const double* met, const double* prim, double* R)
@@ -817,7 +919,12 @@ int orc_rhs(const orc_params* P, const double* met, const double* U, double* L,
         else orc_sensor(P, U, NULL, cls);
     }
     if (cls_out) memcpy(cls_out, cls, (size_t)N);
-    for (int d = 0; d < 3; ++d) inviscid_direction(P, met, prim, cls, R, d); /* steps 4-7 */
+    int st = 0;
+    for (int d = 0; d < 3 && st == 0; ++d) st = inviscid_direction(P, met, U, prim, cls, R, d); /* steps 4-7 */
+    if (st != 0) {
+        free(prim); free(R); free(cls);
+        return st;
+    }
     if (P->Re > 0.0) viscous_terms(P, met, prim, R);                      /* step 8 */
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {                                        /* step 9 */
@@ -859,7 +966,11 @@ int orc_step(const orc_params* P, const double* met, double* U, double dt, int n
         memcpy(Un, U, sizeof(double) * n5);
         memcpy(Uk, U, sizeof(double) * n5);
         for (int st = 1; st <= 3; ++st) {
-            orc_rhs(P, met, Uk, L, NULL);
+            int rc = orc_rhs(P, met, Uk, L, NULL);
+            if (rc != 0) {
+                free(Un); free(Uk); free(L);
+                return rc;
+            }
             orc_rk3_stage(st, n5, Un, Uk, L, dt, Uk);
             orc_apply_bc(P, met, Uk, t + tstage[st - 1] * dt);
         }

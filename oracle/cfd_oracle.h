@@ -23,6 +23,7 @@ enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_INFLOW = 2, ORC_BC_OUTFLOW =
 enum { ORC_SUTHERLAND = 0, ORC_POWER = 1 };
 enum { ORC_UD7 = 0, ORC_WENO5 = 1, ORC_WENO7 = 2, ORC_HYBRID = 3 };
 enum { ORC_METRIC_NODAL = 0, ORC_METRIC_FSP = 1 };
+enum { ORC_RECON_COMPONENT = 0, ORC_RECON_CHARACTERISTIC = 1 };
 
 typedef struct orc_params {
     int nx, ny, nz;
@@ -43,6 +44,7 @@ typedef struct orc_params {
     int blow_m;
     const double* wall_x;         /* [nx] x of the eta-low wall nodes (blowing), or NULL */
     const double* wall_z;         /* [nz] z of the eta-low wall nodes (blowing), or NULL */
+    int recon_vars;               /* ORC_RECON_COMPONENT or ORC_RECON_CHARACTERISTIC (Sec. 2.2.2) */
 } orc_params;
 
 /* ---- whole-field operations ---- */
@@ -71,6 +73,13 @@ int orc_weno_tables(int r, double* c /* [r][r] */, double* d /* [r] */, double* 
 double orc_weno(int r, const double* a /* [2r-1] */, const int* mask /* [r] or NULL */, double eps,
                 double s, double* omega_out /* [r] or NULL */);
 double orc_weno_beta(int r, int k, const double* a /* [r] */);
+/* Eigenvector matrices of Sec. 2.2.2 (Eq. 34-40) at the conserved state
+   U = (rho, rho u, rho v, rho w, E) for the unit normal n: S (rows: left
+   eigenvectors, Eq. 35) and Sinv (columns: right eigenvectors, Eq. 34),
+   both row-major [5][5]; the fields are ordered as the eigenvalues of
+   Eq. 33: u_n (entropy), u_n (shear along l), u_n (shear along m), u_n - c,
+   u_n + c.  Returns -1 for a non-physical state. */
+int orc_char_matrices(double gamma, const double U[5], const double n[3], double S[25], double Sinv[25]);
 int orc_central_deriv(int order, int n, int periodic, const double* g, double* dg);
 int orc_midpoint_weights(double* w /* [8] */);
 double orc_viscosity(const orc_params* P, double T);

@@ -13,6 +13,7 @@ BC_PERIODIC, BC_WALL, BC_INFLOW, BC_OUTFLOW = 0, 1, 2, 3
 SUTHERLAND, POWER = 0, 1
 UD7, WENO5, WENO7, HYBRID = 0, 1, 2, 3
 METRIC_NODAL, METRIC_FSP = 0, 1
+RECON_COMPONENT, RECON_CHARACTERISTIC = 0, 1
 
 _dp = C.POINTER(C.c_double)
 _ucp = C.POINTER(C.c_ubyte)
@@ -32,6 +33,7 @@ class OrcParams(C.Structure):
         ("blow_amp", C.c_double), ("blow_x0", C.c_double), ("blow_x1", C.c_double),
         ("blow_omega", C.c_double), ("blow_Lz", C.c_double), ("blow_m", C.c_int),
         ("wall_x", _dp), ("wall_z", _dp),
+        ("recon_vars", C.c_int),
     ]
 
 
@@ -60,6 +62,7 @@ def lib():
         L.orc_weno.restype = C.c_double
         L.orc_weno_beta.argtypes = [C.c_int, C.c_int, _dp]
         L.orc_weno_beta.restype = C.c_double
+        L.orc_char_matrices.argtypes = [C.c_double, _dp, _dp, _dp, _dp]
         L.orc_central_deriv.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp]
         L.orc_midpoint_weights.argtypes = [_dp]
         L.orc_viscosity.argtypes = [P, C.c_double]
@@ -85,7 +88,8 @@ class Case:
     def __init__(self, nx, ny, nz, *, gamma=1.4, Re=0.0, Ma=0.5, Pr=0.72, T_wall=1.0, T_ref=288.15,
                  visc_law=POWER, visc_omega=0.76, scheme=UD7, theta1=0.02, theta2=0.1,
                  visc_order=8, metric_mode=METRIC_NODAL, weno_eps=1e-6, bc_lo=(0, 0, 0),
-                 bc_hi=(0, 0, 0), nthreads=0, forced_cls=None, inflow=None, blowing=None):
+                 bc_hi=(0, 0, 0), nthreads=0, forced_cls=None, inflow=None, blowing=None,
+                 recon_vars=RECON_COMPONENT):
         p = OrcParams()
         p.nx, p.ny, p.nz = nx, ny, nz
         for d in range(3):
@@ -96,6 +100,7 @@ class Case:
         p.scheme, p.theta1, p.theta2 = scheme, theta1, theta2
         p.visc_order, p.metric_mode, p.weno_eps = visc_order, metric_mode, weno_eps
         p.nthreads = nthreads
+        p.recon_vars = recon_vars
         self._keep = []
         if forced_cls is not None:
             fc = np.ascontiguousarray(forced_cls, dtype=np.uint8).ravel()
@@ -206,6 +211,14 @@ def weno(r, a, mask=None, eps=1e-6, return_omega=False, scale=1.0):
         mptr = C.cast(m, C.POINTER(C.c_int))
     v = lib().orc_weno(r, _ptr(a), mptr, eps, scale, _ptr(om))
     return (v, om) if return_omega else v
+
+
+def char_matrices(gamma, U, n):
+    """(S, S^-1) of Sec. 2.2.2 (Eq. 34-40) at conserved state U, normal n."""
+    U, n = _f64(U), _f64(n)
+    S, Si = np.empty((5, 5)), np.empty((5, 5))
+    _check(lib().orc_char_matrices(gamma, _ptr(U), _ptr(n), _ptr(S), _ptr(Si)), "char_matrices")
+    return S, Si
 
 
 def weno_beta(r, k, a):
