@@ -66,6 +66,7 @@ enum { CFD_UD7 = 0, CFD_WENO5 = 1, CFD_WENO7 = 2, CFD_HYBRID = 3 };  /* Table 2,
 enum { CFD_METRIC_NODAL = 0, CFD_METRIC_FSP = 1 };
 enum { CFD_FP64 = 0, CFD_FP32_BULK = 1 };
 enum { CFD_SENSOR_PLAIN = 0, CFD_SENSOR_MLP = 1 };
+enum { CFD_RECON_COMPONENT = 0, CFD_RECON_CHARACTERISTIC = 1 };  /* Sec. 2.2.2 */
 
 typedef struct {
     int nx, ny, nz;            /* nodes per direction, each >= 1 (>= 8 if not periodic) */
@@ -86,10 +87,17 @@ typedef struct {
     int precision;             /* CFD_FP64 or CFD_FP32_BULK */
     int sensor;                /* CFD_SENSOR_PLAIN or CFD_SENSOR_MLP */
     double weno_eps;           /* epsilon of the WENO weights (1e-6) */
+    int recon_vars;            /* CFD_RECON_COMPONENT, or CFD_RECON_CHARACTERISTIC: the WENO faces
+                                  reconstruct characteristic fields (Eq. 31-40) -- the split fluxes
+                                  of the stencil nodes projected with the left eigenvectors (Eq. 35)
+                                  at the averaged state (Eq. 32) and the interface normal
+                                  (alpha_j + alpha_{j+1})/|.|, mapped back with Eq. 34; UD7 faces
+                                  are linear and stay component-wise */
 } cfd_params;
 
 /* cfd_params with the paper's defaults: gamma 1.4, Pr 0.72, theta 0.02/0.1,
-   8th-order viscous terms, hybrid scheme, FP64, plain sensor, eps 1e-6. */
+   8th-order viscous terms, hybrid scheme, FP64, plain sensor, eps 1e-6,
+   component-wise reconstruction. */
 void cfd_default_params(cfd_params* p);
 
 /*

@@ -41,7 +41,8 @@ class CfdParams(C.Structure):
                 ("T_wall", C.c_double), ("T_ref", C.c_double), ("visc_law", C.c_int),
                 ("visc_omega", C.c_double), ("scheme", C.c_int), ("theta1", C.c_double),
                 ("theta2", C.c_double), ("visc_order", C.c_int), ("metric_mode", C.c_int),
-                ("precision", C.c_int), ("sensor", C.c_int), ("weno_eps", C.c_double)]
+                ("precision", C.c_int), ("sensor", C.c_int), ("weno_eps", C.c_double),
+                ("recon_vars", C.c_int)]
 
 
 class CfdError(RuntimeError):

@@ -135,6 +135,7 @@ static void fill_float_consts(Phys& ph)
     ph.epsf = (float)ph.eps;
     ph.gMa2f = (float)ph.gMa2;
     ph.invMaf = (float)(1.0 / ph.Ma);
+    ph.gammaf = (float)ph.gamma;
 }
 
 extern "C" void cfd_default_params(cfd_params* p)
@@ -179,6 +180,8 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
     if (!(p->gamma > 1.0) || !(p->Ma > 0.0)) return fail(ctx, CFD_EINVAL, "gamma must be > 1 and Ma > 0");
     if (p->Re > 0.0 && !(p->Pr > 0.0)) return fail(ctx, CFD_EINVAL, "Pr must be > 0");
     if (p->scheme < 0 || p->scheme > 3) return fail(ctx, CFD_EINVAL, "unknown scheme");
+    if (p->recon_vars != CFD_RECON_COMPONENT && p->recon_vars != CFD_RECON_CHARACTERISTIC)
+        return fail(ctx, CFD_EINVAL, "unknown recon_vars");
     if (p->visc_order != 6 && p->visc_order != 8) return fail(ctx, CFD_EINVAL, "visc_order must be 6 or 8");
     if (p->visc_law != CFD_SUTHERLAND && p->visc_law != CFD_POWER) return fail(ctx, CFD_EINVAL, "bad visc_law");
     if (p->visc_law == CFD_SUTHERLAND && !(p->T_ref > 0.0)) return fail(ctx, CFD_EINVAL, "T_ref must be > 0");
@@ -253,6 +256,7 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     ph.omega = p.visc_omega;
     ph.suth_s = p.visc_law == CFD_SUTHERLAND ? 110.4 / p.T_ref : 0.0;
     ph.scheme = p.scheme;
+    ph.charrec = p.recon_vars == CFD_RECON_CHARACTERISTIC;
     ph.th1 = p.theta1;
     ph.th2 = p.theta2;
     ph.eps = p.weno_eps;
@@ -397,7 +401,11 @@ static cfd_status launch_sweep_dir(cfd_ctx* ctx, SweepArgs& A, int kind, int par
     const Geo& g = ctx->g;
     const int n = DIR == 1 ? g.ny : g.nz, nother = DIR == 1 ? g.nz : g.ny;
     const int lo = g.per[DIR] ? 0 : 1, hi = g.per[DIR] ? n : n - 1;
-    if (kind == 0) {
+    if (ctx->ph.charrec) {
+        // characteristic reconstruction: 16-node tiles only
+        dim3 grid((g.nx + 31) / 32, nother, (hi - lo + 15) / 16);
+        k_sweep_t<R, DIR, EP, 16, true><<<grid, 256, tile_smem_bytes<R, 16>(), ctx->stream>>>(A);
+    } else if (kind == 0) {
         A.seg_len = param;
         const long long nseg = (hi - lo + param - 1) / param;
         const long long warps = (long long)((g.nx + 31) / 32) * nother * nseg;
@@ -422,9 +430,17 @@ static cfd_status launch_sweeps(cfd_ctx* ctx, SweepArgs& A, cudaEvent_t* ev = nu
         int lo = g.per[0] ? 0 : 1, hi = g.per[0] ? g.nx : g.nx - 1;
         int nb = ctx->bx;
         dim3 grid((hi - lo + nb - 1) / nb, g.ny, g.nz);
-        if (nb == 32) k_sweep_x<R, 32, EP_STORE><<<grid, 32, 0, ctx->stream>>>(A);
-        else if (nb == 64) k_sweep_x<R, 64, EP_STORE><<<grid, 64, 0, ctx->stream>>>(A);
-        else k_sweep_x<R, 128, EP_STORE><<<grid, 128, 0, ctx->stream>>>(A);
+        if (ctx->ph.charrec) {
+            if (nb == 32) k_sweep_x<R, 32, EP_STORE, true><<<grid, 32, 0, ctx->stream>>>(A);
+            else if (nb == 64) k_sweep_x<R, 64, EP_STORE, true><<<grid, 64, 0, ctx->stream>>>(A);
+            else k_sweep_x<R, 128, EP_STORE, true><<<grid, 128, 0, ctx->stream>>>(A);
+        } else if (nb == 32) {
+            k_sweep_x<R, 32, EP_STORE><<<grid, 32, 0, ctx->stream>>>(A);
+        } else if (nb == 64) {
+            k_sweep_x<R, 64, EP_STORE><<<grid, 64, 0, ctx->stream>>>(A);
+        } else {
+            k_sweep_x<R, 128, EP_STORE><<<grid, 128, 0, ctx->stream>>>(A);
+        }
         LAUNCH_CHECK();
     }
     if (ev) cudaEventRecord(ev[1], ctx->stream);
@@ -457,6 +473,9 @@ static cudaError_t set_sweep_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 32>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile_smem_bytes<R, 16>());
     return e;
 }
 
@@ -782,7 +801,7 @@ static void batch_tiles(const Geo& g, int kind, int out[3])
         return g.per[d] ? n : n - 2;
     };
     switch (kind) {
-    case MK_NODE: out[0] = cdiv(g.nx, 128); out[1] = g.ny; out[2] = g.nz; break;
+    case MK_NODE: out[0] = (int)((g.N + 127) / 128); out[1] = 1; out[2] = 1; break;  // flat node runs
     case MK_VISC: out[0] = cdiv(g.nx, 32); out[1] = cdiv(g.ny, 8); out[2] = cdiv(g.nz, kBatchTZ); break;
     case MK_SX: out[0] = cdiv(span(0), kBatchBX); out[1] = g.ny; out[2] = g.nz; break;
     case MK_T1: out[0] = cdiv(g.nx, 32); out[1] = g.nz; out[2] = cdiv(span(1), kBatchTL); break;
@@ -864,6 +883,8 @@ static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids
             ctx->msg = "block " + std::to_string(b) + ": " + sb->msg;
             return st;
         }
+        if (sb->g.N >= (1LL << 31))
+            return fail(ctx, CFD_EINVAL, "block " + std::to_string(b) + ": ensemble blocks hold fewer than 2^31 nodes");
     }
     // per-stage argument tables (stage 1: Uk = U + dt L(U); 2: Uk = 3/4 U + 1/4(Uk + dt L);
     // 3: U = 1/3 U + 2/3 (Uk + dt L)), sharing the ensemble's dt
@@ -926,9 +947,12 @@ extern "C" cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_gri
         if (st != CFD_OK) return st;
         const cfd_params &p = params[b], &p0 = params[0];
         if (p.precision != p0.precision || p.scheme != p0.scheme || (p.Re > 0.0) != (p0.Re > 0.0) ||
-            p.visc_order != p0.visc_order || p.metric_mode != p0.metric_mode || p.sensor != p0.sensor)
+            p.visc_order != p0.visc_order || p.metric_mode != p0.metric_mode || p.sensor != p0.sensor ||
+            p.recon_vars != p0.recon_vars)
             return fail(nullptr, CFD_EINVAL,
                         "all blocks of a batch share precision, scheme, viscous/inviscid, visc_order and sensor");
+        if (p.recon_vars != CFD_RECON_COMPONENT)
+            return fail(nullptr, CFD_EUNSUPPORTED, "characteristic reconstruction: single-block contexts only");
     }
     cfd_ctx* ctx = new (std::nothrow) cfd_ctx();
     if (!ctx) return fail(nullptr, CFD_ENOMEM, "host allocation");
@@ -1343,6 +1367,7 @@ static void fill_phys(Phys& ph, const cfd_params& p)
     ph.omega = p.visc_omega;
     ph.suth_s = p.visc_law == CFD_SUTHERLAND ? 110.4 / p.T_ref : 0.0;
     ph.scheme = p.scheme;
+    ph.charrec = p.recon_vars == CFD_RECON_CHARACTERISTIC;
     ph.th1 = p.theta1;
     ph.th2 = p.theta2;
     ph.eps = p.weno_eps;
@@ -1361,6 +1386,8 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
     if (st != CFD_OK) return st;
     if (params->precision != CFD_FP64)
         return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc computes in FP64 only");
+    if (params->recon_vars != CFD_RECON_COMPONENT)
+        return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc reconstructs component-wise only");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > kMaxNodes)
         return fail(nullptr, CFD_ENOMEM, "cfd_rhs_noalloc: grid has more than CFD_NOALLOC_MAX_NODES nodes");

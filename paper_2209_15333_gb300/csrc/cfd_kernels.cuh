@@ -38,11 +38,12 @@ struct Phys {
     int viscous, visc_law;
     double omega, suth_s;  // power exponent, S/T_ref
     int scheme;            // 0 UD7, 1 WENO5, 2 WENO7, 3 HYBRID
+    int charrec;           // WENO faces reconstruct characteristic fields (Sec. 2.2.2)
     double th1, th2, eps;
     int vorder;
     // the constants rounded once to float, for the FP32 kernels (no
     // double-to-float conversion in the loops: it runs on the FP64 pipe)
-    float gm1f, inv_gm1f, inv2gf, invRef, kcoeff, omegaf, suth_sf, th1f, th2f, epsf, gMa2f, invMaf;
+    float gm1f, inv_gm1f, inv2gf, invRef, kcoeff, omegaf, suth_sf, th1f, th2f, epsf, gMa2f, invMaf, gammaf;
 };
 
 template <class R>
@@ -93,11 +94,30 @@ __device__ __forceinline__ float metr<float>(const Geo& g, int e, long long mi)
 
 // node (i, j, k) of a node-parallel kernel on a (x-chunks, ny, nz) grid of
 // (virtual) blocks vb; the body that follows runs only when i < nx
-#define NODE_IJK(g)                                                                                   \
-    const int i = vb.x * blockDim.x + threadIdx.x;                                                    \
-    const int j = vb.y, k = vb.z;                                                                     \
-    const long long n = (long long)i + (long long)(g).nx * ((long long)j + (long long)(g).ny * k);     \
-    if (i < (g).nx)
+// Node kernels: vb = (x segment, j, k) with x on threads, or (FLAT) vb.x
+// counts runs of blockDim.x consecutive nodes of the flattened grid (N < 2^31;
+// used by the ensemble, whose blocks can be narrower than a CTA).
+#define NODE_IJK_SEL(g, FLAT)                                                                         \
+    int i, j, k;                                                                                      \
+    long long n;                                                                                      \
+    bool node_ok_;                                                                                    \
+    if constexpr (FLAT) {                                                                             \
+        const unsigned t_ = vb.x * blockDim.x + threadIdx.x;                                          \
+        const unsigned r_ = t_ / (unsigned)(g).nx;                                                    \
+        i = (int)(t_ - r_ * (unsigned)(g).nx);                                                        \
+        j = (int)(r_ % (unsigned)(g).ny);                                                             \
+        k = (int)(r_ / (unsigned)(g).ny);                                                             \
+        n = (long long)t_;                                                                            \
+        node_ok_ = n < (g).N;                                                                         \
+    } else {                                                                                          \
+        i = vb.x * blockDim.x + threadIdx.x;                                                          \
+        j = vb.y;                                                                                     \
+        k = vb.z;                                                                                     \
+        n = (long long)i + (long long)(g).nx * ((long long)j + (long long)(g).ny * k);                \
+        node_ok_ = i < (g).nx;                                                                        \
+    }                                                                                                 \
+    if (node_ok_)
+#define NODE_IJK(g) NODE_IJK_SEL(g, false)
 
 __device__ __forceinline__ bool is_bnd(const Geo& g, int i, int j, int k)
 {
@@ -159,7 +179,7 @@ struct SweepArgs {
 // oracle's (no contraction), so that p -- and with it the sensor's class
 // decisions -- are bit-identical to a plain IEEE evaluation.
 // ---------------------------------------------------------------------------
-template <class RT>
+template <class RT, bool FLAT = false>
 __device__ __forceinline__ void prim_body(const SweepArgs& A, uint3 vb)
 {
     const Geo& g = A.g;
@@ -168,7 +188,7 @@ __device__ __forceinline__ void prim_body(const SweepArgs& A, uint3 vb)
     RT* __restrict__ P = (RT*)A.P;
     int* err = A.err;
     const long long N = g.N;
-    NODE_IJK(g)
+    NODE_IJK_SEL(g, FLAT)
     {
         double rho = U[n];
         double u = __ddiv_rn(U[N + n], rho);
@@ -207,6 +227,7 @@ __device__ __forceinline__ bool near_wall(const Geo& g, int i, int j, int k)
     return false;
 }
 
+template <bool FLAT = false>
 __device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
 {
     const Geo& g = A.g;
@@ -216,7 +237,7 @@ __device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
     const uint8_t* __restrict__ cls_prev = A.cls_io;
     int* err = A.err;
     const long long N = g.N;
-    NODE_IJK(g)
+    NODE_IJK_SEL(g, FLAT)
     {
         float rho, u, v, w, p, T, c;
         if (cls_prev[n] != 0 || near_wall(g, i, j, k)) {
@@ -259,6 +280,7 @@ __device__ __forceinline__ double sensor_phi(double pm, double p0, double pp)
     return __ddiv_rn(num, den);
 }
 
+template <bool FLAT = false>
 __device__ __forceinline__ void sensor_body(const SweepArgs& A, uint3 vb)
 {
     const Geo& g = A.g;
@@ -266,7 +288,7 @@ __device__ __forceinline__ void sensor_body(const SweepArgs& A, uint3 vb)
     const double* __restrict__ p = (const double*)A.P + 4 * g.N;
     uint8_t* __restrict__ cls = A.cls_io;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    NODE_IJK(g)
+    NODE_IJK_SEL(g, FLAT)
     {
         double p0 = p[n];
         double phi[3];
@@ -290,6 +312,7 @@ __device__ __forceinline__ void sensor_body(const SweepArgs& A, uint3 vb)
 }
 
 // the same sensor in FP32 arithmetic on FP32 pressures (mixed precision)
+template <bool FLAT = false>
 __device__ __forceinline__ void sensor32_body(const SweepArgs& A, uint3 vb)
 {
     const Geo& g = A.g;
@@ -298,7 +321,7 @@ __device__ __forceinline__ void sensor32_body(const SweepArgs& A, uint3 vb)
     uint8_t* __restrict__ cls = A.cls_io;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const float th1 = ph.th1f, th2 = ph.th2f;
-    NODE_IJK(g)
+    NODE_IJK_SEL(g, FLAT)
     {
         float p0 = p[n];
         const int pos[3] = {i, j, k};
@@ -754,6 +777,89 @@ __device__ __forceinline__ R face_flux(int use, const R fp8[8], const R fm8[8], 
     return recon<R>(use, vp, eps, isc, maskp) + recon<R>(use, vm, eps, isc, maskm);
 }
 
+// ---------------------------------------------------------------------------
+// characteristic-variable reconstruction of one WENO face (Sec. 2.2.2,
+// Eq. 31-40): the interface state U_{j+1/2} = (U_j + U_{j+1})/2 (Eq. 32,
+// from the FP64 state), the unit normal n of the face, the left eigenvectors
+// S (Eq. 35) applied to the split fluxes of the eight stencil nodes, one
+// reconstruction per characteristic field, and the right eigenvectors
+// (Eq. 34) applied to the result.  fpl(o, q) / fml(o, q): component q of
+// f+ / f- at stencil node j-3+o, o = 0..7.
+// ---------------------------------------------------------------------------
+template <class R, class FP, class FM>
+__device__ __forceinline__ void face_flux_char(const Phys& ph, int use, R eps, R isc, int mp, int mm,
+                                               const double* __restrict__ U, long long N, long long na,
+                                               long long nb, R n1, R n2, R n3, FP fpl, FM fml, R out[5])
+{
+    const double r0 = 0.5 * (U[na] + U[nb]);
+    const double r1 = 0.5 * (U[N + na] + U[N + nb]);
+    const double r2 = 0.5 * (U[2 * N + na] + U[2 * N + nb]);
+    const double r3 = 0.5 * (U[3 * N + na] + U[3 * N + nb]);
+    const double r4 = 0.5 * (U[4 * N + na] + U[4 * N + nb]);
+    const R rho = (R)r0, ri = (R)1 / rho;
+    const R u = (R)r1 * ri, v = (R)r2 * ri, w = (R)r3 * ri;
+    const R V = (R)0.5 * (u * u + v * v + w * w);                         // Eq. 25
+    const R p = pk<R>(ph.gm1, ph.gm1f) * ((R)r4 - rho * V);
+    const R c2 = pk<R>(ph.gamma, ph.gammaf) * p * ri;
+    const R c = sqrt(c2);
+    const R H = V + c2 * pk<R>(ph.inv_gm1, ph.inv_gm1f);                  // Eq. 36
+    const R kap = pk<R>(ph.gm1, ph.gm1f) / c2, kap1 = (R)0.5 * kap;       // Eq. 37
+    const R chi = (R)0.5 / c;
+    R l1, l2, l3;                                                          // Eq. 39
+    if (fabs(n3) <= fabs(n2)) {
+        const R r = (R)1 / sqrt(n1 * n1 + n2 * n2);
+        l1 = -n2 * r; l2 = n1 * r; l3 = (R)0;
+    } else {
+        const R r = (R)1 / sqrt(n1 * n1 + n3 * n3);
+        l1 = -n3 * r; l2 = (R)0; l3 = n1 * r;
+    }
+    const R m1 = n2 * l3 - n3 * l2, m2 = n3 * l1 - n1 * l3, m3 = n1 * l2 - n2 * l1;  // Eq. 40
+    const R un = u * n1 + v * n2 + w * n3, ul = u * l1 + v * l2 + w * l3, um = u * m1 + v * m2 + w * m3;
+    R gh[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        R s0, s1, s2, s3, s4;  // row k of S (Eq. 35)
+        if (k == 0) { s0 = (R)1 - kap * V; s1 = kap * u; s2 = kap * v; s3 = kap * w; s4 = -kap; }
+        else if (k == 1) { s0 = -ul; s1 = l1; s2 = l2; s3 = l3; s4 = (R)0; }
+        else if (k == 2) { s0 = -um; s1 = m1; s2 = m2; s3 = m3; s4 = (R)0; }
+        else if (k == 3) {
+            s0 = kap1 * V + chi * un; s1 = -chi * n1 - kap1 * u; s2 = -chi * n2 - kap1 * v;
+            s3 = -chi * n3 - kap1 * w; s4 = kap1;
+        } else {
+            s0 = kap1 * V - chi * un; s1 = chi * n1 - kap1 * u; s2 = chi * n2 - kap1 * v;
+            s3 = chi * n3 - kap1 * w; s4 = kap1;
+        }
+        R vp[7], vm[7];
+#pragma unroll
+        for (int o = 0; o < 7; ++o) {
+            vp[o] = s0 * fpl(o, 0) + s1 * fpl(o, 1) + s2 * fpl(o, 2) + s3 * fpl(o, 3) + s4 * fpl(o, 4);
+            vm[o] = s0 * fml(7 - o, 0) + s1 * fml(7 - o, 1) + s2 * fml(7 - o, 2) + s3 * fml(7 - o, 3) +
+                    s4 * fml(7 - o, 4);
+        }
+        gh[k] = recon<R>(use, vp, eps, isc, mp) + recon<R>(use, vm, eps, isc, mm);
+    }
+    // columns of S^-1 (Eq. 34)
+    out[0] = gh[0] + gh[3] + gh[4];
+    out[1] = u * gh[0] + l1 * gh[1] + m1 * gh[2] + (u - c * n1) * gh[3] + (u + c * n1) * gh[4];
+    out[2] = v * gh[0] + l2 * gh[1] + m2 * gh[2] + (v - c * n2) * gh[3] + (v + c * n2) * gh[4];
+    out[3] = w * gh[0] + l3 * gh[1] + m3 * gh[2] + (w - c * n3) * gh[3] + (w + c * n3) * gh[4];
+    out[4] = V * gh[0] + ul * gh[1] + um * gh[2] + (H - c * un) * gh[3] + (H + c * un) * gh[4];
+}
+
+// unit normal of face j+1/2 in direction d from the metric vectors alpha of
+// its two nodes (metric indices ma, mb)
+template <class R>
+__device__ __forceinline__ void face_normal(const Geo& g, int d, long long ma, long long mb, R* n1, R* n2, R* n3)
+{
+    const R a1 = metr<R>(g, M_ALPHA + 3 * d, ma) + metr<R>(g, M_ALPHA + 3 * d, mb);
+    const R a2 = metr<R>(g, M_ALPHA + 3 * d + 1, ma) + metr<R>(g, M_ALPHA + 3 * d + 1, mb);
+    const R a3 = metr<R>(g, M_ALPHA + 3 * d + 2, ma) + metr<R>(g, M_ALPHA + 3 * d + 2, mb);
+    const R r = (R)1 / sqrt(a1 * a1 + a2 * a2 + a3 * a3);
+    *n1 = a1 * r;
+    *n2 = a2 * r;
+    *n3 = a3 * r;
+}
+
 // scheme class of face j+1/2 (nodes j-3..j+4 of one line): returns use and masks.
 // Non-periodic lines: a face whose stencil leaves [0, n-1] uses masked WENO5.
 __device__ __forceinline__ int face_use(const Phys& ph, int per, int n, int j, int cmax, int* maskp,
@@ -1119,7 +1225,8 @@ __device__ __forceinline__ R node_split(const SweepArgs& A, int d, long long n, 
 }
 
 // xi sweep: one CTA per segment of BX nodes of one x-line, halo of 4 nodes.
-template <class R, int BX, int EP>
+// CHAR: WENO faces reconstruct characteristic fields (Sec. 2.2.2).
+template <class R, int BX, int EP, bool CHAR = false>
 __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
 {
     __shared__ __align__(16) R sf[10][BX + 12];  // rows padded so a 12-value window never leaves a row
@@ -1222,6 +1329,7 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
             const int code = suse[slot];
             if (code == 0xff) continue;
             const int use = code & 3, mp = (code >> 2) & 7, mm = code >> 5;
+            if (CHAR && use) continue;  // characteristic faces below
             const R isc = sisc[slot];
             R p8[8], m8[8];
 #pragma unroll
@@ -1230,6 +1338,25 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
                 m8[o] = mv[u + o];
             }
             sh[q][slot] = face_flux<R>(use, p8, m8, pk<R>(A.ph.eps, A.ph.epsf), isc, mp, mm);
+        }
+    }
+    if constexpr (CHAR) {
+        // WENO faces in characteristic variables: one thread per face, all
+        // five components (slots other threads' jobs skipped above)
+        for (int slot = t; slot <= BX; slot += BX) {
+            const int code = suse[slot];
+            if (code == 0xff || (code & 3) == 0) continue;
+            const int jf = i0 - 1 + slot;
+            const int ia = per ? wrapi(jf, n) : jf, ib = per ? wrapi(jf + 1, n) : jf + 1;
+            R n1, n2, n3;
+            face_normal<R>(g, 0, midx(g, ia, j, row + ia), midx(g, ib, j, row + ib), &n1, &n2, &n3);
+            R out[5];
+            face_flux_char<R>(A.ph, code & 3, pk<R>(A.ph.eps, A.ph.epsf), sisc[slot], (code >> 2) & 7, code >> 5,
+                              A.U, g.N, row + ia, row + ib, n1, n2, n3,
+                              [&](int o, int q) { return sf[q][slot + o]; },
+                              [&](int o, int q) { return sf[5 + q][slot + o]; }, out);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) sh[q][slot] = out[q];
         }
     }
     __syncthreads();
@@ -1362,7 +1489,7 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
 // once (many loads in flight), faces are computed from shared memory, then
 // differenced.  The halo costs 8/TL extra splits -- cheap in FP32, where the
 // streaming form is latency-bound instead.
-template <class R, int DIR, int EP, int TL>
+template <class R, int DIR, int EP, int TL, bool CHAR = false>
 __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
 {
     constexpr int ROWS = TL + 8;
@@ -1462,6 +1589,27 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
                                      metr<R>(g, M_SIG + DIR, midx(g, i, DIR == 1 ? mb : o, nb)));
         }
     }
+    if constexpr (CHAR) {
+        // WENO faces in characteristic variables (all five components)
+#pragma unroll
+        for (int u = 0; u < FPT; ++u) {
+            if (usev[u] <= 0) continue;
+            if (!lane_ok) {
+#pragma unroll
+                for (int q = 0; q < 5; ++q) fh[u][q] = (R)0;
+                continue;
+            }
+            const int f = fbase + u, jf = m0 - 1 + f;
+            const int ma = per ? wrapi(jf, n) : jf, mb = per ? wrapi(jf + 1, n) : jf + 1;
+            const long long na = base + (long long)ma * stride, nb = base + (long long)mb * stride;
+            R n1, n2, n3;
+            face_normal<R>(g, DIR, midx(g, i, DIR == 1 ? ma : o, na), midx(g, i, DIR == 1 ? mb : o, nb), &n1, &n2,
+                           &n3);
+            face_flux_char<R>(A.ph, usev[u], pk<R>(A.ph.eps, A.ph.epsf), iscv[u], mpv[u], mmv[u], A.U, N, na, nb,
+                              n1, n2, n3, [&](int b, int q) { return sf[((f + b) * 10 + q) * 32 + lane]; },
+                              [&](int b, int q) { return sf[((f + b) * 10 + 5 + q) * 32 + lane]; }, fh[u]);
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         R pv[WIN], mv[WIN];
@@ -1477,6 +1625,7 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
                 fh[u][q] = (R)0;
                 continue;
             }
+            if (CHAR && usev[u] > 0) continue;  // done above
             R p8[8], m8[8];
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
@@ -1667,19 +1816,19 @@ __global__ void k_advance_time(double* t, const double* dt)
 // ---------------------------------------------------------------------------
 template <class RT>
 __global__ void k_prim(SweepArgs A) { prim_body<RT>(A, blockIdx); }
-__global__ void k_prim_mixed(SweepArgs A) { prim_mixed_body(A, blockIdx); }
-__global__ void k_sensor(SweepArgs A) { sensor_body(A, blockIdx); }
-__global__ void k_sensor32(SweepArgs A) { sensor32_body(A, blockIdx); }
+__global__ void k_prim_mixed(SweepArgs A) { prim_mixed_body<false>(A, blockIdx); }
+__global__ void k_sensor(SweepArgs A) { sensor_body<false>(A, blockIdx); }
+__global__ void k_sensor32(SweepArgs A) { sensor32_body<false>(A, blockIdx); }
 template <class R>
 __global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R>(A, blockIdx); }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<R, TZ>(A, blockIdx); }
-template <class R, int BX, int EP>
-__global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A) { sweep_x_body<R, BX, EP>(A, blockIdx); }
-template <class R, int DIR, int EP, int TL>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (TL == 16 ? 4 : 3) : 1) k_sweep_t(SweepArgs A)
+template <class R, int BX, int EP, bool CHAR = false>
+__global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A) { sweep_x_body<R, BX, EP, CHAR>(A, blockIdx); }
+template <class R, int DIR, int EP, int TL, bool CHAR = false>
+__global__ void __launch_bounds__(256, CHAR ? 1 : (sizeof(R) == 4 ? (TL == 16 ? 4 : 3) : 1)) k_sweep_t(SweepArgs A)
 {
-    sweep_t_body<R, DIR, EP, TL>(A, blockIdx);
+    sweep_t_body<R, DIR, EP, TL, CHAR>(A, blockIdx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1713,15 +1862,20 @@ __device__ __forceinline__ int batch_find(const BatchMap& m, int item, uint3* v)
     return lo;
 }
 
-// The block's argument record is copied to shared memory when a CTA moves to
-// a new block (consecutive items of a CTA mostly stay in one block), so the
-// bodies read it from shared memory instead of global memory.
-#define BATCH_LOOP(BODY, SYNC)                                                                        \
+// CONTIG: each CTA takes a contiguous range of items (node kernels: its
+// items stay in one block); otherwise items are dealt round-robin, so CTAs
+// that run at the same time work on neighbouring tiles and share their halos
+// in L2.  The block's argument record is copied to shared memory when a CTA
+// moves to a new block, so the bodies read it from shared memory.
+#define BATCH_LOOP(BODY, SYNC, CONTIG)                                                                \
     __shared__ __align__(16) SweepArgs sA;                                                            \
     constexpr int AW = (int)(sizeof(SweepArgs) / sizeof(int));                                        \
     int cached = -1;                                                                                  \
     const int total = __ldg(m.prefix + m.nb);                                                         \
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {                                    \
+    const int per_cta = CONTIG ? (total + gridDim.x - 1) / gridDim.x : 1;                             \
+    const int item_end = CONTIG ? min(total, ((int)blockIdx.x + 1) * per_cta) : total;                \
+    const int item_step = CONTIG ? 1 : (int)gridDim.x;                                                \
+    for (int item = blockIdx.x * per_cta; item < item_end; item += item_step) {                       \
         uint3 v;                                                                                      \
         const int b = batch_find(m, item, &v);                                                        \
         if (b != cached) {                                                                            \
@@ -1736,18 +1890,18 @@ __device__ __forceinline__ int batch_find(const BatchMap& m, int item, uint3* v)
     }
 
 template <class RT>
-__global__ void kb_prim(BatchMap m) { BATCH_LOOP(prim_body<RT>, false) }
-__global__ void kb_prim_mixed(BatchMap m) { BATCH_LOOP(prim_mixed_body, false) }
-__global__ void kb_sensor(BatchMap m) { BATCH_LOOP(sensor_body, false) }
-__global__ void kb_sensor32(BatchMap m) { BATCH_LOOP(sensor32_body, false) }
+__global__ void kb_prim(BatchMap m) { BATCH_LOOP((prim_body<RT, true>), false, true) }
+__global__ void kb_prim_mixed(BatchMap m) { BATCH_LOOP(prim_mixed_body<true>, false, true) }
+__global__ void kb_sensor(BatchMap m) { BATCH_LOOP(sensor_body<true>, false, true) }
+__global__ void kb_sensor32(BatchMap m) { BATCH_LOOP(sensor32_body<true>, false, true) }
 template <class R, int TZ>
-__global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((visc25_body<R, TZ>), true) }
+__global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((visc25_body<R, TZ>), true, false) }
 template <class R, int BX, int EP>
-__global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m) { BATCH_LOOP((sweep_x_body<R, BX, EP>), true) }
+__global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m) { BATCH_LOOP((sweep_x_body<R, BX, EP>), true, false) }
 template <class R, int DIR, int EP, int TL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) kb_sweep_t(BatchMap m)
 {
-    BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true)
+    BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true, false)
 }
 
 }  // namespace cfdk
