@@ -1899,7 +1899,7 @@ __global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((
 template <class R, int BX, int EP>
 __global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m) { BATCH_LOOP((sweep_x_body<R, BX, EP>), true, false) }
 template <class R, int DIR, int EP, int TL>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) kb_sweep_t(BatchMap m)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (TL == 16 ? 4 : 3) : 1) kb_sweep_t(BatchMap m)
 {
     BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true, false)
 }
