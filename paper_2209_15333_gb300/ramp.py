@@ -52,6 +52,35 @@ def wall_quantities(U, met2, Ma, Tw, T_ref, gamma=1.4, Re=RE):
     return pw, cf
 
 
+def van_driest(y, u, rho, mu_w, Re):
+    """Van Driest transformed mean-velocity profile in wall units along one
+    wall-normal line (y from the wall, y[0] = 0; u tangential velocity, rho
+    density, span/time-averaged):
+        u_VD = int_0^u sqrt(rho/rho_w) du,  u_tau = sqrt(tau_w/rho_w),
+        tau_w = (mu_w/Re) du/dy|_w,  y+ = Re rho_w u_tau y / mu_w,
+        u_VD+ = u_VD / u_tau
+    (trapezoidal rule; du/dy at the wall second-order one-sided)."""
+    y, u, rho = (np.asarray(a, dtype=np.float64) for a in (y, u, rho))
+    h1, h2 = y[1] - y[0], y[2] - y[0]
+    dudy = (u[1] * h2 * h2 - u[2] * h1 * h1 - u[0] * (h2 * h2 - h1 * h1)) / (h1 * h2 * (h2 - h1))
+    tau_w = mu_w / Re * dudy
+    rho_w = rho[0]
+    u_tau = np.sqrt(abs(tau_w) / rho_w)
+    w = np.sqrt(rho / rho_w)
+    u_vd = np.concatenate([[0.0], np.cumsum(0.5 * (w[1:] + w[:-1]) * np.diff(u))])
+    return Re * rho_w * u_tau * y / mu_w, u_vd / u_tau, u_tau
+
+
+def station_profile(U, rc, x_station):
+    """span-averaged density and tangential velocity along the eta line
+    nearest to x_station, with the wall distance"""
+    i = int(np.argmin(np.abs(rc["X"][0] - x_station)))
+    rho = U[0, :, :, i].mean(axis=0)
+    u = (U[1, :, :, i] / U[0, :, :, i]).mean(axis=0)
+    y = rc["Y"][:, i] - rc["Y"][0, i]
+    return y, u, rho
+
+
 def case_shape(case, scale=1):
     nx, ny, nz = CASES[case]["shape"]
     return nx // scale, ny // scale, max(8, nz // scale)
@@ -136,6 +165,11 @@ def compare(case, steps, sample_every=None, mlp_path=None, scale=1, cfl=0.3):
         rec["class_fraction"] = (np.bincount(cls.ravel(), minlength=3)[:3] / cls.size).tolist()
         rec["gpu_seconds"] = t_gpu
         stats[name] = rec
+        y, u, rho = station_profile(s.get_state(), rc, -5.0)
+        sw = 110.4 / c["T_ref"]
+        mu_w = c["Tw"] ** 1.5 * (1.0 + sw) / (c["Tw"] + sw)
+        yp, up, utau = van_driest(y, u, rho, mu_w, RE)
+        rec["van_driest_x-5"] = {"y_plus": yp.tolist(), "u_vd_plus": up.tolist(), "u_tau": float(utau)}
         if s is not ref:
             s.close()
     ref.close()
@@ -148,6 +182,9 @@ def compare(case, steps, sample_every=None, mlp_path=None, scale=1, cfl=0.3):
         stats[name]["pw_max_rel_err"] = float(np.abs(pw1 - pw0).max() / np.abs(pw0).max())
         stats[name]["cf_max_rel_err"] = float(np.abs(cf1 - cf0).max() / np.abs(cf0).max())
         stats[name]["speedup_vs_fp64"] = stats[name]["point_stage_per_s"] / base["point_stage_per_s"]
+        u0 = np.array(base["van_driest_x-5"]["u_vd_plus"])
+        u1 = np.array(stats[name]["van_driest_x-5"]["u_vd_plus"])
+        stats[name]["u_vd_plus_max_rel_err"] = float(np.abs(u1 - u0).max() / np.abs(u0).max())
     out["results"] = stats
     return out
 
@@ -164,7 +201,8 @@ def main():
     a = ap.parse_args()
     res = compare(a.case, a.steps, a.sample_every or None, a.mlp or None, a.scale, a.cfl)
     summary = {k: v for k, v in res.items() if k != "results"}
-    summary["results"] = {n: {k: v for k, v in r.items() if k not in ("pw", "cf")} for n, r in res["results"].items()}
+    summary["results"] = {n: {k: v for k, v in r.items() if k not in ("pw", "cf", "van_driest_x-5")}
+                          for n, r in res["results"].items()}
     print(json.dumps(summary))
     if a.out:
         with open(a.out, "w") as f:
