@@ -51,8 +51,14 @@ enum {
     CFD_BC_PERIODIC = 0,        /* both faces of the direction must say so */
     CFD_BC_WALL_ISOTHERMAL = 1, /* u = 0 (+ blowing), T = T_wall, p_w = (4 p1 - p2)/3 */
     CFD_BC_INFLOW = 2,          /* Dirichlet from cfd_set_inflow (xi-low face) */
-    CFD_BC_OUTFLOW_EXTRAP = 3   /* zeroth-order extrapolation of primitives */
+    CFD_BC_OUTFLOW_EXTRAP = 3,  /* zeroth-order extrapolation of primitives */
+    CFD_BC_HALO = 4             /* the first / last CFD_HALO_WIDTH layers are ghost layers that
+                                   cfd_set_halo_links fills from a neighbouring block */
 };
+
+/* ghost layers per HALO face: the viscous terms reach 8 nodes (a central
+   derivative of node fluxes that are central derivatives themselves) */
+#define CFD_HALO_WIDTH 8
 
 /* how the metrics argument of cfd_create is laid out */
 enum {
@@ -127,6 +133,26 @@ cfd_status cfd_create(cfd_ctx** out, const cfd_grid* grid, const double* metrics
 cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_grid* grids,
                             const double* const* metrics, int metrics_on_device,
                             const cfd_params* params, void* stream);
+
+/*
+ * Multi-block domains on one GPU (the single-GPU form of the paper's block
+ * decomposition, Sec. 3): blocks of an ensemble exchange ghost layers.
+ * links[(b * 3 + d) * 2 + side] is the block whose interior lies beyond face
+ * (d, side) of block b, or -1.  A linked face must be CFD_BC_HALO; the grids
+ * of the two blocks must agree in the two other directions (ghost layers
+ * included), and a HALO direction needs at least 2 * CFD_HALO_WIDTH + 1
+ * nodes.  Block b's ghost layers at the low face receive the neighbour's
+ * layers [n - 2H, n - H), at the high face its layers [H, 2H) (H =
+ * CFD_HALO_WIDTH), direction by direction (xi, then eta, then zeta, each
+ * copying whole planes, so edges and corners are filled too).  The exchange
+ * runs once here on the current states and, inside cfd_step, before every
+ * RK3 stage; a block may be its own neighbour (periodic through ghosts).
+ * Interior nodes then evolve exactly as in the undivided domain; ghost layers
+ * of the state returned by cfd_get_state are stale.  links = NULL removes the
+ * links.  Errors: CFD_EINVAL (not an ensemble, bad index, face not HALO,
+ * size mismatch).
+ */
+cfd_status cfd_set_halo_links(cfd_ctx* ctx, const int* links);
 
 /* Inflow profile for CFD_BC_INFLOW on the xi-low face: prim[5][ny] =
    rho, u, v, w, p per eta index, the same for every zeta (host memory). */
@@ -261,9 +287,10 @@ cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const
    four on its first cfd_rhs / cfd_step and keeps the fastest (cached per
    process by precision, grid and scheme); cfd_set_sweep_variant fixes one
    and turns the tuning off.  dir 0 selects the viscous node-flux kernel the
-   same way: kind 0 one thread per node reading its neighbours, kind 1 / 2 a
-   32 x 8 tile streaming along zeta in segments of 64 / 32 planes with a
-   9-plane shared ring (param ignored). */
+   same way: kind 0 one thread per node reading its neighbours (CTAs along
+   x rows), kind 1 / 2 a 32 x 8 tile streaming along zeta in segments of
+   64 / 32 planes with a 9-plane shared ring, kind 3 as kind 0 with CTAs of
+   32 x 4 nodes in x-y tiles (param ignored). */
 cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param);
 cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param);
 

@@ -11,7 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libcfd_gb300.so")
 
 CFD_OK, CFD_EINVAL, CFD_ENOMEM, CFD_ECUDA, CFD_ENONPHYS, CFD_ETIMEOUT, CFD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-BC_PERIODIC, BC_WALL_ISOTHERMAL, BC_INFLOW, BC_OUTFLOW_EXTRAP = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL_ISOTHERMAL, BC_INFLOW, BC_OUTFLOW_EXTRAP, BC_HALO = 0, 1, 2, 3, 4
+HALO_WIDTH = 8
 METRICS_3D, METRICS_2D, METRICS_UNIFORM = 0, 1, 2
 SUTHERLAND, POWER = 0, 1
 UD7, WENO5, WENO7, HYBRID = 0, 1, 2, 3
@@ -27,7 +28,7 @@ EXPORTS = ["cfd_default_params", "cfd_create", "cfd_create_batch", "cfd_set_infl
            "cfd_get_state", "cfd_rhs", "cfd_step", "cfd_cfl_dt", "cfd_get_flags", "cfd_force_flags",
            "cfd_get_time", "cfd_set_time", "cfd_sync", "cfd_last_error", "cfd_launch_count", "cfd_fma_peak",
            "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
-           "cfd_set_sensor_mlp", "cfd_sensor_features", "cfd_sensor_fallbacks",
+           "cfd_set_sensor_mlp", "cfd_sensor_features", "cfd_sensor_fallbacks", "cfd_set_halo_links",
            "cfd_destroy"]
 
 
@@ -92,6 +93,7 @@ def lib():
         L.cfd_set_sweep_variant.argtypes = [vp, C.c_int, C.c_int, C.c_int]
         L.cfd_get_sweep_variant.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.cfd_rhs_noalloc.argtypes = [C.POINTER(CfdGrid), C.POINTER(CfdParams), vp, vp, vp, vp]
+        L.cfd_set_halo_links.argtypes = [vp, vp]
         L.cfd_destroy.argtypes = [vp]
         L.cfd_destroy.restype = None
         for name in EXPORTS:

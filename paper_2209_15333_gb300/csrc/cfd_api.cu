@@ -60,6 +60,10 @@ struct cfd_ctx {
     int* d_maps = nullptr;                              // all prefix / gdim arrays
     BatchMap maps[3][5];                                // [stage][kind]
     int map_grid[5] = {0, 0, 0, 0, 0};                  // persistent grid per kind
+    // multi-block halo links: [0] between the U arrays, [1] between the Uk
+    // arrays; per direction
+    HaloLink* d_halo[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int n_halo[3] = {0, 0, 0};
     int* err = nullptr;             // device non-physical flag
     double* dt = nullptr;           // device scalars
     double* t = nullptr;
@@ -167,11 +171,13 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
         if (n[d] < 1) return fail(ctx, CFD_EINVAL, "grid dimension < 1");
         for (int side = 0; side < 2; ++side) {
             int t = side ? gr->bc_hi[d] : gr->bc_lo[d];
-            if (t < 0 || t > 3) return fail(ctx, CFD_EINVAL, "unknown boundary condition");
+            if (t < 0 || t > 4) return fail(ctx, CFD_EINVAL, "unknown boundary condition");
         }
         bool plo = gr->bc_lo[d] == CFD_BC_PERIODIC, phi = gr->bc_hi[d] == CFD_BC_PERIODIC;
         if (plo != phi) return fail(ctx, CFD_EINVAL, "periodic must be set on both faces of a direction");
         if (!plo && n[d] < 8) return fail(ctx, CFD_EINVAL, "non-periodic directions need >= 8 nodes");
+        if ((gr->bc_lo[d] == CFD_BC_HALO || gr->bc_hi[d] == CFD_BC_HALO) && n[d] < 2 * CFD_HALO_WIDTH + 1)
+            return fail(ctx, CFD_EINVAL, "a direction with ghost layers needs >= 2 CFD_HALO_WIDTH + 1 nodes");
         if (gr->bc_lo[d] == CFD_BC_INFLOW && d != 0) return fail(ctx, CFD_EINVAL, "inflow only on the xi-low face");
         if (gr->bc_hi[d] == CFD_BC_INFLOW) return fail(ctx, CFD_EINVAL, "inflow only on the xi-low face");
     }
@@ -205,6 +211,9 @@ static void free_all(cfd_ctx* c)
     c->sub.clear();
     for (int s = 0; s < 3; ++s)
         if (c->d_tbl[s]) cudaFree(c->d_tbl[s]);
+    for (int a = 0; a < 2; ++a)
+        for (int d = 0; d < 3; ++d)
+            if (c->d_halo[a][d]) cudaFree(c->d_halo[a][d]);
     if (c->d_maps) cudaFree(c->d_maps);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void* ptrs[] = {c->b.U, c->b.Uk, c->b.P, c->b.Fv, c->b.R, c->b.cls, c->b.cls_tune, c->met, c->metf, c->err, c->dt, c->t,
@@ -383,6 +392,9 @@ static cfd_status launch_visc(cfd_ctx* ctx, const SweepArgs& A, int kind)
     if (kind == 0) {
         const NodeLaunch nl = node_launch(g);
         k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+    } else if (kind == 3) {
+        dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
+        k_visc_flux<R, 4><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
     } else {
         const int tz = kind == 1 ? 64 : 32;
         dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + tz - 1) / tz);
@@ -603,7 +615,7 @@ static cfd_status autotune_t(cfd_ctx* ctx)
     }
     if (ctx->ph.viscous) {
         float best = 1e30f;
-        for (int kind = 0; kind < 3 && st == CFD_OK; ++kind) {
+        for (int kind = 0; kind < 4 && st == CFD_OK; ++kind) {
             for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, ctx->stream);
                 st = launch_visc<R>(ctx, A, kind);
@@ -659,7 +671,7 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
 {
     if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
     if (dir == 0) {
-        if (kind < 0 || kind > 2) return fail(ctx, CFD_EINVAL, "viscous kernel kind must be 0, 1 or 2");
+        if (kind < 0 || kind > 3) return fail(ctx, CFD_EINVAL, "viscous kernel kind must be 0, 1, 2 or 3");
         ctx->visc_kind = kind;
         ctx->tuned = true;
         ctx->graph_valid = false;
@@ -934,6 +946,70 @@ static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids
     return CFD_OK;
 }
 
+static cfd_status launch_halo(cfd_ctx* ctx, int which);
+
+extern "C" cfd_status cfd_set_halo_links(cfd_ctx* ctx, const int* links)
+{
+    if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
+    if (ctx->sub.empty()) return fail(ctx, CFD_EINVAL, "halo links join the blocks of an ensemble");
+    const int nb = (int)ctx->sub.size();
+    const int H = CFD_HALO_WIDTH;
+    std::vector<HaloLink> h[2][3];
+    if (links) {
+        for (int b = 0; b < nb; ++b)
+            for (int d = 0; d < 3; ++d)
+                for (int side = 0; side < 2; ++side) {
+                    const int c = links[(b * 3 + d) * 2 + side];
+                    const Geo& gb = ctx->sub[b]->g;
+                    const int tb = side ? gb.bc_hi[d] : gb.bc_lo[d];
+                    if (c < 0) {
+                        if (tb == CFD_BC_HALO) return fail(ctx, CFD_EINVAL, "a HALO face without a link");
+                        continue;
+                    }
+                    if (c >= nb) return fail(ctx, CFD_EINVAL, "halo link to a block that does not exist");
+                    if (tb != CFD_BC_HALO) return fail(ctx, CFD_EINVAL, "a linked face must be CFD_BC_HALO");
+                    const Geo& gc = ctx->sub[c]->g;
+                    const int db[3] = {gb.nx, gb.ny, gb.nz}, dc[3] = {gc.nx, gc.ny, gc.nz};
+                    const int a = (d + 1) % 3, e = (d + 2) % 3;
+                    if (db[a] != dc[a] || db[e] != dc[e])
+                        return fail(ctx, CFD_EINVAL, "linked blocks differ across the shared face");
+                    if (dc[d] < 2 * H + 1) return fail(ctx, CFD_EINVAL, "neighbour too thin for its ghost layers");
+                    for (int w = 0; w < 2; ++w) {
+                        HaloLink L;
+                        L.dst = w ? ctx->sub[b]->b.Uk : ctx->sub[b]->b.U;
+                        L.src = w ? ctx->sub[c]->b.Uk : ctx->sub[c]->b.U;
+                        L.dstN = gb.N;
+                        L.srcN = gc.N;
+                        L.dnx = gb.nx; L.dny = gb.ny; L.snx = gc.nx; L.sny = gc.ny;
+                        L.dl0 = side ? db[d] - H : 0;
+                        L.sl0 = side ? H : dc[d] - 2 * H;
+                        L.na = db[a];
+                        L.nb = db[e];
+                        h[w][d].push_back(L);
+                    }
+                }
+    }
+    for (int w = 0; w < 2; ++w)
+        for (int d = 0; d < 3; ++d) {
+            if (ctx->d_halo[w][d]) {
+                CU(cudaStreamSynchronize(ctx->stream));
+                CU(cudaFree(ctx->d_halo[w][d]));
+                ctx->d_halo[w][d] = nullptr;
+            }
+            if (!h[w][d].empty()) {
+                CU(cudaMalloc(&ctx->d_halo[w][d], h[w][d].size() * sizeof(HaloLink)));
+                CU(cudaMemcpyAsync(ctx->d_halo[w][d], h[w][d].data(), h[w][d].size() * sizeof(HaloLink),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+            }
+            ctx->n_halo[d] = (int)h[0][d].size();
+        }
+    ctx->graph_valid = false;
+    cfd_status st = launch_halo(ctx, 0);
+    if (st != CFD_OK) return st;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return CFD_OK;
+}
+
 extern "C" cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_grid* grids,
                                        const double* const* metrics, int metrics_on_device, const cfd_params* params,
                                        void* stream)
@@ -1015,9 +1091,24 @@ static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
     return CFD_OK;
 }
 
+// ghost layers of linked faces from the neighbours' interiors: which = 0 the
+// U arrays, 1 the Uk arrays; xi, then eta, then zeta
+static cfd_status launch_halo(cfd_ctx* ctx, int which)
+{
+    for (int d = 0; d < 3; ++d) {
+        if (!ctx->n_halo[d]) continue;
+        k_halo<<<dim3(128, ctx->n_halo[d]), 256, 0, ctx->stream>>>(ctx->d_halo[which][d], d, CFD_HALO_WIDTH);
+        LAUNCH_CHECK();
+    }
+    return CFD_OK;
+}
+
 static cfd_status enqueue_batch_step(cfd_ctx* ctx)
 {
     for (int s = 0; s < 3; ++s) {
+        // stage s reads U (s = 0) or Uk: refresh its ghost layers first
+        cfd_status sh = launch_halo(ctx, s == 0 ? 0 : 1);
+        if (sh != CFD_OK) return sh;
         cfd_status st = ctx->prm.precision == CFD_FP32_BULK ? enqueue_batch_stage<float>(ctx, s, nullptr)
                                                             : enqueue_batch_stage<double>(ctx, s, nullptr);
         if (st != CFD_OK) return st;

@@ -947,7 +947,9 @@ __device__ __forceinline__ float viscosity(const Phys& ph, float T)
     return T * sqrtf(T) * (1.0f + s) / (T + s);
 }
 
-template <class R>
+// YB > 0: CTAs of 32 x YB nodes in an x-y tile (the y neighbours of a tile's
+// nodes are shared through L1); YB = 0: CTAs along one x row.
+template <class R, int YB = 0>
 __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
 {
     const Geo& g = A.g;
@@ -957,7 +959,19 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
     const long long N = g.N;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int ord = ph.vorder;
-    NODE_IJK(g)
+    int i, j, k;
+    long long n;
+    if constexpr (YB > 0) {
+        i = vb.x * 32 + threadIdx.x;
+        j = vb.y * YB + threadIdx.y;
+        k = vb.z;
+    } else {
+        i = vb.x * blockDim.x + threadIdx.x;
+        j = vb.y;
+        k = vb.z;
+    }
+    n = (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
+    if (i < g.nx && j < g.ny)
     {
         const int st[3] = {1, nx, nx * ny};
         const int pos[3] = {i, j, k};
@@ -1701,6 +1715,43 @@ __device__ __forceinline__ void put_prim(const Phys& ph, double* U, long long N,
     U[4 * N + n] = p * ph.inv_gm1 + 0.5 * rho * (u * u + v * v + w * w);
 }
 
+// ---------------------------------------------------------------------------
+// multi-block halo exchange: ghost layers of one face of a block receive
+// H layers of the neighbouring block's interior, all five conserved fields.
+// One CTA row (blockIdx.y) per link of direction d.
+// ---------------------------------------------------------------------------
+struct HaloLink {
+    double* dst;
+    const double* src;
+    long long dstN, srcN;
+    int dnx, dny, snx, sny;  // node index = i + nx (j + ny k) in each grid
+    int dl0, sl0;            // first layer along d in the destination / source
+    int na, nb;              // extents in the directions (d+1)%3, (d+2)%3
+};
+
+__global__ void k_halo(const HaloLink* __restrict__ links, int d, int H)
+{
+    const HaloLink L = links[blockIdx.y];
+    const int a = (d + 1) % 3, b = (d + 2) % 3;
+    const long long plane = (long long)L.na * L.nb;
+    const long long per_field = (long long)H * plane;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 5 * per_field;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(e / per_field);
+        const long long r = e - q * per_field;
+        const int l = (int)(r / plane);
+        const long long t = r - l * plane;
+        int pd[3], ps[3];
+        pd[a] = ps[a] = (int)(t % L.na);
+        pd[b] = ps[b] = (int)(t / L.na);
+        pd[d] = L.dl0 + l;
+        ps[d] = L.sl0 + l;
+        const long long nd = pd[0] + (long long)L.dnx * (pd[1] + (long long)L.dny * pd[2]);
+        const long long ns = ps[0] + (long long)L.snx * (ps[1] + (long long)L.sny * ps[2]);
+        L.dst[q * L.dstN + nd] = L.src[q * L.srcN + ns];
+    }
+}
+
 __global__ void k_bc(Geo g, Phys ph, BCData bc, double* U, int d, const double* tptr, const double* dtptr,
                      double tfrac)
 {
@@ -1717,7 +1768,7 @@ __global__ void k_bc(Geo g, Phys ph, BCData bc, double* U, int d, const double* 
         const int side = (int)(e / nface);
         const long long f = e % nface;
         const int type = side ? g.bc_hi[d] : g.bc_lo[d];
-        if (type == 0) continue;
+        if (type == 0 || type == 4) continue;  // periodic, or ghost layers filled by the halo exchange
         int pos[3];
         pos[a] = (int)(f % na);
         pos[b] = (int)(f / na);
@@ -1819,8 +1870,8 @@ __global__ void k_prim(SweepArgs A) { prim_body<RT>(A, blockIdx); }
 __global__ void k_prim_mixed(SweepArgs A) { prim_mixed_body<false>(A, blockIdx); }
 __global__ void k_sensor(SweepArgs A) { sensor_body<false>(A, blockIdx); }
 __global__ void k_sensor32(SweepArgs A) { sensor32_body<false>(A, blockIdx); }
-template <class R>
-__global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R>(A, blockIdx); }
+template <class R, int YB = 0>
+__global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R, YB>(A, blockIdx); }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<R, TZ>(A, blockIdx); }
 template <class R, int BX, int EP, bool CHAR = false>

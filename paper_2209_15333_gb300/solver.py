@@ -220,6 +220,16 @@ class BatchSolver(Solver):
             out = np.empty((5,) + self.shapes[block])
         return super().get_state(out, block)
 
+    def set_halo_links(self, links):
+        """links: int array [nblocks][3][2] (neighbour across face (d, side),
+        -1 for none), or None; see cfd_set_halo_links."""
+        if links is None:
+            L.check(L.lib().cfd_set_halo_links(self.ctx, None), self.ctx)
+            return
+        a = np.ascontiguousarray(links, dtype=np.int32)
+        assert a.shape == (len(self.shapes), 3, 2)
+        L.check(L.lib().cfd_set_halo_links(self.ctx, C.c_void_p(a.ctypes.data)), self.ctx)
+
     def rhs(self, out=None, block=0):
         if out is None:
             out = np.empty((5,) + self.shapes[block])

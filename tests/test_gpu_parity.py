@@ -256,7 +256,7 @@ def test_sweep_variants_bit_identical(orc, precision):
     met = cases.uniform_metrics(*sh)
     U = turbulence_field(sh, 61)
     outs = []
-    for (kind, param), vk in zip(((0, 128), (0, 5), (1, 32), (1, 16)), (0, 1, 2, 1)):
+    for (kind, param), vk in zip(((0, 128), (0, 5), (1, 32), (1, 16), (1, 16)), (0, 1, 2, 1, 3)):
         with Solver(sh, met, precision=precision, scheme=3, Re=150.0, theta1=0.004, theta2=0.012, **bc) as s:
             s.set_state(U)
             for d in (1, 2):
