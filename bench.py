@@ -40,11 +40,12 @@ MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_
 # hash prefix and the variant each kernel ran in; scaled to the full launch by the
 # node count (traffic grows with it: the arrays exceed L2).
 NCU_TRAFFIC = {
-    "fp64": {"src": "2b744d3cad74", "per_node": {"visc_flux": 117.1, "sweep_xi": 106.4},
-             "variant": {"visc_flux": [0, 0], "sweep_xi": None}},
-    "mixed": {"src": "2b744d3cad74", "per_node": {"visc_flux": 51.9, "sweep_xi": 50.2, "sweep_eta": 72.5,
-                                                  "sweep_zeta": 90.7},
-              "variant": {"visc_flux": [0, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
+    "fp64": {"src": "6d0de673c508", "per_node": {"visc_flux": 117.2, "sweep_xi": 106.5, "sweep_eta": 151.6,
+                                                 "sweep_zeta": 160.1},
+             "variant": {"visc_flux": [3, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
+    "mixed": {"src": "6d0de673c508", "per_node": {"visc_flux": 51.9, "sweep_xi": 50.3, "sweep_eta": 72.6,
+                                                  "sweep_zeta": 91.0},
+              "variant": {"visc_flux": [3, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
 }
 
 
