@@ -121,3 +121,30 @@ def test_mlp_fallback_to_plain_sensor():
         s.set_sensor_mlp(None, None, None, None, None, None)
         s.rhs()
         assert np.array_equal(s.flags(), plain)
+
+
+def test_packaged_model_against_plain_sensor():
+    """The packaged weights on a held-out ensemble block (seed not used in
+    training) after it has evolved: learned classes against the plain
+    sensor's on the same state (rates over all nodes)."""
+    from paper_2209_15333_gb300.solver import Solver
+    from paper_2209_15333_gb300.train_sensor import load
+    W, conf, report = load()
+    blk = cases.ensemble_blocks(1, seed=777)[0]
+    with Solver(blk["shape"], blk["metrics"], scheme=3, Re=blk["Re"], Ma=blk["Mt"], visc_law=1, visc_omega=0.76,
+                precision=1) as s:
+        s.set_state(blk["U"])
+        s.step(s.cfl_dt(0.5), 60)
+        s.rhs()
+        plain = s.flags()
+        s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=conf)
+        s.sensor_fallbacks()
+        s.rhs()
+        learned = s.flags()
+        fb = s.sensor_fallbacks() / plain.size
+    mis = float((learned != plain).mean())
+    unsafe = float((learned < plain).mean())
+    print("packaged model: non-UD7 %.4f, misclassification %.4g, unsafe %.4g, fallback %.4g"
+          % ((plain > 0).mean(), mis, unsafe, fb))
+    assert (plain > 0).any()
+    assert mis < 0.01 and unsafe < 0.002 and fb < 0.05
