@@ -753,6 +753,34 @@ extern "C" cfd_status cfd_set_blowing(cfd_ctx* ctx, double amp, double x0, doubl
     return CFD_OK;
 }
 
+// Copy n doubles in stream order on ctx->stream.  When the host side is
+// pinned, device-mapped memory the SMs move the data themselves
+// (k_copy_mapped); otherwise the copy engine does.
+static cfd_status copy_state(cfd_ctx* ctx, double* dst, const double* src, long long n, cudaMemcpyKind kind)
+{
+    if (kind != cudaMemcpyDeviceToDevice) {
+        const void* host = kind == cudaMemcpyHostToDevice ? (const void*)src : (const void*)dst;
+        cudaPointerAttributes at{};
+        const bool mapped = cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                            at.devicePointer;
+        double* d = mapped && kind == cudaMemcpyDeviceToHost ? (double*)at.devicePointer : dst;
+        const double* sp = mapped && kind == cudaMemcpyHostToDevice ? (const double*)at.devicePointer : src;
+        if (mapped && ((uintptr_t)d % 16) == 0 && ((uintptr_t)sp % 16) == 0) {
+            const long long n2 = n / 2;
+            int dev = 0, sms = 152;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            k_copy_mapped<<<sms * 8, 256, 0, ctx->stream>>>((double2*)d, (const double2*)sp, n2, d + 2 * n2,
+                                                            sp + 2 * n2, (int)(n & 1));
+            LAUNCH_CHECK();
+            return CFD_OK;
+        }
+        cudaGetLastError();  // a pointer the runtime does not know is pageable host memory
+    }
+    CU(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), kind, ctx->stream));
+    return CFD_OK;
+}
+
 extern "C" cfd_status cfd_set_state(cfd_ctx* ctx, int block, const double* U, int on_device)
 {
     cfd_status st = check_block(ctx, block);
@@ -760,8 +788,8 @@ extern "C" cfd_status cfd_set_state(cfd_ctx* ctx, int block, const double* U, in
     DELEGATE(cfd_set_state(b_, 0, U, on_device));
     if (!U) return fail(ctx, CFD_EINVAL, "null state");
     const long long N = ctx->g.N;
-    CU(cudaMemcpyAsync(ctx->b.U, U, 5 * N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                       ctx->stream));
+    st = copy_state(ctx, ctx->b.U, U, 5 * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    if (st != CFD_OK) return st;
     if (ctx->prm.precision == CFD_FP32_BULK && !ctx->forced) CU(cudaMemsetAsync(ctx->b.cls, 2, N, ctx->stream));
     st = launch_bc(ctx, ctx->b.U, 0.0, false);
     if (st != CFD_OK) return st;
@@ -776,8 +804,8 @@ extern "C" cfd_status cfd_get_state(cfd_ctx* ctx, int block, double* U, int on_d
     DELEGATE(cfd_get_state(b_, 0, U, on_device));
     if (!U) return fail(ctx, CFD_EINVAL, "null output");
     const long long N = ctx->g.N;
-    CU(cudaMemcpyAsync(U, ctx->b.U, 5 * N * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    st = copy_state(ctx, U, ctx->b.U, 5 * N, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    if (st != CFD_OK) return st;
     return read_err(ctx);
 }
 

@@ -1752,6 +1752,17 @@ __global__ void k_halo(const HaloLink* __restrict__ links, int d, int H)
     }
 }
 
+// state copy between device memory and pinned (device-mapped) host memory
+// by the SMs: 16-byte loads and stores over the CPU-GPU link, many in flight
+// (n2: number of double2 items; a trailing odd double is copied by thread 0)
+__global__ void k_copy_mapped(double2* __restrict__ dst, const double2* __restrict__ src, long long n2, double* dst1,
+                              const double* src1, int odd)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+    if (odd && blockIdx.x == 0 && threadIdx.x == 0) *dst1 = *src1;
+}
+
 __global__ void k_bc(Geo g, Phys ph, BCData bc, double* U, int d, const double* tptr, const double* dtptr,
                      double tfrac)
 {

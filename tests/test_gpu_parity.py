@@ -272,3 +272,23 @@ def test_sweep_variants_bit_identical(orc, precision):
         c = orc.Case(*sh, Re=150.0, Ma=0.5, scheme=3, theta1=0.004, theta2=0.012, **bc)
         Lo = orc.rhs(c, cases.expand_metrics(met, sh[::-1]), orc.apply_bc(c, cases.expand_metrics(met, sh[::-1]), U))
         assert field_rel_err(outs[0][0], Lo) <= TOL
+
+
+@pytest.mark.parametrize("n", [(17, 9, 5), (16, 8, 4)])
+def test_pinned_host_state_round_trip(n):
+    """State copies from and to pinned (device-mapped) host memory, which
+    the SMs move themselves, are exact; odd and even element counts."""
+    import torch
+    from paper_2209_15333_gb300.solver import Solver
+    met = cases.uniform_metrics(*n)
+    U = turbulence_field(n, 71)
+    host_in = torch.from_numpy(U.copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    with Solver(n, met, scheme=0, Re=0.0) as s:
+        s.set_state(host_in)
+        s.get_state(out=host_out)
+        assert np.array_equal(host_out.numpy(), U)
+        s.step(1e-3, 1)
+        ref = s.get_state()            # pageable numpy: copy engine
+        s.get_state(out=host_out)      # pinned: mapped copy
+        assert np.array_equal(host_out.numpy(), ref)
