@@ -67,3 +67,37 @@ def test_default_params_and_validation_without_gpu(built):
     assert _lib.lib().cfd_step(None, 0.1, 1) == _lib.CFD_EINVAL
     assert _lib.lib().cfd_sync(None, 1.0) == _lib.CFD_EINVAL
     _lib.lib().cfd_destroy(None)
+
+
+def test_more_validation_without_gpu(built):
+    """Degenerate and unsupported inputs are refused before any device call."""
+    from paper_2209_15333_gb300 import _lib
+    L = _lib.lib()
+    ctx = C.c_void_p()
+    met = (C.c_double * 10)()
+    mp = C.cast(met, C.c_void_p)
+
+    def create(g, p):
+        return L.cfd_create(C.byref(ctx), C.byref(g), mp, 0, C.byref(p), None)
+
+    p = _lib.default_params()
+    assert create(_lib.make_grid(0, 8, 8, metric_layout=_lib.METRICS_UNIFORM), p) == _lib.CFD_EINVAL   # empty
+    assert create(_lib.make_grid(8, 8, 8, bc_lo=(5, 0, 0), bc_hi=(5, 0, 0), metric_layout=_lib.METRICS_UNIFORM),
+                  p) == _lib.CFD_EINVAL                                                               # unknown BC
+    # a direction with ghost layers needs 2 * 8 + 1 nodes
+    g = _lib.make_grid(16, 8, 8, bc_lo=(_lib.BC_HALO, 0, 0), bc_hi=(_lib.BC_HALO, 0, 0),
+                       metric_layout=_lib.METRICS_UNIFORM)
+    assert create(g, p) == _lib.CFD_EINVAL
+    assert b"ghost" in L.cfd_last_error(None)
+    q = _lib.default_params(recon_vars=7)
+    assert create(_lib.make_grid(8, 8, 8, metric_layout=_lib.METRICS_UNIFORM), q) == _lib.CFD_EINVAL
+    q = _lib.default_params(precision=1, weno_eps=0.0)
+    assert create(_lib.make_grid(8, 8, 8, metric_layout=_lib.METRICS_UNIFORM), q) == _lib.CFD_EINVAL
+    # characteristic reconstruction in an ensemble, and in the allocation-free call
+    q = _lib.default_params(recon_vars=1)
+    grids = (_lib.CfdGrid * 2)(_lib.make_grid(8, 8, 8, metric_layout=_lib.METRICS_UNIFORM),
+                               _lib.make_grid(8, 8, 8, metric_layout=_lib.METRICS_UNIFORM))
+    prms = (_lib.CfdParams * 2)(q, q)
+    mets = (C.c_void_p * 2)(mp, mp)
+    assert L.cfd_create_batch(C.byref(ctx), 2, grids, mets, 0, prms, None) == _lib.CFD_EUNSUPPORTED
+    assert L.cfd_set_halo_links(None, None) == _lib.CFD_EINVAL
