@@ -64,6 +64,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest x over all ranks (x itself on one rank): the job's time
+    is its slowest replica's."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, nodes, steps, seconds):
+    """Whole-job point-stage updates per second: every rank advances its own
+    replica of `nodes` nodes by `steps` RK3 steps of 3 stages."""
+    return world * nodes * 3 * steps / seconds
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -272,13 +290,10 @@ def run_precision(args, prec, U, met, params, world, local, dt):
     ms = e0.elapsed_time(e1)
     launches = s.launches() - l0
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     cls = s.flags()
     frac = np.bincount(cls.ravel(), minlength=3)[:3] / cls.size
-    value = world * N * 3 * args.steps / (ms * 1e-3)
+    value = job_throughput(world, N, args.steps, ms * 1e-3)
     # end to end through the public API with pinned host buffers
     host_in = torch.from_numpy(s.get_state()).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -290,16 +305,12 @@ def run_precision(args, prec, U, met, params, world, local, dt):
         s.set_state(host_in)
         s.step(dt, 1)
         s.get_state(out=host_out)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     prof = s.profile_stage(3)
     variants = {"visc": s.sweep_variant(0), "eta": s.sweep_variant(1), "zeta": s.sweep_variant(2)}
     s.close()
     return dict(value=value, ms=ms, launches=launches, clocks=clk, class_fraction=[float(x) for x in frac],
-                e2e=world * N * 3 * args.steps / e2e_s, prof=prof, U1=U1, variants=variants)
+                e2e=job_throughput(world, N, args.steps, e2e_s), prof=prof, U1=U1, variants=variants)
 
 
 def run_ensemble(args, world):
@@ -331,14 +342,15 @@ def run_ensemble(args, world):
     bs.step(dt, args.steps)
     e1.record(stream)
     bs.sync(600.0)
-    ms = e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
     launches = bs.launches() - l0
     prof = bs.profile_stage(3)
     bs.close()
     names = {"sweep_xi": "sweep_xi", "sweep_eta": "sweep_eta", "sweep_zeta": "sweep_zeta"}
     return {"workload": "48 periodic isotropic-turbulence blocks, dims i.i.d. from {32,48,64,96,128}, "
                         "Mt in [0.3,0.7], hybrid, viscous, FP32 bulk / FP64 state",
-            "nodes": nodes, "value": world * nodes * 3 * args.steps / (ms * 1e-3), "unit": "point-stage/s",
+            "nodes": nodes, "value": job_throughput(world, nodes, args.steps, ms * 1e-3), "unit": "point-stage/s",
             "ms_per_step": ms / args.steps, "gpu_launches": launches,
             "launches_per_step": launches / max(1, args.steps), "kernel_ms": prof}
 
