@@ -761,8 +761,9 @@ static cfd_status copy_state(cfd_ctx* ctx, double* dst, const double* src, long 
     if (kind != cudaMemcpyDeviceToDevice) {
         const void* host = kind == cudaMemcpyHostToDevice ? (const void*)src : (const void*)dst;
         cudaPointerAttributes at{};
-        const bool mapped = cudaPointerGetAttributes(&at, host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-                            at.devicePointer;
+        const cudaError_t qe = cudaPointerGetAttributes(&at, host);
+        if (qe != cudaSuccess) cudaGetLastError();  // not a pointer the runtime knows: pageable host memory
+        const bool mapped = qe == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer;
         double* d = mapped && kind == cudaMemcpyDeviceToHost ? (double*)at.devicePointer : dst;
         const double* sp = mapped && kind == cudaMemcpyHostToDevice ? (const double*)at.devicePointer : src;
         if (mapped && ((uintptr_t)d % 16) == 0 && ((uintptr_t)sp % 16) == 0) {
@@ -775,7 +776,6 @@ static cfd_status copy_state(cfd_ctx* ctx, double* dst, const double* src, long 
             LAUNCH_CHECK();
             return CFD_OK;
         }
-        cudaGetLastError();  // a pointer the runtime does not know is pageable host memory
     }
     CU(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), kind, ctx->stream));
     return CFD_OK;
