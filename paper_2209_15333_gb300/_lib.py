@@ -8,7 +8,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libcfd_gb300.so")
+# CFD_GB300_LIB selects another build of the same library (the bounds-checked
+# one in its test); there is no fallback when the library is missing
+LIB_PATH = os.environ.get("CFD_GB300_LIB") or os.path.join(HERE, "_build", "libcfd_gb300.so")
 
 CFD_OK, CFD_EINVAL, CFD_ENOMEM, CFD_ECUDA, CFD_ENONPHYS, CFD_ETIMEOUT, CFD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 BC_PERIODIC, BC_WALL_ISOTHERMAL, BC_INFLOW, BC_OUTFLOW_EXTRAP, BC_HALO = 0, 1, 2, 3, 4

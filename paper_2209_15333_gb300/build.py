@@ -1,6 +1,9 @@
 """Build the CUDA library ``_build/libcfd_gb300.so`` for sm_103a with nvcc.
 
 One translation unit, one -gencode, static CUDA runtime; no torch headers.
+``checked=True`` builds ``_build/libcfd_gb300_checked.so`` with index-bounds
+checks in the kernels (CFD_BOUNDS_CHECK): an out-of-range node index sets an
+error word and skips the access instead of trapping.
 """
 import os
 import shutil
@@ -12,6 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcfd_gb300.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libcfd_gb300_checked.so")
 SOURCES = [os.path.join(CSRC, "cfd_api.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(ROOT, "include", "cfd.h"), __file__]
@@ -27,20 +31,22 @@ def nvcc():
     raise RuntimeError("nvcc not found")
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        if os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in DEPS if os.path.exists(p)):
-            return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), *FLAGS, *(["-Xptxas", "-v"] if verbose else []), *SOURCES, "-o", tmp]
+    lib = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(lib):
+        if os.path.getmtime(lib) >= max(os.path.getmtime(p) for p in DEPS if os.path.exists(p)):
+            return lib
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = [nvcc(), *FLAGS, *(["-DCFD_BOUNDS_CHECK"] if checked else []), *(["-Xptxas", "-v"] if verbose else []),
+           *SOURCES, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stderr[-20000:])
     if verbose:
         sys.stderr.write(r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

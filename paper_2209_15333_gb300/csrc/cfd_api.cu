@@ -708,6 +708,7 @@ static cfd_status read_err(cfd_ctx* ctx)
     std::memcpy(&h, ctx->h_pinned, sizeof(int));
     if (h) {
         CU(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+        if (h & 2) return fail(ctx, CFD_ECUDA, "index out of bounds (caught by the bounds-checked build)");
         return fail(ctx, CFD_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) met on the device");
     }
     return CFD_OK;

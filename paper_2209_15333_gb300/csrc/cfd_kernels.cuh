@@ -74,6 +74,20 @@ __device__ __forceinline__ long long midx(const Geo& g, int i, int j, long long 
     return g.mlayout == 0 ? n : (g.mlayout == 1 ? (long long)i + (long long)g.nx * j : 0LL);
 }
 
+// Index-bounds checks of the bounds-checked build (CFD_BOUNDS_CHECK): an
+// index outside [0, n) sets bit 2 of the error word and the access is
+// skipped; the normal build compiles the check away.
+#ifdef CFD_BOUNDS_CHECK
+__device__ __forceinline__ bool in_range(int* err, long long i, long long n)
+{
+    if (i >= 0 && i < n) return true;
+    atomicOr(err, 2);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_range(int*, long long, long long) { return true; }
+#endif
+
 __device__ __forceinline__ double metv(const Geo& g, int e, long long mi)
 {
     return __ldg(g.met + (long long)e * g.M + mi);
@@ -987,6 +1001,19 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
             for (int t = 0; t < 9; ++t)
                 off[d][t] = wrap ? (wrapi(pos[d] + t - 4, nd[d]) - pos[d]) * st[d] : (t - 4) * st[d];
         }
+#ifdef CFD_BOUNDS_CHECK
+        {
+            bool inb = true;
+            // positions a derivative reads: all 9 on periodic lines, those
+            // inside the line otherwise (the boundary closures stay inside)
+            for (int d = 0; d < 3; ++d)
+                for (int t = 0; t < 9; ++t) {
+                    const int q = pos[d] + t - 4;
+                    if (g.per[d] || (q >= 0 && q < nd[d])) inb = inb && in_range(A.err, n + off[d][t], N);
+                }
+            if (!inb) return;
+        }
+#endif
         // dq[var][d]: var = u, v, w, T (P rows 1, 2, 3, 5)
         R dq[4][3];
 #pragma unroll
@@ -1158,6 +1185,7 @@ template <class R, int EP>
 __device__ __forceinline__ void epilogue(const SweepArgs& A, long long n, int i, int j, int k, const R val[5])
 {
     const long long N = A.g.N;
+    if (!in_range(A.err, n, N)) return;
     R* Racc = (R*)A.R;
     if (EP == EP_STORE) {
 #pragma unroll
@@ -1263,6 +1291,7 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
         bool ok = per || (i >= 0 && i < n);
         R fp[5], fm[5], sg = (R)0;
         uint8_t c = 0;
+        if (ok) ok = in_range(A.err, row + (per ? wrapi(i, n) : i), g.N);
         if (ok) {
             int ii = per ? wrapi(i, n) : i;
             sg = node_split<R>(A, 0, row + ii, ii, j, fp, fm);
@@ -1438,6 +1467,7 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
         R fp[5], fm[5], sg = (R)0;
         uint8_t c = 0;
         bool ok = lane_ok && (per || (m >= 0 && m < n));
+        if (ok) ok = in_range(A.err, base + (long long)(per ? wrapi(m, n) : m) * stride, g.N);
         if (ok) {
             int mm = per ? wrapi(m, n) : m;
             long long nn = base + (long long)mm * stride;
@@ -1539,6 +1569,7 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
         const int r = ty + 8 * it;
         const int m = m0 - 4 + r;
         okv[it] = r < ROWS && lane_ok && (per || (m >= 0 && m < n));
+        if (okv[it]) okv[it] = in_range(A.err, base + (long long)(per ? wrapi(m, n) : m) * stride, N);
         cv[it] = 0;
         miv[it] = 0;
         if (okv[it]) {
