@@ -40,10 +40,10 @@ MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_
 # hash prefix and the variant each kernel ran in; scaled to the full launch by the
 # node count (traffic grows with it: the arrays exceed L2).
 NCU_TRAFFIC = {
-    "fp64": {"src": "a343126dcb0b", "per_node": {"visc_flux": 116.9, "sweep_xi": 106.4, "sweep_eta": 151.5,
+    "fp64": {"src": "90a3a246dda5", "per_node": {"visc_flux": 116.9, "sweep_xi": 106.4, "sweep_eta": 151.5,
                                                  "sweep_zeta": 160.3},
              "variant": {"visc_flux": [3, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
-    "mixed": {"src": "a343126dcb0b", "per_node": {"visc_flux": 51.9, "sweep_xi": 50.2, "sweep_eta": 72.6,
+    "mixed": {"src": "90a3a246dda5", "per_node": {"visc_flux": 51.9, "sweep_xi": 50.2, "sweep_eta": 72.6,
                                                   "sweep_zeta": 91.0},
               "variant": {"visc_flux": [3, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
 }
