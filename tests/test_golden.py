@@ -43,3 +43,20 @@ def test_mach_2_9_ramp_follows_table8():
     assert c["Ma"] == ma and c["T_ref"] == t_inf
     # the wall temperature ratio 307 / 108.1 = 2.84, taken as 2.8
     assert abs(c["Tw"] - t_w / t_inf) < 0.05
+
+
+def test_oracle_tgv_regression_fixture():
+    """The oracle reproduces its own stored 10-step Taylor-Green summary
+    (written by tests/golden/make_tgv_reference.py); a change of the oracle's
+    arithmetic shows up here."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_tgv_reference", os.path.join(HERE, "make_tgv_reference.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    stored = {}
+    for line in open(os.path.join(HERE, "tgv32_10steps.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            stored[k] = float(v)
+    for k, v in m.summary():
+        assert abs(v - stored[k]) <= 1e-12 * max(1.0, abs(stored[k])), k
