@@ -18,8 +18,11 @@
  *    nondimensional as in Eq. 17 (p = rho T/(gamma Ma^2)).
  *  - Pointers flagged on_device = 1 are device pointers on the context's
  *    device; they are read or written on the context's stream.  Host
- *    pointers are read or written before the call returns.  Caller arrays
- *    stay caller-owned; the context copies what it keeps.
+ *    pointers are read or written before the call returns; pinned
+ *    (page-locked, device-mapped) host buffers of the state are moved by
+ *    the GPU's SMs through the mapped pointer, pageable ones by the copy
+ *    engine.  Caller arrays stay caller-owned; the context copies what it
+ *    keeps.
  *  - Directions without periodicity exclude nothing; periodic directions
  *    hold no duplicate end node.
  *  - A context is not thread-safe: use one context per host thread.
