@@ -1,15 +1,25 @@
-"""Benchmark: grid-point stage updates per second of the TVD-RK3 step on the
-256^3 decaying isotropic-turbulence workload (hybrid UD7/WENO7/WENO5 scheme,
-8th-order viscous terms, periodic box), through the C ABI of the CUDA library.
+"""Benchmark: grid-point stage updates per second of the TVD-RK3 step through
+the C ABI of the CUDA library, on one GPU.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                    [--precision both|mixed|fp64] [--n 256]
+                    [--forms fp64,mixed,mixed_learned] [--n 256] [--no-ramp] [--no-ensemble]
 
-Rank 0 prints one JSON line.  The headline `value` is the FP32-bulk/FP64-state
-form; the plain FP64 form is reported beside it under "fp64", each with its
-error against the FP64 oracle after one RK3 step of the full field.  The path
-exchanges no data between ranks (independent boxes), so N > 1 runs replicas
-with a barrier and max-over-ranks timing (weak scaling).
+Workloads (seeded, synthetic):
+  * headline: decaying isotropic turbulence on a 256^3 periodic box (hybrid
+    UD7/WENO7/WENO5, 8th-order viscous terms).  The headline `value` is the
+    plain FP64 form (the paper's arithmetic); the FP32-bulk / FP64-state form
+    with the plain sensor ("mixed") and with the learned sensor
+    ("mixed_learned") are reported beside it, each with its error against the
+    FP64 oracle after one RK3 step of the full field.
+  * "ramp": the Mach 2.9, 24 degree compression ramp on its 1024 x 256 x 128
+    body-fitted grid from its initial field (corner shock present, so WENO
+    classes occur), all three forms, with the class fractions, the mixed
+    forms' state and wall-quantity differences from the FP64 form, and the
+    learned sensor's fallback and misclassification rates.
+  * "ensemble": 48 uneven periodic blocks in persistent launches.
+Rank 0 prints one JSON line.  The path exchanges no data between ranks
+(independent boxes), so N > 1 runs replicas with a barrier and max-over-ranks
+timing (weak scaling).
 """
 import argparse
 import hashlib
@@ -29,24 +39,24 @@ SEED = 20220930
 MT = 0.5
 GAMMA = 1.4
 KERNEL_NAMES = ["prim", "sensor", "visc_flux", "sweep_xi", "sweep_eta", "sweep_zeta"]
+FORMS = {"fp64": dict(precision=0, learned=False), "mixed": dict(precision=1, learned=False),
+         "mixed_learned": dict(precision=1, learned=True)}
 
-# Algorithmic work per node of each kernel:
-# FP64 form: counted flops (FMA = 2; division, sqrt, pow = 1);
-# mixed form: compulsory bytes (inputs read once, outputs written once).
+# Algorithmic work per node of each kernel, counted from the method's
+# operations (FMA = 2 flops; division, square root, power = 1):
 FP64_FLOPS = {"prim": 25, "sensor": 20, "visc_flux": 305, "sweep_xi": 247, "sweep_eta": 252, "sweep_zeta": 277}
+# compulsory bytes per node of each kernel in the FP32-bulk form (inputs read
+# once, outputs written once)
 MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_eta": 77, "sweep_zeta": 164}
-# DRAM bytes per node measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# on a 160^3 stage (the profiles directory), valid for the kernel sources with this
-# hash prefix and the variant each kernel ran in; scaled to the full launch by the
-# node count (traffic grows with it: the arrays exceed L2).
-NCU_TRAFFIC = {
-    "fp64": {"src": "90a3a246dda5", "per_node": {"visc_flux": 116.9, "sweep_xi": 106.4, "sweep_eta": 151.5,
-                                                 "sweep_zeta": 160.3},
-             "variant": {"visc_flux": [3, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
-    "mixed": {"src": "90a3a246dda5", "per_node": {"visc_flux": 51.9, "sweep_xi": 50.2, "sweep_eta": 72.6,
-                                                  "sweep_zeta": 91.0},
-              "variant": {"visc_flux": [3, 0], "sweep_xi": None, "sweep_eta": [1, 16], "sweep_zeta": [1, 16]}},
-}
+# What one point-stage must move through HBM whatever the kernel design: read
+# the stage state (40 B), read U^n in stages 2-3 (26.7 B on average), write
+# the new state (40 B); metrics are constant on the uniform box.
+ALG_BYTES_PER_POINT_STAGE = 40.0 + 80.0 / 3.0 + 40.0
+# DRAM bytes per launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the full 256^3 workload, one launch of the named
+# kernel in the variant it ran in; valid only for the kernel sources with this
+# hash prefix.
+NCU_TRAFFIC = {"src": None, "fp64": {}, "mixed": {}}
 
 
 def parse():
@@ -55,11 +65,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--forms", default="fp64,mixed,mixed_learned")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-only", action="store_true", help="one profiled stage per precision (ncu runs)")
+    ap.add_argument("--profile-only", action="store_true", help="one profiled stage per form (ncu runs)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-block ensemble measurement")
+    ap.add_argument("--no-ramp", action="store_true", help="skip the Mach 2.9 ramp workload")
+    ap.add_argument("--ramp-scale", type=int, default=1, help="divide the ramp grid by this factor")
     ap.add_argument("--variants", default="", help="pin kernel variants, e.g. 0:2,1:1:16,2:1:16 (dir:kind[:param])")
     return ap.parse_args()
 
@@ -97,9 +109,10 @@ def workload(n):
 
 def kernel_src_hash():
     h = hashlib.sha256()
-    for f in ("cfd_kernels.cuh", "weno_coeffs.cuh"):
-        with open(os.path.join(ROOT, "paper_2209_15333_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2209_15333_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(ROOT, "paper_2209_15333_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:12]
 
 
@@ -109,6 +122,20 @@ def field_rel_err(a, b):
         den = float(np.abs(b[q]).max())
         num = float(np.abs(a[q] - b[q]).max())
         e = max(e, num / den if den > 0 else num)
+    return e
+
+
+def state_rel_err(a, b):
+    """Largest difference of two states relative to the field's scale:
+    density and energy against their own maxima, each momentum component
+    against the largest momentum magnitude (a component that vanishes in the
+    reference, like the spanwise momentum of a two-dimensional flow, is not
+    its own scale)."""
+    mom = float(np.sqrt(np.sum(b[1:4] ** 2, axis=0)).max())
+    e = 0.0
+    for q in range(5):
+        den = mom if 1 <= q <= 3 else float(np.abs(b[q]).max())
+        e = max(e, float(np.abs(a[q] - b[q]).max()) / den)
     return e
 
 
@@ -209,8 +236,7 @@ def workload_params(n):
 
 
 def arm_config(n, Re, world, precision):
-    """The workload both arms report (the reference arm times a bounded
-    sample of it, stated in its cpu_baseline)."""
+    """The workload both arms report."""
     N = n ** 3
     return {"workload": "decaying isotropic turbulence %d^3 periodic, hybrid UD7/WENO7/WENO5, 8th-order "
                         "viscous" % n,
@@ -220,10 +246,11 @@ def arm_config(n, Re, world, precision):
 
 
 def run_reference(args, rank):
-    """Reference arm: the CPU oracle on the host cores (rank 0 only)."""
+    """Reference arm: the CPU oracle on the host cores (rank 0 only), one
+    RK3 step of the full n^3 field per timed step."""
     if rank != 0:
         return
-    n = min(args.n, 128)
+    n = args.n
     U, met, params, Re = workload_params(n)
     import oracle
     from paper_2209_15333_gb300 import cases
@@ -240,23 +267,48 @@ def run_reference(args, rank):
         "impl": "reference", "metric": "grid-point stage updates/s", "value": value, "unit": "point-stage/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": arm_config(args.n, workload_params(args.n)[3], args.gpus, "FP64 CPU oracle"),
+        "config": arm_config(n, Re, args.gpus, "FP64"),
         "cpu_baseline": {"value": value, "unit": "point-stage/s", "cores": th, "kind": "oracle",
-                         "sample": "one RK3 step of a %d^3 box of the same recipe per timed step (the %d^3 "
-                                   "case's throughput is measured on a bounded sample)" % (n, args.n)},
+                         "sample": "one RK3 step of the full %d^3 field per timed step" % n},
         "e2e": {"value": value, "unit": "point-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_precision(args, prec, U, met, params, world, local, dt):
-    """Time K graph-replayed steps of one precision; returns a result dict."""
+def set_learned_sensor(s):
+    from paper_2209_15333_gb300.train_sensor import load
+    W, conf, _ = load()
+    s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=conf)
+
+
+def timed_steps(s, stream, dt, steps, world):
+    """CUDA-event milliseconds of `steps` graph-replayed steps on the
+    context stream (slowest rank), and the launches they issued."""
+    import torch
+    l0 = s.launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(dt, steps)
+    e1.record(stream)
+    s.sync(600.0)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1), world), s.launches() - l0
+
+
+def run_form(args, form, U, met, params, world, local, dt):
+    """Time K graph-replayed steps of one form on the 256^3 box."""
     import torch
     from paper_2209_15333_gb300.solver import Solver
     n = args.n
     N = n ** 3
     stream = torch.cuda.Stream()
-    s = Solver((n, n, n), met, stream=stream, precision=1 if prec == "mixed" else 0, **params)
+    s = Solver((n, n, n), met, stream=stream, precision=FORMS[form]["precision"], **params)
+    if FORMS[form]["learned"]:
+        set_learned_sensor(s)
     Ud = torch.tensor(U, device="cuda")
     s.set_state(Ud)
     for item in filter(None, args.variants.split(",")):
@@ -274,23 +326,13 @@ def run_precision(args, prec, U, met, params, world, local, dt):
     for _ in range(args.warmup):
         s.step(dt, 1)
     s.sync(600.0)
+    if FORMS[form]["learned"]:
+        s.sensor_fallbacks()  # reset the counter
     clocks = ClockSampler(local)
     clocks.start()
-    l0 = s.launches()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(dt, args.steps)
-    e1.record(stream)
-    s.sync(600.0)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = s.launches() - l0
+    ms, launches = timed_steps(s, stream, dt, args.steps, world)
     clk = clocks.stop()
-    ms = max_over_ranks(ms, world)
+    fallbacks = s.sensor_fallbacks() if FORMS[form]["learned"] else None
     cls = s.flags()
     frac = np.bincount(cls.ravel(), minlength=3)[:3] / cls.size
     value = job_throughput(world, N, args.steps, ms * 1e-3)
@@ -309,8 +351,78 @@ def run_precision(args, prec, U, met, params, world, local, dt):
     prof = s.profile_stage(3)
     variants = {"visc": s.sweep_variant(0), "eta": s.sweep_variant(1), "zeta": s.sweep_variant(2)}
     s.close()
-    return dict(value=value, ms=ms, launches=launches, clocks=clk, class_fraction=[float(x) for x in frac],
-                e2e=job_throughput(world, N, args.steps, e2e_s), prof=prof, U1=U1, variants=variants)
+    r = dict(value=value, ms=ms, launches=launches, clocks=clk, class_fraction=[float(x) for x in frac],
+             e2e=job_throughput(world, N, args.steps, e2e_s), prof=prof, U1=U1, variants=variants)
+    if fallbacks is not None:
+        r["fallback_fraction"] = fallbacks / (3.0 * args.steps * N)
+    return r
+
+
+def run_ramp(args, world):
+    """Mach 2.9, 24 degree ramp (1024 x 256 x 128) from its initial field:
+    K timed steps of each form at a fixed dt (CFL 0.3 on the initial field)."""
+    import torch
+    from paper_2209_15333_gb300 import ramp
+    c = ramp.CASES[4]
+    nx, ny, nz = ramp.case_shape(4, args.ramp_scale)
+    N = nx * ny * nz
+    out = {"workload": "Mach 2.9, 24 deg compression ramp %dx%dx%d, hybrid, Sutherland, Re_delta 20000, "
+                       "isothermal wall with blowing strip, from the initial field" % (nx, ny, nz),
+           "grid": [nx, ny, nz], "nodes": N, "unit": "point-stage/s"}
+    states, flags, rc, dt = {}, {}, None, None
+    for form in [f for f in ("fp64", "mixed", "mixed_learned") if f in args.forms.split(",")]:
+        stream = torch.cuda.Stream()
+        s, rc = ramp.run(4, FORMS[form]["precision"], FORMS[form]["learned"], 0, 1, scale=args.ramp_scale,
+                         stream=stream)
+        if dt is None:
+            dt = s.cfl_dt(0.3)
+        for _ in range(args.warmup):
+            s.step(dt, 1)
+        s.sync(600.0)
+        if FORMS[form]["learned"]:
+            s.sensor_fallbacks()
+        t0 = time.perf_counter()
+        ms, launches = timed_steps(s, stream, dt, args.steps, world)
+        wall = time.perf_counter() - t0
+        rec = {"value": job_throughput(world, N, args.steps, ms * 1e-3), "ms_per_step": ms / args.steps,
+               "gpu_launches": launches, "host_wall_s": wall}
+        if FORMS[form]["learned"]:
+            rec["fallback_fraction"] = s.sensor_fallbacks() / (3.0 * args.steps * N)
+        U = s.get_state()
+        states[form] = U
+        # classes of the final state's evaluation, plus (learned) the plain
+        # sensor's classes of the same state for the misclassification rate
+        s.rhs(np.empty_like(U))
+        g = s.flags()
+        flags[form] = g
+        rec["class_fraction"] = (np.bincount(g.ravel(), minlength=3)[:3] / g.size).tolist()
+        if FORMS[form]["learned"]:
+            s.set_sensor_mlp(None, None, None, None, None, None)
+            s.rhs(np.empty_like(U))
+            p = s.flags()
+            rec["misclassification"] = float((g != p).mean())
+            rec["unsafe_rate"] = float((g < p).mean())
+        pw, cf = ramp.wall_quantities(U, rc["metrics2d"], c["Ma"], c["Tw"], c["T_ref"])
+        rec["_pw"], rec["_cf"] = pw, cf
+        s.close()
+        out[form] = rec
+    if "fp64" in out:
+        base = out["fp64"]
+        for form in ("mixed", "mixed_learned"):
+            if form not in out:
+                continue
+            r = out[form]
+            r["speedup_vs_fp64"] = r["value"] / base["value"]
+            r["state_rel_err_vs_fp64"] = state_rel_err(states[form], states["fp64"])
+            r["pw_rel_l2_err_vs_fp64"] = float(np.linalg.norm(r["_pw"] - base["_pw"]) / np.linalg.norm(base["_pw"]))
+            r["cf_rel_l2_err_vs_fp64"] = float(np.linalg.norm(r["_cf"] - base["_cf"]) / np.linalg.norm(base["_cf"]))
+    for r in out.values():
+        if isinstance(r, dict):
+            r.pop("_pw", None)
+            r.pop("_cf", None)
+    out["dt"] = dt
+    out["steps_from_initial_field"] = args.warmup + args.steps
+    return out
 
 
 def run_ensemble(args, world):
@@ -332,59 +444,71 @@ def run_ensemble(args, world):
     for _ in range(args.warmup):
         bs.step(dt, 1)
     bs.sync(600.0)
-    l0 = bs.launches()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    bs.step(dt, args.steps)
-    e1.record(stream)
-    bs.sync(600.0)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1), world)
-    launches = bs.launches() - l0
+    ms, launches = timed_steps(bs, stream, dt, args.steps, world)
     prof = bs.profile_stage(3)
+    variants = bs.batch_variants() if hasattr(bs, "batch_variants") else None
     bs.close()
-    names = {"sweep_xi": "sweep_xi", "sweep_eta": "sweep_eta", "sweep_zeta": "sweep_zeta"}
     return {"workload": "48 periodic isotropic-turbulence blocks, dims i.i.d. from {32,48,64,96,128}, "
                         "Mt in [0.3,0.7], hybrid, viscous, FP32 bulk / FP64 state",
             "nodes": nodes, "value": job_throughput(world, nodes, args.steps, ms * 1e-3), "unit": "point-stage/s",
             "ms_per_step": ms / args.steps, "gpu_launches": launches,
-            "launches_per_step": launches / max(1, args.steps), "kernel_ms": prof}
+            "launches_per_step": launches / max(1, args.steps), "kernel_ms": prof, "kernel_variants": variants}
 
 
-def roofline(prec, r, N, peaks, fma, src_hash):
+def kernel_traffic(form, dom, variants, N, src_hash):
+    tr = NCU_TRAFFIC
+    rec = tr.get(form, {}).get(dom)
+    if not tr["src"] or tr["src"] != src_hash or rec is None:
+        return None
+    if rec.get("variant") is not None and list(rec["variant"]) != list(variants):
+        return None
+    return rec["bytes_per_launch"] * N / rec["nodes"]
+
+
+def rooflines(form, r, N, peaks, fma, src_hash, world):
+    """Dominant-kernel roofline (CUDA-event time of one launch per stage) and
+    the whole-stage algorithmic fractions."""
     prof = r["prof"]
     dom = max(prof, key=prof.get)
-    tr = NCU_TRAFFIC[prec]
-    traffic = None
     ran = {"visc_flux": r["variants"]["visc"], "sweep_eta": r["variants"]["eta"],
            "sweep_zeta": r["variants"]["zeta"]}.get(dom)
-    if (tr["src"] and tr["src"] == src_hash and dom in tr["per_node"]
-            and (tr["variant"][dom] is None or list(tr["variant"][dom]) == list(ran))):
-        traffic = tr["per_node"][dom] * N
-    if prec == "fp64":
+    traffic = kernel_traffic("fp64" if form == "fp64" else "mixed", dom, ran, N, src_hash)
+    per_gpu = r["value"] / world
+    stage = {"hbm_bytes_per_point_stage": ALG_BYTES_PER_POINT_STAGE,
+             "hbm_achieved_gbs": ALG_BYTES_PER_POINT_STAGE * per_gpu / 1e9,
+             "hbm_peak_gbs": peaks["hbm_gbs"],
+             "hbm_frac": ALG_BYTES_PER_POINT_STAGE * per_gpu / 1e9 / peaks["hbm_gbs"]}
+    if form == "fp64":
+        flops = sum(FP64_FLOPS.values())
+        stage.update(fp64_flops_per_point_stage=flops, fp64_achieved_tflops=flops * per_gpu / 1e12,
+                     fp64_peak_tflops=fma["fp64"], fp64_frac=flops * per_gpu / 1e12 / fma["fp64"])
         achieved = FP64_FLOPS[dom] * N / (prof[dom] * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fma["fp64"], "unit": "TFLOP/s",
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fma["fp64"], "unit": "TFLOP/s",
                 "frac": achieved / fma["fp64"], "traffic": traffic,
-                "peak_source": "FP64 FMA throughput measured in this run (cfd_fma_peak)", "kernel_ms": prof}
-    achieved = MIXED_BYTES[dom] * N / (prof[dom] * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)", "kernel_ms": prof}
+                "peak_source": "FP64 FMA throughput measured in this run (cfd_fma_peak; nominal 1.25 TFLOP/s)",
+                "algorithmic_per_node": FP64_FLOPS[dom], "kernel_ms": prof}
+    else:
+        achieved = ALG_BYTES_PER_POINT_STAGE * N / (sum(prof.values()) * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "whole stage", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "traffic_kernel": dom,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "algorithmic_per_node": ALG_BYTES_PER_POINT_STAGE, "kernel_ms": prof}
+        kc = MIXED_BYTES[dom] * N / (prof[dom] * 1e-3) / 1e9
+        roof["kernel_compulsory"] = {"kernel": dom, "bytes_per_node": MIXED_BYTES[dom], "achieved_gbs": kc,
+                                     "frac": kc / peaks["hbm_gbs"]}
+    return roof, stage
 
 
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group(backend="nccl")
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
     import torch
     torch.cuda.set_device(local)
     from paper_2209_15333_gb300 import build
@@ -397,10 +521,11 @@ def main():
     with Solver((n, n, n), met, **params) as s0:
         s0.set_state(U)
         dt = s0.cfl_dt(0.5)
-    precs = ["mixed", "fp64"] if args.precision == "both" else [args.precision]
-    res = {p: run_precision(args, p, U, met, params, world, local, dt) for p in precs}
+    forms = [f for f in args.forms.split(",") if f]
+    res = {f: run_form(args, f, U, met, params, world, local, dt) for f in forms}
     if args.profile_only:
         return
+    ramp_res = None if args.no_ramp else run_ramp(args, world)
     ens = None if args.no_ensemble else run_ensemble(args, world)
     fma = fma_peaks()
     peaks, peak_kind = measured_peaks()
@@ -414,43 +539,42 @@ def main():
         if world > 1:
             torch.distributed.destroy_process_group()
         return
-    alg_b = (40 + 26.7 + 40)
 
-    def summary(p):
-        r = res[p]
+    def summary(f):
+        r = res[f]
+        roof, stage = rooflines(f, r, N, peaks, fma, src_hash, world)
         d = {"value": r["value"], "unit": "point-stage/s", "ms_per_step": r["ms"] / args.steps,
-             "dtype": "f32+f64" if p == "mixed" else "f64",
-             "roofline": roofline(p, r, N, peaks, fma, src_hash),
-             "hbm_algorithmic": {"bytes_per_point_stage": alg_b,
-                                 "frac": alg_b * r["value"] / world / 1e9 / peaks["hbm_gbs"]},
+             "dtype": "f64" if f == "fp64" else "f32+f64", "roofline": roof, "stage_roofline": stage,
              "err_vs_oracle_1step": field_rel_err(r["U1"], U1o) if U1o is not None else None,
              "class_fraction": r["class_fraction"], "gpu_launches": r["launches"], "clocks": r["clocks"],
-             "e2e": r["e2e"], "kernel_variants": r["variants"]}
-        if p == "fp64":
-            d["fp64_alu_frac_whole_step"] = sum(FP64_FLOPS.values()) * r["value"] / world / 1e12 / fma["fp64"]
+             "e2e": {"value": r["e2e"], "unit": "point-stage/s", "h2d_bytes_per_step": 40 * N,
+                     "d2h_bytes_per_step": 40 * N},
+             "kernel_variants": r["variants"]}
+        if "fallback_fraction" in r:
+            d["fallback_fraction"] = r["fallback_fraction"]
+        if f != "fp64" and "fp64" in res:
+            d["speedup_vs_fp64"] = r["value"] / res["fp64"]["value"]
         return d
 
-    head = "mixed" if "mixed" in res else precs[0]
+    head = "fp64" if "fp64" in res else forms[0]
     h = summary(head)
     line = {
         "metric": "grid-point stage updates/s", "value": h["value"], "unit": "point-stage/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": h["dtype"], "data": "synthetic",
-        "config": arm_config(n, Re, world, "FP32 bulk / FP64 state" if head == "mixed" else "FP64"),
-        "clocks": h["clocks"],
-        "e2e": {"value": h["e2e"], "unit": "point-stage/s", "h2d_bytes_per_step": 40 * N, "d2h_bytes_per_step": 40 * N},
-        "gpu_launches": h["gpu_launches"],
-        "roofline": h["roofline"],
-        "hbm_algorithmic": dict(h["hbm_algorithmic"], peak_gbs=peaks["hbm_gbs"], peak_source=peak_kind),
-        "err_vs_oracle_1step": h["err_vs_oracle_1step"],
-        "class_fraction": h["class_fraction"],
-        "kernel_variants": h["kernel_variants"],
-        "fma_peak_tflops": fma,
-        "kernel_src": src_hash,
-        "cpu_baseline": cpu,
+        "config": arm_config(n, Re, world, "FP64" if head == "fp64" else "FP32 bulk / FP64 state"),
+        "clocks": h["clocks"], "e2e": h["e2e"], "gpu_launches": h["gpu_launches"],
+        "roofline": h["roofline"], "stage_roofline": h["stage_roofline"],
+        "err_vs_oracle_1step": h["err_vs_oracle_1step"], "class_fraction": h["class_fraction"],
+        "kernel_variants": h["kernel_variants"], "fma_peak_tflops": fma, "hbm_peak": {"gbs": peaks["hbm_gbs"],
+                                                                                     "source": peak_kind},
+        "kernel_src": src_hash, "cpu_baseline": cpu,
     }
-    if head == "mixed" and "fp64" in res:
-        line["fp64"] = summary("fp64")
+    for f in forms:
+        if f != head:
+            line[f] = summary(f)
+    if ramp_res is not None:
+        line["ramp"] = ramp_res
     if ens is not None:
         line["ensemble"] = ens
     print(json.dumps(line), flush=True)

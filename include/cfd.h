@@ -271,29 +271,37 @@ cfd_status cfd_profile_stage(cfd_ctx* ctx, int reps, double* ms);
  *  - Every call shares the one array and leaves its contents behind; calls
  *    that overlap on the GPU (several streams, several host threads) race.
  *    Order them on one stream.
- *  - A non-physical state is not reported (no host synchronisation): check
- *    with cfd_rhs when that matters.
+ *  - Nothing detected on the device is reported (the call never
+ *    synchronises with the host): neither a non-physical state nor, in the
+ *    bounds-checked build, an out-of-range index; the next call clears the
+ *    word that records them.  Check with cfd_rhs when that matters.
  * Errors: CFD_EINVAL (null pointer, bad grid or params), CFD_ENOMEM (the
- * grid has more than CFD_NOALLOC_MAX_NODES nodes), CFD_EUNSUPPORTED (as for
- * cfd_create), CFD_ECUDA.
+ * grid has more than CFD_NOALLOC_MAX_NODES nodes), CFD_EUNSUPPORTED (FP32
+ * bulk precision, characteristic reconstruction, the learned sensor -- it
+ * has no weights here -- and what cfd_create rejects), CFD_ECUDA.
  */
 #define CFD_NOALLOC_MAX_NODES 32768
 cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const double* metrics,
                            const double* U, double* dUdt, void* stream);
 
 /* Tuning control, not a step of the method.  The eta (dir 1) and zeta
-   (dir 2) sweeps have two implementations with bit-identical results:
+   (dir 2) sweeps have three implementations with bit-identical results:
    kind 0 streams each x-row of 32 lanes along the line in segments of
-   `param` nodes (no recomputation; best when FP64 arithmetic binds), kind 1
-   works on tiles of 32 x `param` (16 or 32) nodes with a 4-node halo (more
-   parallelism; best when latency binds).  By default the context times all
-   four on its first cfd_rhs / cfd_step and keeps the fastest (cached per
-   process by precision, grid and scheme); cfd_set_sweep_variant fixes one
-   and turns the tuning off.  dir 0 selects the viscous node-flux kernel the
-   same way: kind 0 one thread per node reading its neighbours (CTAs along
-   x rows), kind 1 / 2 a 32 x 8 tile streaming along zeta in segments of
-   64 / 32 planes with a 9-plane shared ring, kind 3 as kind 0 with CTAs of
-   32 x 4 nodes in x-y tiles (param ignored). */
+   `param` nodes (one warp per row), kind 1 works on tiles of 32 x `param`
+   (16 or 32) nodes with a 4-node halo that is split again in every tile,
+   kind 2 walks segments of `param` nodes (0 = the whole line) with 8 warps
+   in chunks of 8 positions, carrying the last stencil rows and face from
+   chunk to chunk (no recomputation).  dir 3 selects the xi sweep: kind 0
+   one CTA per 128-node segment with its halo, kind 1 walking segments of
+   `param` nodes (0 = the whole line) in chunks of 128.  By default the
+   context times the candidates on its first cfd_rhs / cfd_step and keeps the
+   fastest (cached per process by precision, grid and scheme);
+   cfd_set_sweep_variant fixes one and turns the tuning off.  dir 0 selects
+   the viscous node-flux kernel the same way: kind 0 one thread per node
+   reading its neighbours (CTAs along x rows), kind 1 / 2 a 32 x 8 tile
+   streaming along zeta in segments of 64 / 32 planes with a 9-plane shared
+   ring, kind 3 as kind 0 with CTAs of 32 x 4 nodes in x-y tiles (param
+   ignored). */
 cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param);
 cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param);
 

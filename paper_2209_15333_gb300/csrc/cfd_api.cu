@@ -45,8 +45,10 @@ struct cfd_ctx {
     Bufs b;
     double* met = nullptr;          // [31][M]
     float* metf = nullptr;          // [31][M] float mirror
-    int sweep_kind[3] = {0, 0, 0};  // eta/zeta: 0 streaming, 1 tile (chosen by the autotuner)
+    int sweep_kind[3] = {0, 0, 0};  // eta/zeta: 0 streaming, 1 tile, 2 walking (chosen by the autotuner)
     int sweep_param[3] = {0, 128, 128};
+    int xi_kind = 1;                // xi: 0 one CTA per segment of bx nodes with its halo, 1 walking
+    int xi_seg = 0;                 // walking xi: nodes per CTA (0 = the whole line)
     int visc_kind = 0;
     // learned sensor
     void* mlp_buf = nullptr;                    // w1, w2, w3 (bf16), b1, b2, b3 (f32), fallback counter
@@ -422,6 +424,11 @@ static cfd_status launch_sweep_dir(cfd_ctx* ctx, SweepArgs& A, int kind, int par
         const long long nseg = (hi - lo + param - 1) / param;
         const long long warps = (long long)((g.nx + 31) / 32) * nother * nseg;
         k_sweep_s<R, DIR, EP><<<(unsigned)((warps + 3) / 4), 128, stream_smem_bytes<R>(), ctx->stream>>>(A);
+    } else if (kind == 2) {
+        const int seg = param > 0 ? param : std::max(1, hi - lo);
+        A.seg_len = seg;
+        dim3 grid((g.nx + 31) / 32, nother, (hi - lo + seg - 1) / seg);
+        k_sweep_w<R, DIR, EP><<<grid, 256, walk_smem_bytes<R>(), ctx->stream>>>(A);
     } else {
         dim3 grid((g.nx + 31) / 32, nother, (hi - lo + param - 1) / param);
         if (param == 16)
@@ -433,27 +440,40 @@ static cfd_status launch_sweep_dir(cfd_ctx* ctx, SweepArgs& A, int kind, int par
     return CFD_OK;
 }
 
+// xi sweep: kind 0 one CTA per segment of bx nodes (with its 8-node halo),
+// kind 1 walking (seg nodes per CTA, 0 = the whole line)
+template <class R>
+static cfd_status launch_xi(cfd_ctx* ctx, SweepArgs& A, int kind, int seg)
+{
+    const Geo& g = ctx->g;
+    int lo = g.per[0] ? 0 : 1, hi = g.per[0] ? g.nx : g.nx - 1;
+    int nb = ctx->bx;
+    dim3 grid((hi - lo + nb - 1) / nb, g.ny, g.nz);
+    if (!ctx->ph.charrec && kind == 1) {
+        const int sl = seg > 0 ? seg : std::max(1, hi - lo);
+        dim3 gw((hi - lo + sl - 1) / sl, g.ny, g.nz);
+        k_sweep_xw<R, EP_STORE><<<gw, XW, 0, ctx->stream>>>(A, sl);
+    } else if (ctx->ph.charrec) {
+        if (nb == 32) k_sweep_x<R, 32, EP_STORE, true><<<grid, 32, 0, ctx->stream>>>(A);
+        else if (nb == 64) k_sweep_x<R, 64, EP_STORE, true><<<grid, 64, 0, ctx->stream>>>(A);
+        else k_sweep_x<R, 128, EP_STORE, true><<<grid, 128, 0, ctx->stream>>>(A);
+    } else if (nb == 32) {
+        k_sweep_x<R, 32, EP_STORE><<<grid, 32, 0, ctx->stream>>>(A);
+    } else if (nb == 64) {
+        k_sweep_x<R, 64, EP_STORE><<<grid, 64, 0, ctx->stream>>>(A);
+    } else {
+        k_sweep_x<R, 128, EP_STORE><<<grid, 128, 0, ctx->stream>>>(A);
+    }
+    LAUNCH_CHECK();
+    return CFD_OK;
+}
+
 template <class R, int EPF>
 static cfd_status launch_sweeps(cfd_ctx* ctx, SweepArgs& A, cudaEvent_t* ev = nullptr)
 {
-    const Geo& g = ctx->g;
-    // xi
     {
-        int lo = g.per[0] ? 0 : 1, hi = g.per[0] ? g.nx : g.nx - 1;
-        int nb = ctx->bx;
-        dim3 grid((hi - lo + nb - 1) / nb, g.ny, g.nz);
-        if (ctx->ph.charrec) {
-            if (nb == 32) k_sweep_x<R, 32, EP_STORE, true><<<grid, 32, 0, ctx->stream>>>(A);
-            else if (nb == 64) k_sweep_x<R, 64, EP_STORE, true><<<grid, 64, 0, ctx->stream>>>(A);
-            else k_sweep_x<R, 128, EP_STORE, true><<<grid, 128, 0, ctx->stream>>>(A);
-        } else if (nb == 32) {
-            k_sweep_x<R, 32, EP_STORE><<<grid, 32, 0, ctx->stream>>>(A);
-        } else if (nb == 64) {
-            k_sweep_x<R, 64, EP_STORE><<<grid, 64, 0, ctx->stream>>>(A);
-        } else {
-            k_sweep_x<R, 128, EP_STORE><<<grid, 128, 0, ctx->stream>>>(A);
-        }
-        LAUNCH_CHECK();
+        cfd_status sx = launch_xi<R>(ctx, A, ctx->xi_kind, ctx->xi_seg);
+        if (sx != CFD_OK) return sx;
     }
     if (ev) cudaEventRecord(ev[1], ctx->stream);
     cfd_status st = launch_sweep_dir<R, 1, EP_ACCUM>(ctx, A, ctx->sweep_kind[1], ctx->sweep_param[1]);
@@ -488,6 +508,12 @@ static cudaError_t set_sweep_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<R, 16>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_w<R, DIR, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)walk_smem_bytes<R>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sweep_w<R, DIR, EP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
@@ -590,13 +616,13 @@ static cfd_status autotune_t(cfd_ctx* ctx)
     cfd_status st = run_stage<EP_FINAL_RHS>(ctx, ctx->b.U, nullptr, nullptr, ctx->b.Uk, 0.0, 1.0);
     if (st != CFD_OK) return st;
     SweepArgs A = make_args(ctx, ctx->b.U, nullptr, nullptr, ctx->b.Uk, 0.0, 1.0);
-    const int cands[4][2] = {{0, 128}, {0, 64}, {1, 32}, {1, 16}};
+    const int cands[6][2] = {{0, 128}, {0, 64}, {1, 32}, {1, 16}, {2, 0}, {2, 64}};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     for (int dir = 1; dir <= 2 && st == CFD_OK; ++dir) {
         float best = 1e30f;
-        for (int c = 0; c < 4 && st == CFD_OK; ++c) {
+        for (int c = 0; c < 6 && st == CFD_OK; ++c) {
             for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, ctx->stream);
                 if (dir == 1) st = launch_sweep_dir<R, 1, EP_ACCUM>(ctx, A, cands[c][0], cands[c][1]);
@@ -610,6 +636,26 @@ static cfd_status autotune_t(cfd_ctx* ctx)
                 best = ms;
                 ctx->sweep_kind[dir] = cands[c][0];
                 ctx->sweep_param[dir] = cands[c][1];
+            }
+        }
+    }
+    if (!ctx->ph.charrec) {
+        // xi: the per-segment tiles, or walking whole lines / 256-node segments
+        const int xc[3][2] = {{0, 0}, {1, 0}, {1, 256}};
+        float best = 1e30f;
+        for (int c = 0; c < 3 && st == CFD_OK; ++c) {
+            for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, ctx->stream);
+                st = launch_xi<R>(ctx, A, xc[c][0], xc[c][1]);
+            }
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, CFD_ECUDA, "autotune timing");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == CFD_OK && ms < best) {
+                best = ms;
+                ctx->xi_kind = xc[c][0];
+                ctx->xi_seg = xc[c][1];
             }
         }
     }
@@ -648,6 +694,8 @@ static cfd_status autotune(cfd_ctx* ctx)
                     ctx->sweep_param[d] = kv.second[2 * d - 1];
                 }
                 ctx->visc_kind = kv.second[4];
+                ctx->xi_kind = kv.second[5];
+                ctx->xi_seg = kv.second[6];
                 ctx->tuned = true;
                 return CFD_OK;
             }
@@ -663,7 +711,8 @@ static cfd_status autotune(cfd_ctx* ctx)
     ctx->graph_valid = false;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache.push_back(
-        {key, {ctx->sweep_kind[1], ctx->sweep_param[1], ctx->sweep_kind[2], ctx->sweep_param[2], ctx->visc_kind}});
+        {key, {ctx->sweep_kind[1], ctx->sweep_param[1], ctx->sweep_kind[2], ctx->sweep_param[2], ctx->visc_kind,
+               ctx->xi_kind, ctx->xi_seg}});
     return CFD_OK;
 }
 
@@ -677,9 +726,18 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
         ctx->graph_valid = false;
         return CFD_OK;
     }
-    if (dir < 1 || dir > 2 || kind < 0 || kind > 1) return fail(ctx, CFD_EINVAL, "dir must be 0, 1 or 2");
+    if (dir == 3) {
+        if (kind < 0 || kind > 1 || param < 0) return fail(ctx, CFD_EINVAL, "xi kind must be 0 or 1, param >= 0");
+        ctx->xi_kind = kind;
+        ctx->xi_seg = param;
+        ctx->tuned = true;
+        ctx->graph_valid = false;
+        return CFD_OK;
+    }
+    if (dir < 1 || dir > 2 || kind < 0 || kind > 2) return fail(ctx, CFD_EINVAL, "dir must be 0, 1, 2 or 3");
     if (kind == 1 && param != 16 && param != 32) return fail(ctx, CFD_EINVAL, "tile length must be 16 or 32");
     if (kind == 0 && (param < 1 || param > 65535)) return fail(ctx, CFD_EINVAL, "segment length out of range");
+    if (kind == 2 && (param < 0 || param > 65535)) return fail(ctx, CFD_EINVAL, "segment length out of range");
     ctx->sweep_kind[dir] = kind;
     ctx->sweep_param[dir] = param;
     ctx->tuned = true;
@@ -689,7 +747,12 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
 
 extern "C" cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param)
 {
-    if (!ctx || !kind || !param || dir < 0 || dir > 2) return fail(ctx, CFD_EINVAL, "bad argument");
+    if (!ctx || !kind || !param || dir < 0 || dir > 3) return fail(ctx, CFD_EINVAL, "bad argument");
+    if (dir == 3) {
+        *kind = ctx->xi_kind;
+        *param = ctx->xi_seg;
+        return CFD_OK;
+    }
     if (dir == 0) {
         *kind = ctx->visc_kind;
         *param = ctx->visc_kind == 1 ? 64 : (ctx->visc_kind == 2 ? 32 : 0);
@@ -1508,6 +1571,8 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
         return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc computes in FP64 only");
     if (params->recon_vars != CFD_RECON_COMPONENT)
         return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc reconstructs component-wise only");
+    if (params->sensor != CFD_SENSOR_PLAIN)
+        return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc has no learned-sensor weights: plain sensor only");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > kMaxNodes)
         return fail(nullptr, CFD_ENOMEM, "cfd_rhs_noalloc: grid has more than CFD_NOALLOC_MAX_NODES nodes");

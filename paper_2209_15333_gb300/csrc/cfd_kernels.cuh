@@ -1717,6 +1717,346 @@ constexpr size_t tile_smem_bytes()
     return (size_t)(TL + 8) * 32 * (10 + 4) * sizeof(R) + (size_t)(TL + 8) * 32;
 }
 
+// ---------------------------------------------------------------------------
+// walking sweeps: a CTA walks along its line segment in chunks and carries the
+// split fluxes of the last eight stencil nodes and the last face value from
+// one chunk to the next, so every node of the segment is split once and every
+// face is reconstructed once (the tiles above split their 8-node halos again
+// in every tile).  Same operations, in the same order per face and node, as
+// the tiled sweeps: the results are bit-identical.
+// ---------------------------------------------------------------------------
+
+// split fluxes (+ sigma, class, viscous fluxes of direction d) of line
+// position m of a line, or zeros outside a non-periodic line
+template <class R>
+struct RowVals {
+    R fp[5], fm[5], sg, fv[4];
+    uint8_t c;
+    bool ok;
+};
+
+template <class R, int DIR>
+__device__ __forceinline__ void row_vals(const SweepArgs& A, long long base, long long stride, int n, int per, int m,
+                                         int i, int o, bool lane_ok, RowVals<R>& r)
+{
+    const Geo& g = A.g;
+    r.ok = lane_ok && (per || (m >= 0 && m < n));
+    const int mm = per ? wrapi(m, n) : m;
+    if (r.ok) r.ok = in_range(A.err, base + (long long)mm * stride, g.N);
+    r.c = 0;
+    if (r.ok) {
+        const long long nn = base + (long long)mm * stride;
+        const int jj = DIR == 0 ? o : (DIR == 1 ? mm : o);
+        const int ii = DIR == 0 ? mm : i;
+        r.sg = node_split<R>(A, DIR, nn, ii, jj, r.fp, r.fm);
+        if (A.cls) r.c = __ldg(A.cls + nn);
+        if (A.Fv) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r.fv[q] = __ldg((const R*)A.Fv + (long long)(4 * DIR + q) * g.N + nn);
+        }
+    } else {
+        r.sg = (R)0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) r.fp[q] = r.fm[q] = (R)0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r.fv[q] = (R)0;
+    }
+}
+
+// xi sweep, walking: one CTA of XW threads per segment of an x-line (j, k) =
+// (vb.y, vb.z); segment vb.x covers right-hand-side nodes [ms, me) of the
+// line in chunks of XW nodes.  Buffer row r holds line position m0 - 4 + r
+// (r = 0..XW+7), face slot f holds face m0 - 1/2 + f (stencil rows f..f+7).
+// Rows 0..7 and face slot 0 come from the previous chunk.  Rows are stored
+// with an offset of 3 so that the four-face windows of slots 1+4g.. start on
+// a 16-byte boundary.
+constexpr int XW = 128;
+
+template <class R, int EP>
+__device__ __forceinline__ void sweep_xw_body(const SweepArgs& A, uint3 vb, int seg_len)
+{
+    constexpr int ROWS = XW + 8;
+    constexpr int OFF = 3;
+    __shared__ __align__(16) R sf[10][ROWS + OFF + 5];
+    __shared__ R ss[ROWS];
+    __shared__ R sv[4][ROWS];
+    __shared__ uint8_t sc[ROWS];
+    __shared__ R sh[5][XW + 1];
+    __shared__ uint8_t suse[XW + 1];
+    __shared__ R sisc[XW + 1];
+    const Geo& g = A.g;
+    const int n = g.nx;
+    const int per = g.per[0];
+    const int j = vb.y, k = vb.z;
+    const int lo = per ? 0 : 1, hi = per ? n : n - 1;
+    const int ms = lo + (int)vb.x * seg_len;
+    if (ms >= hi) return;
+    const int me = min(ms + seg_len, hi);
+    const long long row = (long long)n * (j + (long long)g.ny * k);
+    const int t = threadIdx.x;
+    const R eps = pk<R>(A.ph.eps, A.ph.epsf);
+    auto put_row = [&](int r, const RowVals<R>& v) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            sf[q][OFF + r] = v.fp[q];
+            sf[5 + q][OFF + r] = v.fm[q];
+        }
+        ss[r] = v.sg;
+        sc[r] = v.c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sv[q][r] = v.fv[q];
+    };
+    // scheme of face slot f (face j = m0 - 1 + f)
+    auto decide = [&](int m0, int f) {
+        const int jf = m0 - 1 + f;
+        uint8_t code = 0xff;
+        R isc = (R)0;
+        if (jf <= me - 1 && (per || jf >= 0)) {
+            int cm = 0;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) cm = max(cm, (int)sc[f + o]);
+            int mp, mm;
+            const int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+            code = (uint8_t)(use | (mp << 2) | (mm << 5));
+            if (use) isc = face_iscale<R>(ss[f + 3], ss[f + 4]);
+        }
+        suse[f] = code;
+        sisc[f] = isc;
+    };
+    auto one_face = [&](int f, int q) {
+        const int code = suse[f];
+        if (code == 0xff) return;
+        R p8[8], m8[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            p8[o] = sf[q][OFF + f + o];
+            m8[o] = sf[5 + q][OFF + f + o];
+        }
+        sh[q][f] = face_flux<R>(code & 3, p8, m8, eps, sisc[f], (code >> 2) & 7, code >> 5);
+    };
+    for (int m0 = ms; m0 < me; m0 += XW) {
+        const bool first = m0 == ms;
+        // new rows: line positions m0+4 .. m0+XW+3 (all XW+8 rows in the first
+        // chunk); loaded and split before the barrier, stored after it
+        RowVals<R> v, v2;
+        {
+            const int m = first ? m0 - 4 + t : m0 + 4 + t;
+            if (m <= me + 3) row_vals<R, 0>(A, row, 1, n, per, m, 0, j, true, v);
+            else v = RowVals<R>{};
+            v2 = RowVals<R>{};
+            if (first && t < 8 && m0 - 4 + XW + t <= me + 3)
+                row_vals<R, 0>(A, row, 1, n, per, m0 - 4 + XW + t, 0, j, true, v2);
+        }
+        // carried values (rows XW..XW+7 and face slot XW of the previous chunk,
+        // stable since that chunk's second barrier) into registers
+        R cv = (R)0, hv = (R)0;
+        uint8_t cc = 0;
+        if (!first) {
+            if (t < 8 * 15) {
+                const int r = t & 7, e = t >> 3;
+                cv = e < 10 ? sf[e][OFF + XW + r] : (e == 10 ? ss[XW + r] : sv[e - 11][XW + r]);
+                if (e == 0) cc = sc[XW + r];
+            }
+            if (t < 5) hv = sh[t][XW];
+        }
+        __syncthreads();  // the previous chunk's faces and rows are consumed
+        if (first) {
+            put_row(t, v);
+            if (t < 8) put_row(XW + t, v2);
+        } else {
+            if (t < 8 * 15) {
+                const int r = t & 7, e = t >> 3;
+                if (e < 10) sf[e][OFF + r] = cv;
+                else if (e == 10) ss[r] = cv;
+                else sv[e - 11][r] = cv;
+                if (e == 0) sc[r] = cc;
+            }
+            if (t < 5) sh[t][0] = hv;
+            put_row(8 + t, v);
+        }
+        __syncthreads();
+        decide(m0, 1 + t);
+        if (first && t == 0) decide(m0, 0);
+        __syncthreads();
+        // faces 1..XW: jobs of four consecutive faces of one component from one
+        // twelve-value window per side (vector shared-memory loads)
+        constexpr int NG = XW / 4;
+        for (int job = t; job < 5 * NG; job += XW) {
+            const int q = job / NG, f0 = 1 + 4 * (job - q * NG);
+            if (m0 - 1 + f0 > me - 1) continue;
+            R pv[12], mv[12];
+#pragma unroll
+            for (int b = 0; b < 12; b += 16 / (int)sizeof(R)) {
+                if constexpr (sizeof(R) == 4) {
+                    const float4 a = *reinterpret_cast<const float4*>(&sf[q][OFF + f0 + b]);
+                    const float4 c = *reinterpret_cast<const float4*>(&sf[5 + q][OFF + f0 + b]);
+                    pv[b] = (R)a.x; pv[b + 1] = (R)a.y; pv[b + 2] = (R)a.z; pv[b + 3] = (R)a.w;
+                    mv[b] = (R)c.x; mv[b + 1] = (R)c.y; mv[b + 2] = (R)c.z; mv[b + 3] = (R)c.w;
+                } else {
+                    const double2 a = *reinterpret_cast<const double2*>(&sf[q][OFF + f0 + b]);
+                    const double2 c = *reinterpret_cast<const double2*>(&sf[5 + q][OFF + f0 + b]);
+                    pv[b] = (R)a.x; pv[b + 1] = (R)a.y;
+                    mv[b] = (R)c.x; mv[b + 1] = (R)c.y;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + u;
+                const int code = suse[f];
+                if (code == 0xff) continue;
+                R p8[8], m8[8];
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    p8[o] = pv[u + o];
+                    m8[o] = mv[u + o];
+                }
+                sh[q][f] = face_flux<R>(code & 3, p8, m8, eps, sisc[f], (code >> 2) & 7, code >> 5);
+            }
+        }
+        if (first && t < 5) one_face(0, t);
+        __syncthreads();
+        const int i = m0 + t;
+        if (i < me) {
+            R val[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) val[q] = -(sh[q][t + 1] - sh[q][t]);
+            if (A.Fv) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    val[r + 1] += dcentral_tile<R>(A.ph.vorder, per, n, i, [&](int mm) { return sv[r][mm - (m0 - 4)]; });
+            }
+            epilogue<R, EP>(A, row + i, i, j, k, val);
+        }
+    }
+    // zero the non-periodic boundary nodes of the accumulator
+    if (EP == EP_STORE && !per && vb.x == 0 && t < 2) {
+        const int ib = t == 0 ? 0 : n - 1;
+        R* Racc = (R*)A.R;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Racc[q * g.N + row + ib] = (R)0;
+    }
+}
+
+// eta / zeta sweep, walking: a CTA of 8 warps owns 32 consecutive x (lanes)
+// of one line family (o = vb.y) and walks the right-hand-side nodes [ms, me)
+// of segment vb.z in chunks of 8 line positions, one per warp.  Walk position
+// q = m - (ms - 4); the split fluxes, sigma and classes of position q live in
+// ring slot q & 15, the viscous fluxes in slot q & 31, face j + 1/2 in slot
+// (j - ms + 1) & 15.  Per chunk: (A) each warp splits one new position,
+// (B) each warp reconstructs one face, (C) each warp differences one node.
+// The split ring is rewritten only after the barrier that ends (B), the
+// viscous ring holds the 24 positions a chunk's (C) and the next chunk's (A)
+// touch, and the face ring is rewritten only after the next chunk's first
+// barrier -- two barriers per chunk.
+constexpr int WS_RING = 16, WV_RING = 32;
+
+template <class R>
+constexpr size_t walk_smem_bytes()
+{
+    return (size_t)WS_RING * 11 * 32 * sizeof(R) + (size_t)WV_RING * 4 * 32 * sizeof(R) +
+           (size_t)WS_RING * 5 * 32 * sizeof(R) + (size_t)WS_RING * 32;
+}
+
+template <class R, int DIR, int EP>
+__device__ __forceinline__ void sweep_w_body(const SweepArgs& A, uint3 vb)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sf = reinterpret_cast<R*>(smem_raw);       // [16][10][32] f+, f-
+    R* ss = sf + WS_RING * 10 * 32;               // [16][32] sigma
+    R* sv = ss + WS_RING * 32;                    // [32][4][32] viscous fluxes of DIR
+    R* sh = sv + WV_RING * 4 * 32;                // [16][5][32] faces
+    uint8_t* sc = reinterpret_cast<uint8_t*>(sh + WS_RING * 5 * 32);  // [16][32]
+    const Geo& g = A.g;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nx = g.nx;
+    const int n = DIR == 1 ? g.ny : g.nz;
+    const long long stride = DIR == 1 ? (long long)nx : (long long)nx * g.ny;
+    const int per = g.per[DIR];
+    const int lo = per ? 0 : 1, hi = per ? n : n - 1;
+    const int i = vb.x * 32 + lane;
+    const bool lane_ok = i < nx;
+    const int o = vb.y;
+    const int S = A.seg_len;
+    const int ms = lo + (int)vb.z * S;
+    if (ms >= hi) return;
+    const int me = min(ms + S, hi);
+    const long long base = DIR == 1 ? (long long)i + (long long)nx * g.ny * o : (long long)i + (long long)nx * o;
+    const R eps = pk<R>(A.ph.eps, A.ph.epsf);
+    auto load_row = [&](int m) {
+        const int q = m - (ms - 4);
+        RowVals<R> v;
+        row_vals<R, DIR>(A, base, stride, n, per, m, i, o, lane_ok, v);
+        R* f = sf + (size_t)(q & (WS_RING - 1)) * 10 * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            f[c * 32] = v.fp[c];
+            f[(5 + c) * 32] = v.fm[c];
+        }
+        ss[(q & (WS_RING - 1)) * 32 + lane] = v.sg;
+        sc[(q & (WS_RING - 1)) * 32 + lane] = v.c;
+        if (A.Fv) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sv[((q & (WV_RING - 1)) * 4 + c) * 32 + lane] = v.fv[c];
+        }
+    };
+    // face jf + 1/2 from ring rows q(jf-3) .. q(jf+4)
+    auto face = [&](int jf) {
+        const int q0 = jf - 3 - (ms - 4);
+        int cm = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) cm = max(cm, (int)sc[((q0 + b) & (WS_RING - 1)) * 32 + lane]);
+        int mp, mm;
+        const int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+        const R isc = use && lane_ok ? face_iscale<R>(ss[((q0 + 3) & (WS_RING - 1)) * 32 + lane],
+                                                      ss[((q0 + 4) & (WS_RING - 1)) * 32 + lane])
+                                     : (R)0;
+        R* out = sh + (size_t)((jf - ms + 1) & (WS_RING - 1)) * 5 * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            R p8[8], m8[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const R* f = sf + (size_t)((q0 + b) & (WS_RING - 1)) * 10 * 32 + lane;
+                p8[b] = f[c * 32];
+                m8[b] = f[(5 + c) * 32];
+            }
+            out[c * 32] = face_flux<R>(use, p8, m8, eps, isc, mp, mm);
+        }
+    };
+    // prologue: positions ms-4 .. ms+3 and the face ms - 1/2
+    load_row(ms - 4 + w);
+    __syncthreads();
+    if (w == 0) face(ms - 1);
+    for (int m0 = ms; m0 < me; m0 += 8) {
+        // (A) the new position m0 + 4 + w (needed up to me + 3)
+        if (m0 + 4 + w <= me + 3) load_row(m0 + 4 + w);
+        __syncthreads();
+        // (B) face m0 + w + 1/2
+        if (m0 + w <= me - 1) face(m0 + w);
+        __syncthreads();
+        // (C) node m0 + w
+        const int m = m0 + w;
+        if (m < me && lane_ok) {
+            const R* f0 = sh + (size_t)((m - ms) & (WS_RING - 1)) * 5 * 32 + lane;
+            const R* f1 = sh + (size_t)((m - ms + 1) & (WS_RING - 1)) * 5 * 32 + lane;
+            R val[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) val[c] = -(f1[c * 32] - f0[c * 32]);
+            if (A.Fv) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    val[c + 1] += dcentral_tile<R>(A.ph.vorder, per, n, m, [&](int mm) {
+                        return sv[(((mm - (ms - 4)) & (WV_RING - 1)) * 4 + c) * 32 + lane];
+                    });
+            }
+            const int mm = per ? wrapi(m, n) : m;
+            const long long nn = base + (long long)mm * stride;
+            const int jj = DIR == 1 ? mm : o, kk = DIR == 1 ? o : mm;
+            epilogue<R, EP>(A, nn, i, jj, kk, val);
+        }
+    }
+}
+
 // dynamic shared memory of k_sweep_s: 4 warps x 8 ring slots x 11 values x 32 lanes
 template <class R>
 constexpr size_t stream_smem_bytes()
@@ -1923,6 +2263,10 @@ __global__ void __launch_bounds__(256, CHAR ? 1 : (sizeof(R) == 4 ? (TL == 16 ? 
 {
     sweep_t_body<R, DIR, EP, TL, CHAR>(A, blockIdx);
 }
+template <class R, int EP>
+__global__ void __launch_bounds__(XW) k_sweep_xw(SweepArgs A, int seg_len) { sweep_xw_body<R, EP>(A, blockIdx, seg_len); }
+template <class R, int DIR, int EP>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_sweep_w(SweepArgs A) { sweep_w_body<R, DIR, EP>(A, blockIdx); }
 
 // ---------------------------------------------------------------------------
 // ... and persistent batched launches over an ensemble of uneven blocks: one

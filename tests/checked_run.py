@@ -24,6 +24,12 @@ def case_list():
     out.append(("ramp_walls", (40, 24, 8), rc["metrics2d"], rc["U"],
                 dict(scheme=3, Re=2000.0, Ma=2.9, T_wall=2.8, visc_law=0, T_ref=108.1, theta1=0.005, theta2=0.02),
                 dict(bc_lo=(2, 1, 0), bc_hi=(3, 3, 0), inflow=rc["inflow"])))
+    # walking sweeps pinned (chunks of 128 xi nodes and 8 eta/zeta positions,
+    # several segments per line, one non-periodic direction)
+    sh = (300, 21, 26)
+    out.append(("walking_segments", sh, cases.uniform_metrics(*sh), turbulence_field(sh, 83, amp=1.5),
+                dict(scheme=3, Re=200.0, Ma=0.5, theta1=0.004, theta2=0.012),
+                dict(bc_lo=(3, 3, 0), bc_hi=(3, 3, 0), variants=[(3, 1, 100), (1, 2, 13), (2, 2, 0)])))
     return out
 
 
@@ -31,9 +37,12 @@ def main(out_path):
     res = {}
     for name, sh, met, U, prm, extra in case_list():
         inflow = extra.pop("inflow", None)
+        variants = extra.pop("variants", ())
         with Solver(sh, met, **extra, **prm) as s:
             if inflow is not None:
                 s.set_inflow(inflow)
+            for d, kind, param in variants:
+                s.set_sweep_variant(d, kind, param)
             s.set_state(U)
             res[name + "_rhs"] = s.rhs()
             s.step(s.cfl_dt(0.4), 3)

@@ -245,23 +245,31 @@ def test_device_pointers_and_stream(orc):
         assert field_rel_err(Ld.cpu().numpy(), Lo) <= TOL
 
 
+# (xi kind, xi segment), (eta/zeta kind, param), viscous kind
+SWEEP_VARIANTS = [((0, 0), (0, 128), 0), ((1, 0), (0, 5), 1), ((1, 128), (1, 32), 2), ((1, 100), (1, 16), 1),
+                  ((0, 0), (2, 0), 3), ((1, 0), (2, 8), 0), ((1, 256), (2, 13), 3)]
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_sweep_variants_bit_identical(orc, precision):
-    """The streaming and tiled eta/zeta sweeps (any segment / tile length)
-    and the node-parallel and 2.5-D viscous kernels give identical bits; the
-    autotuner only changes speed."""
+    """The per-segment and walking xi sweeps, the streaming, tiled and
+    walking eta/zeta sweeps (any segment / tile length) and the node-parallel
+    and 2.5-D viscous kernels give identical bits; the autotuner only changes
+    speed.  Lines of 300 xi nodes span several walking chunks and segments."""
     from paper_2209_15333_gb300.solver import Solver
-    sh = (37, 21, 26)
+    sh = (300, 21, 26)
     bc = dict(bc_lo=(0, 3, 0), bc_hi=(0, 3, 0))   # one non-periodic direction too
     met = cases.uniform_metrics(*sh)
     U = turbulence_field(sh, 61)
     outs = []
-    for (kind, param), vk in zip(((0, 128), (0, 5), (1, 32), (1, 16), (1, 16)), (0, 1, 2, 1, 3)):
+    for (xk, xs), (kind, param), vk in SWEEP_VARIANTS:
         with Solver(sh, met, precision=precision, scheme=3, Re=150.0, theta1=0.004, theta2=0.012, **bc) as s:
             s.set_state(U)
             for d in (1, 2):
                 s.set_sweep_variant(d, kind, param)
+            s.set_sweep_variant(3, xk, xs)
             s.set_sweep_variant(0, vk, 0)
+            assert s.sweep_variant(3) == (xk, xs)
             L = s.rhs()
             s.step(1e-3, 2)
             outs.append((L, s.get_state()))

@@ -2,10 +2,14 @@
 cannot call cudaMalloc (their device memory belongs to another allocator or
 budget, or they must not stall the device the way cudaFree does).
 
-Called through the C ABI with caller-owned device buffers and compared with
-the context-based cfd_rhs on consecutive calls, so that contents the shared
-scratch array keeps from one call cannot leak into the next.  This file is
-collected last; it passes alone in a fresh process and after the other tests.
+Called through the C ABI with caller-owned device buffers and compared, on
+consecutive calls, with the context-based cfd_rhs and with the FP64 oracle
+(so that contents the shared scratch array keeps from one call cannot leak
+into the next, and so that a fault shared by both GPU entry points is still
+caught).  The cases cover periodic boxes and a walled curved ramp grid whose
+state already carries its boundary values (the call applies no boundary
+conditions).  This file is collected last; it passes alone in a fresh process
+and after the other tests.
 """
 import ctypes as C
 
@@ -31,8 +35,25 @@ def torch_cuda():
     return torch
 
 
-def _case(name):
-    """(shape, metrics, params, U) of a periodic case whose U needs no BCs."""
+def _case(name, orc=None):
+    """(shape, metrics, params, U, bc_lo, bc_hi) of a case; U already carries
+    its boundary values."""
+    if name == "ramp_walls":
+        nx, ny, nz = 40, 24, 8
+        rc = cases.ramp_case(nx, ny, nz, 24.0, 2.9, Tw=2.8)
+        params = dict(scheme=3, Re=2000.0, Ma=2.9, T_wall=2.8, visc_law=0, T_ref=108.1)
+        bc_lo, bc_hi = (2, 1, 0), (3, 3, 0)
+        U = rc["U"].copy()
+        rng = np.random.default_rng(11)
+        U[1:4] += 0.01 * rng.standard_normal(U[1:4].shape) * U[0]
+        c = orc.Case(nx, ny, nz, Ma=2.9, T_wall=2.8, visc_law=0, T_ref=108.1, Re=2000.0, scheme=3,
+                     bc_lo=bc_lo, bc_hi=bc_hi, inflow=rc["inflow"])
+        U = orc.apply_bc(c, cases.expand_metrics(rc["metrics2d"], (nz, ny, nx)), U)
+        return (nx, ny, nz), rc["metrics2d"], params, U, bc_lo, bc_hi
+    return _periodic_case(name) + ((0, 0, 0), (0, 0, 0))
+
+
+def _periodic_case(name):
     if name == "tgv32_hybrid":
         n = 32
         return (n, n, n), cases.uniform_metrics(n, n, n), dict(scheme=3, Re=400.0, theta1=0.004,
@@ -47,12 +68,12 @@ def _case(name):
     raise KeyError(name)
 
 
-def _noalloc(torch, shape, met, params, U):
+def _noalloc(torch, shape, met, params, U, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0)):
     from paper_2209_15333_gb300 import _lib as L
     nx, ny, nz = shape
     m = np.asarray(met)
     layout = {1: L.METRICS_UNIFORM, 3: L.METRICS_2D, 4: L.METRICS_3D}[m.ndim]
-    grid = L.make_grid(nx, ny, nz, metric_layout=layout)
+    grid = L.make_grid(nx, ny, nz, bc_lo=bc_lo, bc_hi=bc_hi, metric_layout=layout)
     prm = L.default_params(**params)
     dm = torch.tensor(m, device="cuda", dtype=torch.float64).contiguous()
     dU = torch.tensor(U, device="cuda", dtype=torch.float64).contiguous()
@@ -65,20 +86,42 @@ def _noalloc(torch, shape, met, params, U):
     return dL.cpu().numpy()
 
 
-def _with_context(shape, met, params, U):
+def _with_context(shape, met, params, U, bc_lo, bc_hi):
     from paper_2209_15333_gb300.solver import Solver
-    with Solver(shape, met, **params) as s:
+    with Solver(shape, met, bc_lo=bc_lo, bc_hi=bc_hi, **params) as s:
         s.set_state(U)
         return s.rhs()
 
 
-def test_noalloc_matches_context_rhs_on_consecutive_calls(torch_cuda):
-    for name in ("tgv32_hybrid", "wavy_weno7", "ragged_ud7_inviscid", "tgv32_hybrid"):
-        shape, met, params, U = _case(name)
-        got = _noalloc(torch_cuda, shape, met, params, U)
-        ref = _with_context(shape, met, params, U)
-        assert np.isfinite(got).all()
+def _oracle(orc, shape, met, params, U, bc_lo, bc_hi):
+    nx, ny, nz = shape
+    c = orc.Case(nx, ny, nz, bc_lo=bc_lo, bc_hi=bc_hi, **params)
+    return orc.rhs(c, cases.expand_metrics(met, (nz, ny, nx)), U)
+
+
+def test_noalloc_matches_context_rhs_and_oracle_on_consecutive_calls(torch_cuda, orc):
+    for name in ("tgv32_hybrid", "ramp_walls", "wavy_weno7", "ragged_ud7_inviscid", "ramp_walls", "tgv32_hybrid"):
+        shape, met, params, U, lo, hi = _case(name, orc)
+        got = _noalloc(torch_cuda, shape, met, params, U, lo, hi)
+        assert np.isfinite(got).all(), name
+        ref = _with_context(shape, met, params, U, lo, hi)
         assert field_rel_err(got, ref) <= TOL, name
+        ora = _oracle(orc, shape, met, params, U, lo, hi)
+        assert field_rel_err(got, ora) <= TOL, name
+
+
+def test_noalloc_rejects_the_learned_sensor(torch_cuda):
+    """The call holds no network weights: asking for the learned sensor is an
+    error, not a silent switch to the plain sensor."""
+    from paper_2209_15333_gb300 import _lib as L
+    n = 16
+    grid = L.make_grid(n, n, n, metric_layout=L.METRICS_UNIFORM)
+    prm = L.default_params(sensor=L.SENSOR_MLP)
+    dummy = torch_cuda.zeros(5 * n ** 3, device="cuda", dtype=torch_cuda.float64)
+    p = C.c_void_p(dummy.data_ptr())
+    st = L.lib().cfd_rhs_noalloc(C.byref(grid), C.byref(prm), p, p, p, None)
+    assert st == L.CFD_EUNSUPPORTED
+    assert b"learned-sensor" in L.lib().cfd_last_error(None)
 
 
 def test_noalloc_rejects_grids_beyond_the_limit(torch_cuda):
