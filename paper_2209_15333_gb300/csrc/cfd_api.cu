@@ -227,6 +227,23 @@ static void free_all(cfd_ctx* c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
+// 1 when the metrics are one uniform diagonal matrix (a Cartesian box): the
+// kernels then skip the zero off-diagonal terms (same results)
+static int diagonal_metrics(int layout, const double* metrics, int on_device)
+{
+    if (layout != CFD_METRICS_UNIFORM) return 0;
+    double m[10];
+    if (on_device) {
+        if (cudaMemcpy(m, metrics, sizeof(m), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+    } else {
+        std::memcpy(m, metrics, sizeof(m));
+    }
+    return m[1] == 0.0 && m[2] == 0.0 && m[3] == 0.0 && m[5] == 0.0 && m[6] == 0.0 && m[7] == 0.0;
+}
+
 static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double* metrics, int metrics_on_device,
                                const cfd_params* params, void* stream)
 {
@@ -251,6 +268,7 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     }
     g.mlayout = grid->metric_layout;
     g.M = g.mlayout == CFD_METRICS_3D ? g.N : (g.mlayout == CFD_METRICS_2D ? (long long)g.nx * g.ny : 1);
+    g.diag = diagonal_metrics(g.mlayout, metrics, metrics_on_device);
     Phys& ph = ctx->ph;
     const cfd_params& p = *params;
     ph.gamma = p.gamma;
@@ -259,6 +277,7 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     ph.Ma = p.Ma;
     ph.gMa2 = p.gamma * p.Ma * p.Ma;
     ph.inv2g = 1.0 / (2.0 * p.gamma);
+    ph.invMa = 1.0 / p.Ma;
     ph.viscous = p.Re > 0.0;
     ph.invRe = p.Re > 0.0 ? 1.0 / p.Re : 0.0;
     ph.kcoef = p.Re > 0.0 ? 1.0 / ((p.gamma - 1.0) * p.Ma * p.Ma * p.Pr * p.Re) : 0.0;
@@ -1542,6 +1561,7 @@ static void fill_phys(Phys& ph, const cfd_params& p)
     ph.Ma = p.Ma;
     ph.gMa2 = p.gamma * p.Ma * p.Ma;
     ph.inv2g = 1.0 / (2.0 * p.gamma);
+    ph.invMa = 1.0 / p.Ma;
     ph.viscous = p.Re > 0.0;
     ph.invRe = p.Re > 0.0 ? 1.0 / p.Re : 0.0;
     ph.kcoef = p.Re > 0.0 ? 1.0 / ((p.gamma - 1.0) * p.Ma * p.Ma * p.Pr * p.Re) : 0.0;

@@ -26,13 +26,14 @@ struct Geo {
     int per[3];
     int bc_lo[3], bc_hi[3];
     int mlayout;          // 0 3-D, 1 2-D, 2 uniform
+    int diag;             // 1: every metric matrix is diagonal (uniform Cartesian box)
     long long M;          // metric points
     const double* met;    // [31][M]
     const float* metf;    // [31][M] float mirror (FP32 kernels)
 };
 
 struct Phys {
-    double gamma, gm1, inv_gm1, Ma, gMa2, inv2g;
+    double gamma, gm1, inv_gm1, Ma, gMa2, inv2g, invMa;
     double invRe, kcoef;  // 1/Re, 1/((gamma-1) Ma^2 Pr Re)
     double Tw;
     int viscous, visc_law;
@@ -52,6 +53,14 @@ template <>
 __device__ __forceinline__ double pk<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pk<float>(double, float f) { return f; }
+
+// a * b + c with one rounding.  The stencil arithmetic shared by the kernel
+// families (tiles, walks, streams, ensembles) is written with explicit fused
+// multiply-adds in a fixed order: left to the compiler, a sum of two products
+// may be contracted either way, differently in different kernels, and the
+// families would no longer give the same bits.
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
 
 struct BCData {
     const double* inflow;  // [5][ny] or null
@@ -189,10 +198,23 @@ struct SweepArgs {
 };
 
 // ---------------------------------------------------------------------------
-// primitive recovery (Eq. 5, 8, 16, 17).  The operation order matches the
-// oracle's (no contraction), so that p -- and with it the sensor's class
-// decisions -- are bit-identical to a plain IEEE evaluation.
+// primitive recovery (Eq. 5, 8, 16, 17): one reciprocal of rho per node.  On
+// GB300 every FP64 operation takes a slot of a narrow pipe (two per clock and
+// SM), so the checks of a non-physical state run on the bit patterns in the
+// integer pipe: rho and p positive and finite, |u|, |v|, |w| and T below 1e300.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool positive_finite(double x)
+{
+    // positive finite doubles are the bit patterns 1 .. 0x7FEFFFFFFFFFFFFF
+    return (unsigned long long)__double_as_longlong(x) - 1ull < 0x7FEFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ bool below_1e300(double x)
+{
+    // |x| < 1e300 (false for NaN and infinities)
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) <
+           (unsigned long long)__double_as_longlong(1e300);
+}
+
 template <class RT, bool FLAT = false>
 __device__ __forceinline__ void prim_body(const SweepArgs& A, uint3 vb)
 {
@@ -204,16 +226,17 @@ __device__ __forceinline__ void prim_body(const SweepArgs& A, uint3 vb)
     const long long N = g.N;
     NODE_IJK_SEL(g, FLAT)
     {
-        double rho = U[n];
-        double u = __ddiv_rn(U[N + n], rho);
-        double v = __ddiv_rn(U[2 * N + n], rho);
-        double w = __ddiv_rn(U[3 * N + n], rho);
-        double q2 = __dadd_rn(__dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)), __dmul_rn(w, w));
-        double ke = __dmul_rn(__dmul_rn(0.5, rho), q2);
-        double p = __dmul_rn(ph.gm1, __dsub_rn(U[4 * N + n], ke));
-        double T = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(ph.gamma, ph.Ma), ph.Ma), p), rho);
-        double c = __ddiv_rn(__dsqrt_rn(T), ph.Ma);
-        if (!(rho > 0.0) || !(p > 0.0) || !(T < 1e300) || !(fabs(u) + fabs(v) + fabs(w) < 1e300))
+        const double rho = U[n];
+        const double ri = 1.0 / rho;
+        const double u = U[N + n] * ri;
+        const double v = U[2 * N + n] * ri;
+        const double w = U[3 * N + n] * ri;
+        const double q2 = mad(w, w, mad(v, v, u * u));
+        const double p = ph.gm1 * mad(-0.5 * rho, q2, U[4 * N + n]);
+        const double T = ph.gMa2 * p * ri;
+        const double c = sqrt(T) * ph.invMa;
+        if (!positive_finite(rho) || !positive_finite(p) || !below_1e300(T) || !below_1e300(u) ||
+            !below_1e300(v) || !below_1e300(w))
             *err = 1;
         P[n] = (RT)rho;
         P[N + n] = (RT)u;
@@ -258,7 +281,7 @@ __device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
             double rd = U[n];
             double ri = 1.0 / rd;
             double ud = U[N + n] * ri, vd = U[2 * N + n] * ri, wd = U[3 * N + n] * ri;
-            double pd = ph.gm1 * (U[4 * N + n] - 0.5 * rd * (ud * ud + vd * vd + wd * wd));
+            double pd = ph.gm1 * mad(-0.5 * rd, mad(wd, wd, mad(vd, vd, ud * ud)), U[4 * N + n]);
             double Td = ph.gMa2 * pd * ri;
             rho = (float)rd; u = (float)ud; v = (float)vd; w = (float)wd; p = (float)pd; T = (float)Td;
             c = sqrtf(T) * ph.invMaf;
@@ -268,7 +291,7 @@ __device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
             u = (float)U[N + n] * ri;
             v = (float)U[2 * N + n] * ri;
             w = (float)U[3 * N + n] * ri;
-            p = ph.gm1f * ((float)U[4 * N + n] - 0.5f * rho * (u * u + v * v + w * w));
+            p = ph.gm1f * mad(-0.5f * rho, mad(w, w, mad(v, v, u * u)), (float)U[4 * N + n]);
             T = ph.gMa2f * p * ri;
             c = sqrtf(T) * ph.invMaf;
         }
@@ -284,14 +307,18 @@ __device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
 }
 
 // ---------------------------------------------------------------------------
-// modified Jameson sensor (Eq. 42-43), evaluated in double with the same
-// operation order as a plain IEEE evaluation, so class decisions match.
+// modified Jameson sensor (Eq. 42-43) in FP64 without a division: with
+// phi_d = a_d/b_d (a_d = |p_{m-1} - 2 p_m + p_{m+1}|, b_d = p_{m-1} + 2 p_m +
+// p_{m+1} > 0), theta <= theta_k is decided as
+//   a_0 b_1 b_2 + a_1 b_0 b_2 + a_2 b_0 b_1 <= theta_k b_0 b_1 b_2,
+// the same inequality multiplied by the positive common denominator (the
+// decision can differ from a summed-quotient evaluation only where theta lies
+// within a few units of rounding of a threshold).  Both sides are
+// non-negative, so they compare as integers.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double sensor_phi(double pm, double p0, double pp)
+__device__ __forceinline__ bool nonneg_le(double a, double b)
 {
-    double num = fabs(__dsub_rn(__dadd_rn(-pm, __dmul_rn(2.0, p0)), pp));
-    double den = __dadd_rn(__dadd_rn(pm, __dmul_rn(2.0, p0)), pp);
-    return __ddiv_rn(num, den);
+    return __double_as_longlong(a) <= __double_as_longlong(b);
 }
 
 template <bool FLAT = false>
@@ -304,8 +331,9 @@ __device__ __forceinline__ void sensor_body(const SweepArgs& A, uint3 vb)
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     NODE_IJK_SEL(g, FLAT)
     {
-        double p0 = p[n];
-        double phi[3];
+        const double p0 = p[n];
+        const double p2 = p0 + p0;
+        double a[3], b[3];
         const int pos[3] = {i, j, k};
         const int nd[3] = {nx, ny, nz};
         const long long st[3] = {1, nx, (long long)nx * ny};
@@ -313,15 +341,19 @@ __device__ __forceinline__ void sensor_body(const SweepArgs& A, uint3 vb)
         for (int d = 0; d < 3; ++d) {
             int m = pos[d];
             if (!g.per[d] && (m == 0 || m == nd[d] - 1)) {
-                phi[d] = 0.0;
+                a[d] = 0.0;  // phi_d = 0 at a non-periodic boundary node (reading R4)
+                b[d] = 1.0;
                 continue;
             }
-            long long nm = n + (long long)(wrapi(m - 1, nd[d]) - m) * st[d];
-            long long np = n + (long long)(wrapi(m + 1, nd[d]) - m) * st[d];
-            phi[d] = sensor_phi(p[nm], p0, p[np]);
+            const double pm = p[n + (long long)(wrapi(m - 1, nd[d]) - m) * st[d]];
+            const double pp = p[n + (long long)(wrapi(m + 1, nd[d]) - m) * st[d]];
+            a[d] = fabs((p2 - pm) - pp);
+            b[d] = (pm + p2) + pp;
         }
-        double th = __dadd_rn(__dadd_rn(phi[0], phi[1]), phi[2]);
-        cls[n] = th <= ph.th1 ? 0 : (th <= ph.th2 ? 1 : 2);
+        const double b12 = b[1] * b[2];
+        const double num = mad(a[2], b[0] * b[1], mad(a[1], b[0] * b[2], a[0] * b12));
+        const double den = b[0] * b12;
+        cls[n] = nonneg_le(num, ph.th1 * den) ? 0 : (nonneg_le(num, ph.th2 * den) ? 1 : 2);
     }
 }
 
@@ -348,7 +380,8 @@ __device__ __forceinline__ void sensor32_body(const SweepArgs& A, uint3 vb)
             if (!g.per[d] && (m == 0 || m == nd[d] - 1)) continue;
             float pm = p[n + (long long)(wrapi(m - 1, nd[d]) - m) * st[d]];
             float pp = p[n + (long long)(wrapi(m + 1, nd[d]) - m) * st[d]];
-            th += fabsf(-pm + 2.0f * p0 - pp) / (pm + 2.0f * p0 + pp);
+            const float p2 = p0 + p0;
+            th += fabsf((p2 - pm) - pp) / ((pm + p2) + pp);
         }
         cls[n] = th <= th1 ? 0 : (th <= th2 ? 1 : 2);
     }
@@ -626,45 +659,61 @@ __global__ void k_mlp_features(SweepArgs A, float* out)
 //   f4 = a ((g-1) l1 |u|^2 + s H + c dl (u.k)),   a = rho/(2 g),
 // with H = |u|^2/2 + c^2/(g-1) (the same algebra, fewer operations).
 // ---------------------------------------------------------------------------
+// positive and negative parts max(x, 0), min(x, 0) (Eq. 29); in FP64 on the
+// sign bit in the integer pipe (the FP64 pipe is the bottleneck on GB300)
+__device__ __forceinline__ double pos_part(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double(b & ~(b >> 63));
+}
+__device__ __forceinline__ double neg_part(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double(b & (b >> 63));
+}
+__device__ __forceinline__ float pos_part(float x) { return fmaxf(x, 0.0f); }
+__device__ __forceinline__ float neg_part(float x) { return fminf(x, 0.0f); }
+
 template <class R>
 __device__ __forceinline__ void sw_split(const Phys& ph, R rho, R u, R v, R w, R c, R k1, R k2, R k3,
                                          R sig, R fp[5], R fm[5])
 {
     const R gm1 = pk<R>(ph.gm1, ph.gm1f);
-    R uk = k1 * u + k2 * v + k3 * w;
-    R V = sig * uk;
-    R cs = c * sig;
-    R l4 = V - cs, l5 = V + cs;
-    R q2 = u * u + v * v + w * w;
-    R H = (R)0.5 * q2 + c * c * pk<R>(ph.inv_gm1, ph.inv_gm1f);
-    R a = rho * pk<R>(ph.inv2g, ph.inv2gf);
-    R gq = gm1 * q2;
-    R ac = a * c;
+    const R gm1x2 = gm1 + gm1;
+    const R uk = mad(k3, w, mad(k2, v, k1 * u));
+    const R V = sig * uk;
+    const R cs = c * sig;
+    const R l4 = V - cs, l5 = V + cs;
+    const R q2 = mad(w, w, mad(v, v, u * u));
+    const R H = mad(c * c, pk<R>(ph.inv_gm1, ph.inv_gm1f), (R)0.5 * q2);
+    const R a = rho * pk<R>(ph.inv2g, ph.inv2gf);
+    const R gq = gm1 * q2;
+    const R ac = a * c;
     {
-        R l1 = V > (R)0 ? V : (R)0;
-        R a4 = l4 > (R)0 ? l4 : (R)0;
-        R a5 = l5 > (R)0 ? l5 : (R)0;
-        R s = a4 + a5, dl = a5 - a4;
-        R f0 = a * ((R)2 * gm1 * l1 + s);
-        R t = ac * dl;
+        const R l1 = pos_part(V);
+        const R a4 = pos_part(l4);
+        const R a5 = pos_part(l5);
+        const R s = a4 + a5, dl = a5 - a4;
+        const R f0 = a * mad(gm1x2, l1, s);
+        const R t = ac * dl;
         fp[0] = f0;
-        fp[1] = u * f0 + t * k1;
-        fp[2] = v * f0 + t * k2;
-        fp[3] = w * f0 + t * k3;
-        fp[4] = a * (l1 * gq + s * H) + t * uk;
+        fp[1] = mad(u, f0, t * k1);
+        fp[2] = mad(v, f0, t * k2);
+        fp[3] = mad(w, f0, t * k3);
+        fp[4] = mad(t, uk, a * mad(l1, gq, s * H));
     }
     {
-        R l1 = V < (R)0 ? V : (R)0;
-        R a4 = l4 < (R)0 ? l4 : (R)0;
-        R a5 = l5 < (R)0 ? l5 : (R)0;
-        R s = a4 + a5, dl = a5 - a4;
-        R f0 = a * ((R)2 * gm1 * l1 + s);
-        R t = ac * dl;
+        const R l1 = neg_part(V);
+        const R a4 = neg_part(l4);
+        const R a5 = neg_part(l5);
+        const R s = a4 + a5, dl = a5 - a4;
+        const R f0 = a * mad(gm1x2, l1, s);
+        const R t = ac * dl;
         fm[0] = f0;
-        fm[1] = u * f0 + t * k1;
-        fm[2] = v * f0 + t * k2;
-        fm[3] = w * f0 + t * k3;
-        fm[4] = a * (l1 * gq + s * H) + t * uk;
+        fm[1] = mad(u, f0, t * k1);
+        fm[2] = mad(v, f0, t * k2);
+        fm[3] = mad(w, f0, t * k3);
+        fm[4] = mad(t, uk, a * mad(l1, gq, s * H));
     }
 }
 
@@ -676,9 +725,13 @@ template <class R>
 __device__ __forceinline__ R ud7(const R v[7])
 {
     // Eq. 41
-    return ((R)(-3.0 / 420.0)) * v[0] + ((R)(25.0 / 420.0)) * v[1] + ((R)(-101.0 / 420.0)) * v[2] +
-           ((R)(319.0 / 420.0)) * v[3] + ((R)(214.0 / 420.0)) * v[4] + ((R)(-38.0 / 420.0)) * v[5] +
-           ((R)(4.0 / 420.0)) * v[6];
+    R r = ((R)(-3.0 / 420.0)) * v[0];
+    r = mad((R)(25.0 / 420.0), v[1], r);
+    r = mad((R)(-101.0 / 420.0), v[2], r);
+    r = mad((R)(319.0 / 420.0), v[3], r);
+    r = mad((R)(214.0 / 420.0), v[4], r);
+    r = mad((R)(-38.0 / 420.0), v[5], r);
+    return mad((R)(4.0 / 420.0), v[6], r);
 }
 
 // Smoothness indicator as a weighted sum of squares of constant-annihilating
@@ -691,12 +744,23 @@ __device__ __forceinline__ R beta_rows(const double (&S)[NS], const double (&SD)
     R b = (R)0;
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
-        R h = (R)0;
+        R h = (R)S[i * r] * f[0];
 #pragma unroll
-        for (int l = 0; l < r; ++l) h += (R)S[i * r + l] * f[l];
-        b += (R)SD[i] * (h * h);
+        for (int l = 1; l < r; ++l) h = mad((R)S[i * r + l], f[l], h);
+        b = i == 0 ? (R)SD[0] * (h * h) : mad((R)SD[i], h * h, b);
     }
     return b;
+}
+
+template <class R>
+__device__ __forceinline__ R dot4(const double (&c)[4], const R* v)
+{
+    return mad((R)c[3], v[3], mad((R)c[2], v[2], mad((R)c[1], v[1], (R)c[0] * v[0])));
+}
+template <class R>
+__device__ __forceinline__ R dot3(const double (&c)[3], const R* v)
+{
+    return mad((R)c[2], v[2], mad((R)c[1], v[1], (R)c[0] * v[0]));
 }
 
 // WENO7 (Balsara-Shu) on v[0..6]; one division (weights over a common
@@ -709,14 +773,11 @@ __device__ __forceinline__ R weno7(const R v[7], R eps, R isc)
     constexpr double SD[3] = W7_SD;
     constexpr double C0[4] = W7_C0, C1[4] = W7_C1, C2[4] = W7_C2, C3[4] = W7_C3;
     constexpr double S0[12] = W7_S0, S1[12] = W7_S1, S2[12] = W7_S2, S3[12] = W7_S3;
-    R q0 = (R)C0[0] * v[0] + (R)C0[1] * v[1] + (R)C0[2] * v[2] + (R)C0[3] * v[3];
-    R q1 = (R)C1[0] * v[1] + (R)C1[1] * v[2] + (R)C1[2] * v[3] + (R)C1[3] * v[4];
-    R q2 = (R)C2[0] * v[2] + (R)C2[1] * v[3] + (R)C2[2] * v[4] + (R)C2[3] * v[5];
-    R q3 = (R)C3[0] * v[3] + (R)C3[1] * v[4] + (R)C3[2] * v[5] + (R)C3[3] * v[6];
-    R b0 = eps + isc * beta_rows<R>(S0, SD, v + 0);
-    R b1 = eps + isc * beta_rows<R>(S1, SD, v + 1);
-    R b2 = eps + isc * beta_rows<R>(S2, SD, v + 2);
-    R b3 = eps + isc * beta_rows<R>(S3, SD, v + 3);
+    const R q0 = dot4<R>(C0, v + 0), q1 = dot4<R>(C1, v + 1), q2 = dot4<R>(C2, v + 2), q3 = dot4<R>(C3, v + 3);
+    R b0 = mad(isc, beta_rows<R>(S0, SD, v + 0), eps);
+    R b1 = mad(isc, beta_rows<R>(S1, SD, v + 1), eps);
+    R b2 = mad(isc, beta_rows<R>(S2, SD, v + 2), eps);
+    R b3 = mad(isc, beta_rows<R>(S3, SD, v + 3), eps);
     R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2, t3 = b3 * b3;
     R w0, w1, w2, w3;
     if (sizeof(R) == 8) {
@@ -728,7 +789,7 @@ __device__ __forceinline__ R weno7(const R v[7], R eps, R isc)
         // the denormal range, so divide per candidate
         w0 = (R)D[0] / t0; w1 = (R)D[1] / t1; w2 = (R)D[2] / t2; w3 = (R)D[3] / t3;
     }
-    return (w0 * q0 + w1 * q1 + w2 * q2 + w3 * q3) / (w0 + w1 + w2 + w3);
+    return mad(w3, q3, mad(w2, q2, mad(w1, q1, w0 * q0))) / (((w0 + w1) + w2) + w3);
 }
 
 // WENO5 (Jiang-Shu) on v[1..5] = f_{j-2..j+2}; mask bit k drops sub-stencil k
@@ -740,12 +801,10 @@ __device__ __forceinline__ R weno5(const R v[7], R eps, R isc, int mask)
     constexpr double SD[2] = W5_SD;
     constexpr double C0[3] = W5_C0, C1[3] = W5_C1, C2[3] = W5_C2;
     constexpr double S0[6] = W5_S0, S1[6] = W5_S1, S2[6] = W5_S2;
-    R q0 = (R)C0[0] * v[1] + (R)C0[1] * v[2] + (R)C0[2] * v[3];
-    R q1 = (R)C1[0] * v[2] + (R)C1[1] * v[3] + (R)C1[2] * v[4];
-    R q2 = (R)C2[0] * v[3] + (R)C2[1] * v[4] + (R)C2[2] * v[5];
-    R b0 = eps + isc * beta_rows<R>(S0, SD, v + 1);
-    R b1 = eps + isc * beta_rows<R>(S1, SD, v + 2);
-    R b2 = eps + isc * beta_rows<R>(S2, SD, v + 3);
+    const R q0 = dot3<R>(C0, v + 1), q1 = dot3<R>(C1, v + 2), q2 = dot3<R>(C2, v + 3);
+    R b0 = mad(isc, beta_rows<R>(S0, SD, v + 1), eps);
+    R b1 = mad(isc, beta_rows<R>(S1, SD, v + 2), eps);
+    R b2 = mad(isc, beta_rows<R>(S2, SD, v + 3), eps);
     R t0 = b0 * b0, t1 = b1 * b1, t2 = b2 * b2;
     R w0, w1, w2;
     if (sizeof(R) == 8) {
@@ -756,7 +815,7 @@ __device__ __forceinline__ R weno5(const R v[7], R eps, R isc, int mask)
     if (mask & 1) w0 = (R)0;
     if (mask & 2) w1 = (R)0;
     if (mask & 4) w2 = (R)0;
-    return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+    return mad(w2, q2, mad(w1, q1, w0 * q0)) / ((w0 + w1) + w2);
 }
 
 // one face value from upwind-ordered values; use: 0 UD7, 1 WENO7, 2 WENO5
@@ -904,29 +963,33 @@ __device__ __forceinline__ int face_use(const Phys& ph, int per, int n, int j, i
 // ---------------------------------------------------------------------------
 // central first derivative in index space with the closures of Section 2.3
 // ---------------------------------------------------------------------------
+// central first-derivative stencils from the differences d_k = f(m+k) - f(m-k)
+template <class R>
+__device__ __forceinline__ R cen8(R d1, R d2, R d3, R d4)
+{
+    return mad((R)(-3.0 / 840.0), d4, mad((R)(32.0 / 840.0), d3, mad((R)(-168.0 / 840.0), d2, (R)(672.0 / 840.0) * d1)));
+}
+template <class R>
+__device__ __forceinline__ R cen6(R d1, R d2, R d3)
+{
+    return mad((R)(1.0 / 60.0), d3, mad((R)(-9.0 / 60.0), d2, (R)(45.0 / 60.0) * d1));
+}
+
 template <class R, class Ld>
 __device__ __forceinline__ R dcentral(int order, int per, int n, int m, Ld f)
 {
     if (per) {
-        if (order == 8)
-            return ((R)(672.0 / 840.0)) * (f(wrapi(m + 1, n)) - f(wrapi(m - 1, n))) +
-                   ((R)(-168.0 / 840.0)) * (f(wrapi(m + 2, n)) - f(wrapi(m - 2, n))) +
-                   ((R)(32.0 / 840.0)) * (f(wrapi(m + 3, n)) - f(wrapi(m - 3, n))) +
-                   ((R)(-3.0 / 840.0)) * (f(wrapi(m + 4, n)) - f(wrapi(m - 4, n)));
-        return ((R)(45.0 / 60.0)) * (f(wrapi(m + 1, n)) - f(wrapi(m - 1, n))) +
-               ((R)(-9.0 / 60.0)) * (f(wrapi(m + 2, n)) - f(wrapi(m - 2, n))) +
-               ((R)(1.0 / 60.0)) * (f(wrapi(m + 3, n)) - f(wrapi(m - 3, n)));
+        auto d = [&](int k) { return f(wrapi(m + k, n)) - f(wrapi(m - k, n)); };
+        if (order == 8) return cen8<R>(d(1), d(2), d(3), d(4));
+        return cen6<R>(d(1), d(2), d(3));
     }
-    if (m == 0) return (R)(-1.5) * f(0) + (R)2 * f(1) - (R)0.5 * f(2);
-    if (m == n - 1) return (R)1.5 * f(n - 1) - (R)2 * f(n - 2) + (R)0.5 * f(n - 3);
-    if (m == 1 || m == n - 2) return (R)0.5 * (f(m + 1) - f(m - 1));
-    if (m == 2 || m == n - 3)
-        return ((R)(8.0 / 12.0)) * (f(m + 1) - f(m - 1)) - ((R)(1.0 / 12.0)) * (f(m + 2) - f(m - 2));
-    if (m == 3 || m == n - 4 || order == 6)
-        return ((R)(45.0 / 60.0)) * (f(m + 1) - f(m - 1)) + ((R)(-9.0 / 60.0)) * (f(m + 2) - f(m - 2)) +
-               ((R)(1.0 / 60.0)) * (f(m + 3) - f(m - 3));
-    return ((R)(672.0 / 840.0)) * (f(m + 1) - f(m - 1)) + ((R)(-168.0 / 840.0)) * (f(m + 2) - f(m - 2)) +
-           ((R)(32.0 / 840.0)) * (f(m + 3) - f(m - 3)) + ((R)(-3.0 / 840.0)) * (f(m + 4) - f(m - 4));
+    if (m == 0) return mad((R)(-0.5), f(2), mad((R)2, f(1), (R)(-1.5) * f(0)));
+    if (m == n - 1) return mad((R)0.5, f(n - 3), mad((R)(-2), f(n - 2), (R)1.5 * f(n - 1)));
+    auto d = [&](int k) { return f(m + k) - f(m - k); };
+    if (m == 1 || m == n - 2) return (R)0.5 * d(1);
+    if (m == 2 || m == n - 3) return mad((R)(-1.0 / 12.0), d(2), (R)(8.0 / 12.0) * d(1));
+    if (m == 3 || m == n - 4 || order == 6) return cen6<R>(d(1), d(2), d(3));
+    return cen8<R>(d(1), d(2), d(3), d(4));
 }
 
 // central derivative on a tile: f(m) takes unwrapped line positions, so the
@@ -935,11 +998,9 @@ template <class R, class Ld>
 __device__ __forceinline__ R dcentral_tile(int order, int per, int n, int m, Ld f)
 {
     if (per) {
-        if (order == 8)
-            return ((R)(672.0 / 840.0)) * (f(m + 1) - f(m - 1)) + ((R)(-168.0 / 840.0)) * (f(m + 2) - f(m - 2)) +
-                   ((R)(32.0 / 840.0)) * (f(m + 3) - f(m - 3)) + ((R)(-3.0 / 840.0)) * (f(m + 4) - f(m - 4));
-        return ((R)(45.0 / 60.0)) * (f(m + 1) - f(m - 1)) + ((R)(-9.0 / 60.0)) * (f(m + 2) - f(m - 2)) +
-               ((R)(1.0 / 60.0)) * (f(m + 3) - f(m - 3));
+        auto d = [&](int k) { return f(m + k) - f(m - k); };
+        if (order == 8) return cen8<R>(d(1), d(2), d(3), d(4));
+        return cen6<R>(d(1), d(2), d(3));
     }
     return dcentral<R>(order, 0, n, m, f);
 }
@@ -949,7 +1010,10 @@ __device__ __forceinline__ R dcentral_tile(int order, int per, int n, int m, Ld 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double viscosity(const Phys& ph, double T)
 {
-    if (ph.visc_law == 1) return pow(T, ph.omega);
+    // T^omega as exp(omega log T): relative error a few units of rounding for
+    // the temperatures of a flow (|omega log T| < 10), about half the FP64
+    // operations of the general pow
+    if (ph.visc_law == 1) return exp(ph.omega * log(T));
     double s = ph.suth_s;
     return T * sqrt(T) * (1.0 + s) / (T + s);
 }
@@ -959,6 +1023,84 @@ __device__ __forceinline__ float viscosity(const Phys& ph, float T)
     if (ph.visc_law == 1) return powf(T, ph.omegaf);
     float s = ph.suth_sf;
     return T * sqrtf(T) * (1.0f + s) / (T + s);
+}
+
+// Cartesian gradients q_x = xi_x q_xi + eta_x q_eta + zeta_x q_zeta, ... of
+// u, v, w, T (Eq. 9-14 through the metrics of Eq. 3).  On a box whose metric
+// matrices are diagonal the zero terms of the sums are skipped: a fused
+// multiply-add with a zero factor adds exactly nothing, so both forms give
+// the same bits.
+template <class R>
+__device__ __forceinline__ void cartesian_gradients(const Geo& g, long long mi, const R dq[4][3], R gr[4][3])
+{
+    if (g.diag) {
+        const R m0 = metr<R>(g, M_RAW + 0, mi), m1 = metr<R>(g, M_RAW + 4, mi), m2 = metr<R>(g, M_RAW + 8, mi);
+#pragma unroll
+        for (int var = 0; var < 4; ++var) {
+            gr[var][0] = m0 * dq[var][0];
+            gr[var][1] = m1 * dq[var][1];
+            gr[var][2] = m2 * dq[var][2];
+        }
+        return;
+    }
+    R mraw[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) mraw[e] = metr<R>(g, M_RAW + e, mi);
+#pragma unroll
+    for (int var = 0; var < 4; ++var)
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+            gr[var][x] = mad(mraw[6 + x], dq[var][2], mad(mraw[3 + x], dq[var][1], mraw[x] * dq[var][0]));
+}
+
+// viscous fluxes at a node: Fv_d = alpha_d . (tau, Theta) with alpha_d =
+// grad(d)/J (Eq. 9-11); diagonal metrics keep the one nonzero term
+template <class R>
+__device__ __forceinline__ void store_visc_fluxes(const Geo& g, long long mi, long long n, const R tau[3][3],
+                                                  const R Th[3], R* __restrict__ Fv)
+{
+    const long long N = g.N;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (g.diag) {
+            const R ad = metr<R>(g, M_ALPHA + 4 * d, mi);
+#pragma unroll
+            for (int row = 0; row < 3; ++row) Fv[(long long)(4 * d + row) * N + n] = ad * tau[d][row];
+            Fv[(long long)(4 * d + 3) * N + n] = ad * Th[d];
+            continue;
+        }
+        R a0 = metr<R>(g, M_ALPHA + 3 * d, mi), a1 = metr<R>(g, M_ALPHA + 3 * d + 1, mi),
+          a2 = metr<R>(g, M_ALPHA + 3 * d + 2, mi);
+#pragma unroll
+        for (int row = 0; row < 3; ++row)
+            Fv[(long long)(4 * d + row) * N + n] = mad(a2, tau[2][row], mad(a1, tau[1][row], a0 * tau[0][row]));
+        Fv[(long long)(4 * d + 3) * N + n] = mad(a2, Th[2], mad(a1, Th[1], a0 * Th[0]));
+    }
+}
+
+// fluxes of one node from its derivatives of u, v, w, T in index space
+// (gradients through the metrics, mu(T), tau and Theta of Eq. 12-15)
+template <class R>
+__device__ __forceinline__ void visc_node_flux(const Geo& g, const Phys& ph, long long n, int i, int j, const R dq[4][3],
+                                               R T, R u, R v, R w, R* __restrict__ Fv)
+{
+    const long long mi = midx(g, i, j, n);
+    R gr[4][3];
+    cartesian_gradients<R>(g, mi, dq, gr);
+    const R mu = viscosity(ph, T);
+    const R mr = mu * pk<R>(ph.invRe, ph.invRef);
+    const R div = (gr[0][0] + gr[1][1]) + gr[2][2];
+    R tau[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            tau[a][b] = a == b ? mr * mad((R)(-2.0 / 3.0), div, gr[a][a] + gr[a][a]) : mr * (gr[a][b] + gr[b][a]);
+    const R kc = mu * pk<R>(ph.kcoef, ph.kcoeff);
+    R Th[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Th[a] = mad(kc, gr[3][a], mad(w, tau[a][2], mad(v, tau[a][1], u * tau[a][0])));
+    store_visc_fluxes<R>(g, mi, n, tau, Th, Fv);
 }
 
 // YB > 0: CTAs of 32 x YB nodes in an x-y tile (the y neighbours of a tile's
@@ -1026,40 +1168,7 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
                                               [&](int mm) { return __ldg(f + off[d][mm - m + 4]); });
             }
         }
-        const long long mi = midx(g, i, j, n);
-        R mraw[9];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) mraw[e] = metr<R>(g, M_RAW + e, mi);
-        R gr[4][3];
-#pragma unroll
-        for (int var = 0; var < 4; ++var)
-#pragma unroll
-            for (int x = 0; x < 3; ++x)
-                gr[var][x] = mraw[x] * dq[var][0] + mraw[3 + x] * dq[var][1] + mraw[6 + x] * dq[var][2];
-        R T = P[5 * N + n];
-        R mu = viscosity(ph, T);
-        R mr = mu * pk<R>(ph.invRe, ph.invRef);
-        R div = gr[0][0] + gr[1][1] + gr[2][2];
-        R tau[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-                tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? ((R)(2.0 / 3.0)) * div : (R)0));
-        R kc = mu * pk<R>(ph.kcoef, ph.kcoeff);
-        R u = P[N + n], v = P[2 * N + n], w = P[3 * N + n];
-        R Th[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Th[a] = u * tau[a][0] + v * tau[a][1] + w * tau[a][2] + kc * gr[3][a];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            R a0 = metr<R>(g, M_ALPHA + 3 * d, mi), a1 = metr<R>(g, M_ALPHA + 3 * d + 1, mi),
-              a2 = metr<R>(g, M_ALPHA + 3 * d + 2, mi);
-#pragma unroll
-            for (int row = 0; row < 3; ++row)
-                Fv[(long long)(4 * d + row) * N + n] = a0 * tau[0][row] + a1 * tau[1][row] + a2 * tau[2][row];
-            Fv[(long long)(4 * d + 3) * N + n] = a0 * Th[0] + a1 * Th[1] + a2 * Th[2];
-        }
+        visc_node_flux<R>(g, ph, n, i, j, dq, P[5 * N + n], P[N + n], P[2 * N + n], P[3 * N + n], Fv);
     }
 }
 
@@ -1069,45 +1178,6 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
 // derivatives of the centre plane and the zeta derivatives all come from
 // shared memory, so every value is read from L2/HBM about 2.5 times instead of
 // once per stencil use.  Same operations, in the same order, as k_visc_flux.
-template <class R>
-__device__ __forceinline__ void visc_node_flux(const Geo& g, const Phys& ph, long long n, int i, int j, const R dq[4][3],
-                                               R T, R u, R v, R w, R* __restrict__ Fv)
-{
-    const long long N = g.N;
-    const long long mi = midx(g, i, j, n);
-    R mraw[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) mraw[e] = metr<R>(g, M_RAW + e, mi);
-    R gr[4][3];
-#pragma unroll
-    for (int var = 0; var < 4; ++var)
-#pragma unroll
-        for (int x = 0; x < 3; ++x)
-            gr[var][x] = mraw[x] * dq[var][0] + mraw[3 + x] * dq[var][1] + mraw[6 + x] * dq[var][2];
-    R mu = viscosity(ph, T);
-    R mr = mu * pk<R>(ph.invRe, ph.invRef);
-    R div = gr[0][0] + gr[1][1] + gr[2][2];
-    R tau[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            tau[a][b] = mr * (gr[a][b] + gr[b][a] - (a == b ? ((R)(2.0 / 3.0)) * div : (R)0));
-    R kc = mu * pk<R>(ph.kcoef, ph.kcoeff);
-    R Th[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) Th[a] = u * tau[a][0] + v * tau[a][1] + w * tau[a][2] + kc * gr[3][a];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        R a0 = metr<R>(g, M_ALPHA + 3 * d, mi), a1 = metr<R>(g, M_ALPHA + 3 * d + 1, mi),
-          a2 = metr<R>(g, M_ALPHA + 3 * d + 2, mi);
-#pragma unroll
-        for (int row = 0; row < 3; ++row)
-            Fv[(long long)(4 * d + row) * N + n] = a0 * tau[0][row] + a1 * tau[1][row] + a2 * tau[2][row];
-        Fv[(long long)(4 * d + 3) * N + n] = a0 * Th[0] + a1 * Th[1] + a2 * Th[2];
-    }
-}
-
 template <class R>
 constexpr size_t visc25_smem_bytes()
 {
@@ -1207,7 +1277,7 @@ __device__ __forceinline__ void epilogue(const SweepArgs& A, long long n, int i,
                 double L = J * (double)(Racc[q * N + n] + val[q]);
                 double uk = A.U[q * N + n];
                 double un = A.rk_a != 0.0 ? A.Un[q * N + n] : 0.0;
-                A.Uout[q * N + n] = A.rk_a * un + A.rk_b * (uk + dt * L);
+                A.Uout[q * N + n] = mad(A.rk_a, un, A.rk_b * mad(dt, L, uk));
             }
         }
     }
