@@ -291,17 +291,25 @@ cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const
    (16 or 32) nodes with a 4-node halo that is split again in every tile,
    kind 2 walks segments of `param` nodes (0 = the whole line) with 8 warps
    in chunks of 8 positions, carrying the last stencil rows and face from
-   chunk to chunk (no recomputation).  dir 3 selects the xi sweep: kind 0
-   one CTA per 128-node segment with its halo, kind 1 walking segments of
-   `param` nodes (0 = the whole line) in chunks of 128.  By default the
-   context times the candidates on its first cfd_rhs / cfd_step and keeps the
-   fastest (cached per process by precision, grid and scheme);
-   cfd_set_sweep_variant fixes one and turns the tuning off.  dir 0 selects
-   the viscous node-flux kernel the same way: kind 0 one thread per node
-   reading its neighbours (CTAs along x rows), kind 1 / 2 a 32 x 8 tile
-   streaming along zeta in segments of 64 / 32 planes with a 9-plane shared
-   ring, kind 3 as kind 0 with CTAs of 32 x 4 nodes in x-y tiles (param
-   ignored). */
+   chunk to chunk (no recomputation); kind 3 is kind 2 with the rows fetched
+   by the tensor memory accelerator into a ring of staging buffers ahead of
+   the warps (FP32 bulk only, nx a multiple of 32; CFD_EUNSUPPORTED
+   otherwise).  dir 3 selects the xi sweep: kind 0 one CTA per 128-node
+   segment with its halo, kind 1 walking segments of `param` nodes (0 = the
+   whole line) in chunks of 128.  dir 0 selects the viscous node-flux
+   kernel: kind 0 one thread per node reading its neighbours (CTAs along x
+   rows), kind 1 / 2 a 32 x 8 tile streaming along zeta in segments of 64 /
+   32 planes with a 9-plane shared ring, kind 3 as kind 0 with CTAs of 32 x 4
+   nodes in x-y tiles (param ignored).  Ensembles offer three variants per
+   kernel kind: viscous (2, 32), (1, 64), (3, 0); xi (0, 64), (0, 128),
+   (1, 0); eta and zeta (1, 16), (1, 32), (2, 64).
+   By default a context times the candidates on its first cfd_rhs / cfd_step
+   and keeps the fastest; cfd_set_sweep_variant fixes one and turns the
+   tuning off.  Choices are cached in the process and in a text file (the
+   path in the environment variable CFD_GB300_TUNE_CACHE, "off" for none;
+   default $XDG_CACHE_HOME or ~/.cache, paper_2209_15333_gb300/autotune.txt),
+   keyed by library build, GPU name and SM count, precision, grid, boundary
+   conditions and scheme, so that a later process skips the trial runs. */
 cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param);
 cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param);
 

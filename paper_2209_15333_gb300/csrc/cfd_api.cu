@@ -2,6 +2,7 @@
 // orchestration and CUDA-graph replay of the TVD-RK3 step (Eq. 45).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <mutex>
 #include <vector>
@@ -12,6 +13,8 @@
 #include <string>
 #include <thread>
 
+#include <sys/stat.h>
+
 #include "../../include/cfd.h"
 #include "cfd_kernels.cuh"
 
@@ -20,6 +23,11 @@ using namespace cfdk;
 namespace {
 
 constexpr int kSMs = 152;
+// kernel kinds of an ensemble with more than one variant, the number of
+// variants each, and the walking eta/zeta segment of the ensemble
+enum { KIND_VISC = 0, KIND_SX = 1, KIND_T1 = 2, KIND_T2 = 3, KIND_COUNT = 4 };
+constexpr int kBatchVariants = 3;
+constexpr int kBatchWS = 64;
 
 struct Bufs {
     double* U = nullptr;      // [5][N] state U^n
@@ -60,8 +68,9 @@ struct cfd_ctx {
     std::vector<cfd_ctx*> sub;
     SweepArgs* d_tbl[3] = {nullptr, nullptr, nullptr};  // per stage, [nb]
     int* d_maps = nullptr;                              // all prefix / gdim arrays
-    BatchMap maps[3][5];                                // [stage][kind]
-    int map_grid[5] = {0, 0, 0, 0, 0};                  // persistent grid per kind
+    BatchMap maps[3][13];                               // [stage][kernel kind and variant]
+    int map_grid[13] = {};                              // persistent grid per map
+    int bvar[4] = {0, 0, 0, 0};                         // chosen variant per kind (viscous, xi, eta, zeta)
     // multi-block halo links: [0] between the U arrays, [1] between the Uk
     // arrays; per direction
     HaloLink* d_halo[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -109,6 +118,62 @@ static cfd_status fail(cfd_ctx* c, cfd_status s, const std::string& m)
         cudaError_t e_ = cudaGetLastError();                                                      \
         if (e_ != cudaSuccess) return fail(ctx, CFD_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
     } while (0)
+
+// ---------------------------------------------------------------------------
+// tensor-memory-accelerator descriptors (cuTensorMapEncodeTiled, fetched
+// through the runtime so that the library does not link the driver library)
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// a [fields][nz][ny][nx] (rank 4) or [nz][ny][nx] (rank 3) tensor, box of
+// 32 x 1 x 1 (x nbox fields)
+static bool encode_rows(CUtensorMap* m, CUtensorMapDataType type, size_t esize, const void* ptr, const Geo& g,
+                        int nfields, int nbox)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || !ptr) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)nfields};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * esize, (cuuint64_t)g.nx * g.ny * esize,
+                                   (cuuint64_t)g.N * esize};
+    const cuuint32_t box[4] = {32, 1, 1, (cuuint32_t)nbox};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const cuuint32_t rank = nfields > 0 ? 4 : 3;
+    return fn(m, type, rank, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// descriptors of the rows the TMA-staged walking sweep fetches; false when the
+// grid does not meet the copy rules (rows of 32 nodes, 16-byte strides)
+static bool make_row_maps(const SweepArgs& A, TmaRowMaps* m)
+{
+    const Geo& g = A.g;
+    if (g.nx % 32 != 0) return false;
+    if (!encode_rows(&m->p4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A.P, g, 7, 4)) return false;
+    if (!encode_rows(&m->p1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A.P, g, 7, 1)) return false;
+    if (A.Fv && !encode_rows(&m->fv, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A.Fv, g, 12, 4)) return false;
+    if (A.cls && !encode_rows(&m->cls, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, A.cls, g, 0, 1)) return false;
+    return true;
+}
 
 static int grid_for(long long n, int block)
 {
@@ -443,11 +508,15 @@ static cfd_status launch_sweep_dir(cfd_ctx* ctx, SweepArgs& A, int kind, int par
         const long long nseg = (hi - lo + param - 1) / param;
         const long long warps = (long long)((g.nx + 31) / 32) * nother * nseg;
         k_sweep_s<R, DIR, EP><<<(unsigned)((warps + 3) / 4), 128, stream_smem_bytes<R>(), ctx->stream>>>(A);
-    } else if (kind == 2) {
+    } else if (kind == 2 || kind == 3) {
         const int seg = param > 0 ? param : std::max(1, hi - lo);
         A.seg_len = seg;
         dim3 grid((g.nx + 31) / 32, nother, (hi - lo + seg - 1) / seg);
-        k_sweep_w<R, DIR, EP><<<grid, 256, walk_smem_bytes<R>(), ctx->stream>>>(A);
+        TmaRowMaps maps;
+        if (kind == 3 && sizeof(R) == 4 && make_row_maps(A, &maps))
+            k_sweep_wt<DIR, EP><<<grid, 256, walk_tma_smem_bytes(), ctx->stream>>>(A, maps);
+        else
+            k_sweep_w<R, DIR, EP><<<grid, 256, walk_smem_bytes<R>(), ctx->stream>>>(A);
     } else {
         dim3 grid((g.nx + 31) / 32, nother, (hi - lo + param - 1) / param);
         if (param == 16)
@@ -533,6 +602,12 @@ static cudaError_t set_sweep_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep_w<R, DIR, EP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess && sizeof(R) == 4)
+        e = cudaFuncSetAttribute(k_sweep_wt<DIR, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)walk_tma_smem_bytes());
+    if (e == cudaSuccess && sizeof(R) == 4)
+        e = cudaFuncSetAttribute(k_sweep_wt<DIR, EP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
@@ -578,7 +653,15 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
     if (!ctx->forced && (mixed || ctx->prm.scheme == CFD_HYBRID)) {
         if (ctx->prm.sensor == CFD_SENSOR_MLP) {
             if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
-            dim3 grid((g.nx + 127) / 128, g.ny, g.nz);
+            // persistent: the SMs filled to the kernel's occupancy, each CTA
+            // stages the weights once and walks 128-node row tiles
+            const long long tiles = (long long)((g.nx + 127) / 128) * g.ny * g.nz;
+            static int per_sm[2] = {0, 0};
+            int& ps = per_sm[sizeof(R) == 4];
+            if (!ps) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp<R>, 128, 0);
+            int sms = kSMs;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
+            const int grid = (int)std::max(1LL, std::min(tiles, (long long)std::max(1, ps) * sms));
             k_sensor_mlp<R><<<grid, 128, 0, ctx->stream>>>(A, ctx->mlp);
         } else if (mixed) {
             k_sensor32<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
@@ -610,23 +693,137 @@ static cfd_status run_stage(cfd_ctx* ctx, const double* Uin, const double* Un, d
 // Results are identical bit for bit across variants; only speed differs.
 // Tuned choices are cached per process by precision, grid and scheme.
 // ---------------------------------------------------------------------------
+// Tuned choices are cached per process and, unless CFD_GB300_TUNE_CACHE is
+// "off", in a text file (CFD_GB300_TUNE_CACHE, else
+// $XDG_CACHE_HOME/paper_2209_15333_gb300/autotune.txt or
+// ~/.cache/paper_2209_15333_gb300/autotune.txt), one line per entry:
+//   <library build>|<GPU name>|<SMs>|<problem key>=<choice>,<choice>,...
+// An entry is used only by the same library build on the same kind of GPU.
 namespace {
-struct TuneKey {
-    int prec, nx, ny, nz, per0, per1, per2, scheme, viscous;
-    bool operator==(const TuneKey& o) const
-    {
-        return prec == o.prec && nx == o.nx && ny == o.ny && nz == o.nz && per0 == o.per0 && per1 == o.per1 &&
-               per2 == o.per2 && scheme == o.scheme && viscous == o.viscous;
-    }
-};
 std::mutex g_tune_mu;
-std::vector<std::pair<TuneKey, std::vector<int>>> g_tune_cache;
+bool g_tune_loaded = false;
+std::vector<std::pair<std::string, std::vector<int>>> g_tune_cache;
 }  // namespace
 
-static TuneKey tune_key(const cfd_ctx* ctx)
+static std::string tune_file()
 {
-    return {ctx->prm.precision, ctx->g.nx, ctx->g.ny, ctx->g.nz, ctx->g.per[0], ctx->g.per[1], ctx->g.per[2],
-            ctx->prm.scheme, ctx->ph.viscous};
+    const char* env = std::getenv("CFD_GB300_TUNE_CACHE");
+    if (env && *env) return std::strcmp(env, "off") == 0 ? std::string() : std::string(env);
+    std::string dir;
+    if (const char* x = std::getenv("XDG_CACHE_HOME")) dir = x;
+    else if (const char* h = std::getenv("HOME")) dir = std::string(h) + "/.cache";
+    else return std::string();
+    mkdir(dir.c_str(), 0755);
+    dir += "/paper_2209_15333_gb300";
+    mkdir(dir.c_str(), 0755);
+    return dir + "/autotune.txt";
+}
+
+// "<build>|<GPU name>|<SMs>|" of the current device
+static std::string tune_prefix(int dev)
+{
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return std::string();
+    }
+    return std::string(__DATE__ " " __TIME__) + "|" + prop.name + "|" + std::to_string(prop.multiProcessorCount) + "|";
+}
+
+// caller holds g_tune_mu
+static void tune_load_file()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const std::string path = tune_file();
+    if (path.empty()) return;
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string ln(line);
+        while (!ln.empty() && (ln.back() == '\n' || ln.back() == '\r')) ln.pop_back();
+        const size_t eq = ln.rfind('=');
+        if (eq == std::string::npos) continue;
+        std::vector<int> vals;
+        size_t pos = eq + 1;
+        bool ok = true;
+        while (pos <= ln.size() && ok) {
+            const size_t c = ln.find(',', pos);
+            const std::string tok = ln.substr(pos, c == std::string::npos ? std::string::npos : c - pos);
+            char* endp = nullptr;
+            const long v = std::strtol(tok.c_str(), &endp, 10);
+            ok = !tok.empty() && endp && *endp == '\0';
+            vals.push_back((int)v);
+            if (c == std::string::npos) break;
+            pos = c + 1;
+        }
+        if (ok) g_tune_cache.push_back({ln.substr(0, eq), vals});
+    }
+    std::fclose(f);
+}
+
+static bool tune_lookup(const std::string& key, size_t nvals, std::vector<int>* out)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_file();
+    for (auto it = g_tune_cache.rbegin(); it != g_tune_cache.rend(); ++it)
+        if (it->first == key && it->second.size() == nvals) {
+            *out = it->second;
+            return true;
+        }
+    return false;
+}
+
+static void tune_store(const std::string& key, const std::vector<int>& vals)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.push_back({key, vals});
+    const std::string path = tune_file();
+    if (path.empty()) return;
+    std::string line = key + "=";
+    for (size_t i = 0; i < vals.size(); ++i) line += (i ? "," : "") + std::to_string(vals[i]);
+    line += "\n";
+    if (FILE* f = std::fopen(path.c_str(), "a")) {
+        std::fputs(line.c_str(), f);
+        std::fclose(f);
+    }
+}
+
+static std::string tune_key(const cfd_ctx* ctx)
+{
+    const Geo& g = ctx->g;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "single %d %d %d %d %d%d%d %d%d%d%d%d%d %d %d %d %d", ctx->prm.precision, g.nx,
+                  g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.bc_lo[0], g.bc_lo[1], g.bc_lo[2], g.bc_hi[0],
+                  g.bc_hi[1], g.bc_hi[2], ctx->prm.scheme, ctx->ph.viscous, ctx->ph.charrec, g.mlayout);
+    return tune_prefix(ctx->dev) + buf;
+}
+
+static std::string batch_tune_key(const cfd_ctx* ctx)
+{
+    unsigned long long h = 1469598103934665603ull;  // FNV-1a over the block grids
+    for (const cfd_ctx* sb : ctx->sub) {
+        const int v[9] = {sb->g.nx, sb->g.ny, sb->g.nz, sb->g.bc_lo[0], sb->g.bc_lo[1], sb->g.bc_lo[2],
+                          sb->g.bc_hi[0], sb->g.bc_hi[1], sb->g.bc_hi[2]};
+        for (int x : v) {
+            h ^= (unsigned long long)(unsigned)x;
+            h *= 1099511628211ull;
+        }
+    }
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "batch %d %d %d %d %llx", ctx->prm.precision, (int)ctx->sub.size(),
+                  ctx->prm.scheme, (int)ctx->ph.viscous, h);
+    return tune_prefix(ctx->dev) + buf;
+}
+
+// the TMA-staged walking sweep can run on this context (FP32 bulk, rows of 32
+// nodes, descriptors encodable)
+static bool tma_eligible(cfd_ctx* ctx)
+{
+    if (ctx->prm.precision != CFD_FP32_BULK || !ctx->sub.empty()) return false;
+    TmaRowMaps maps;
+    return make_row_maps(make_args(ctx, ctx->b.U, nullptr, nullptr, nullptr, 0.0, 1.0), &maps);
 }
 
 template <class R>
@@ -635,13 +832,14 @@ static cfd_status autotune_t(cfd_ctx* ctx)
     cfd_status st = run_stage<EP_FINAL_RHS>(ctx, ctx->b.U, nullptr, nullptr, ctx->b.Uk, 0.0, 1.0);
     if (st != CFD_OK) return st;
     SweepArgs A = make_args(ctx, ctx->b.U, nullptr, nullptr, ctx->b.Uk, 0.0, 1.0);
-    const int cands[6][2] = {{0, 128}, {0, 64}, {1, 32}, {1, 16}, {2, 0}, {2, 64}};
+    const int cands[8][2] = {{0, 128}, {0, 64}, {1, 32}, {1, 16}, {2, 0}, {2, 64}, {3, 0}, {3, 64}};
+    const int ncand = tma_eligible(ctx) ? 8 : 6;  // the TMA-staged walk is an FP32 kernel
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     for (int dir = 1; dir <= 2 && st == CFD_OK; ++dir) {
         float best = 1e30f;
-        for (int c = 0; c < 6 && st == CFD_OK; ++c) {
+        for (int c = 0; c < ncand && st == CFD_OK; ++c) {
             for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, ctx->stream);
                 if (dir == 1) st = launch_sweep_dir<R, 1, EP_ACCUM>(ctx, A, cands[c][0], cands[c][1]);
@@ -703,21 +901,20 @@ static cfd_status autotune_t(cfd_ctx* ctx)
 static cfd_status autotune(cfd_ctx* ctx)
 {
     if (ctx->tuned) return CFD_OK;
-    const TuneKey key = tune_key(ctx);
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        for (auto& kv : g_tune_cache)
-            if (kv.first == key) {
-                for (int d = 1; d <= 2; ++d) {
-                    ctx->sweep_kind[d] = kv.second[2 * d - 2];
-                    ctx->sweep_param[d] = kv.second[2 * d - 1];
-                }
-                ctx->visc_kind = kv.second[4];
-                ctx->xi_kind = kv.second[5];
-                ctx->xi_seg = kv.second[6];
-                ctx->tuned = true;
-                return CFD_OK;
-            }
+    const std::string key = tune_key(ctx);
+    std::vector<int> v;
+    if (tune_lookup(key, 7, &v) && v[0] >= 0 && v[0] <= 3 && v[2] >= 0 && v[2] <= 3 && v[4] >= 0 && v[4] <= 3 &&
+        (v[0] != 3 || tma_eligible(ctx)) && (v[2] != 3 || tma_eligible(ctx))) {
+        for (int d = 1; d <= 2; ++d) {
+            ctx->sweep_kind[d] = v[2 * d - 2];
+            ctx->sweep_param[d] = v[2 * d - 1];
+        }
+        ctx->visc_kind = v[4];
+        ctx->xi_kind = v[5];
+        ctx->xi_seg = v[6];
+        ctx->tuned = true;
+        ctx->graph_valid = false;
+        return CFD_OK;
     }
     // trial runs work on a copy of the classes: the sensor they run must not
     // change what the next real evaluation sees (the mixed recovery reads it)
@@ -728,16 +925,25 @@ static cfd_status autotune(cfd_ctx* ctx)
     if (st != CFD_OK) return st;
     ctx->tuned = true;
     ctx->graph_valid = false;
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache.push_back(
-        {key, {ctx->sweep_kind[1], ctx->sweep_param[1], ctx->sweep_kind[2], ctx->sweep_param[2], ctx->visc_kind,
-               ctx->xi_kind, ctx->xi_seg}});
+    tune_store(key, {ctx->sweep_kind[1], ctx->sweep_param[1], ctx->sweep_kind[2], ctx->sweep_param[2], ctx->visc_kind,
+                     ctx->xi_kind, ctx->xi_seg});
     return CFD_OK;
 }
+
+static void batch_variant_out(int dir, int var, int* kind, int* param);
+static int batch_variant_in(int dir, int kind, int param);
 
 extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param)
 {
     if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
+    if (!ctx->sub.empty()) {
+        const int var = dir >= 0 && dir <= 3 ? batch_variant_in(dir, kind, param) : -1;
+        if (var < 0) return fail(ctx, CFD_EINVAL, "not an ensemble kernel variant");
+        ctx->bvar[dir == 0 ? KIND_VISC : (dir == 3 ? KIND_SX : (dir == 1 ? KIND_T1 : KIND_T2))] = var;
+        ctx->tuned = true;
+        ctx->graph_valid = false;
+        return CFD_OK;
+    }
     if (dir == 0) {
         if (kind < 0 || kind > 3) return fail(ctx, CFD_EINVAL, "viscous kernel kind must be 0, 1, 2 or 3");
         ctx->visc_kind = kind;
@@ -753,10 +959,12 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
         ctx->graph_valid = false;
         return CFD_OK;
     }
-    if (dir < 1 || dir > 2 || kind < 0 || kind > 2) return fail(ctx, CFD_EINVAL, "dir must be 0, 1, 2 or 3");
+    if (dir < 1 || dir > 2 || kind < 0 || kind > 3) return fail(ctx, CFD_EINVAL, "dir must be 0, 1, 2 or 3");
     if (kind == 1 && param != 16 && param != 32) return fail(ctx, CFD_EINVAL, "tile length must be 16 or 32");
     if (kind == 0 && (param < 1 || param > 65535)) return fail(ctx, CFD_EINVAL, "segment length out of range");
-    if (kind == 2 && (param < 0 || param > 65535)) return fail(ctx, CFD_EINVAL, "segment length out of range");
+    if (kind >= 2 && (param < 0 || param > 65535)) return fail(ctx, CFD_EINVAL, "segment length out of range");
+    if (kind == 3 && !tma_eligible(ctx))
+        return fail(ctx, CFD_EUNSUPPORTED, "the TMA-staged sweep needs FP32 bulk precision and nx a multiple of 32");
     ctx->sweep_kind[dir] = kind;
     ctx->sweep_param[dir] = param;
     ctx->tuned = true;
@@ -767,6 +975,11 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
 extern "C" cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param)
 {
     if (!ctx || !kind || !param || dir < 0 || dir > 3) return fail(ctx, CFD_EINVAL, "bad argument");
+    if (!ctx->sub.empty()) {
+        batch_variant_out(dir, ctx->bvar[dir == 0 ? KIND_VISC : (dir == 3 ? KIND_SX : (dir == 1 ? KIND_T1 : KIND_T2))],
+                          kind, param);
+        return CFD_OK;
+    }
     if (dir == 3) {
         *kind = ctx->xi_kind;
         *param = ctx->xi_seg;
@@ -791,6 +1004,7 @@ static cfd_status read_err(cfd_ctx* ctx)
     if (h) {
         CU(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
         if (h & 2) return fail(ctx, CFD_ECUDA, "index out of bounds (caught by the bounds-checked build)");
+        if (h & 8) return fail(ctx, CFD_ECUDA, "a tensor-memory-accelerator copy did not complete in time");
         return fail(ctx, CFD_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) met on the device");
     }
     return CFD_OK;
@@ -913,42 +1127,62 @@ extern "C" cfd_status cfd_rhs(cfd_ctx* ctx, int block, double* dUdt, int on_devi
 // ---------------------------------------------------------------------------
 // ensembles of uneven blocks (cfd_create_batch): persistent batched launches
 // ---------------------------------------------------------------------------
-enum { MK_NODE = 0, MK_VISC = 1, MK_SX = 2, MK_T1 = 3, MK_T2 = 4, MK_COUNT = 5 };
-constexpr int kBatchBX = 64, kBatchTL = 16, kBatchTZ = 32;
+// Work-list maps, one per kernel kind and variant: MAP_NODE flat node runs;
+// viscous fluxes 2.5-D with 32 or 64 planes per item or 32 x 4 node tiles;
+// xi sweep in segments of 64 / 128 nodes or walking whole lines; eta and zeta
+// sweeps in 16- / 32-node tiles or walking 64-node segments.  The autotuner
+// picks one variant per kind on the live ensemble (all give the same bits).
+enum {
+    MAP_NODE = 0,
+    MAP_VISC = 1,  // + variant (3)
+    MAP_SX = 4,    // + variant (3)
+    MAP_T1 = 7,    // + variant (3)
+    MAP_T2 = 10,   // + variant (3)
+    MAP_COUNT = 13
+};
 
-static void batch_tiles(const Geo& g, int kind, int out[3])
+static void batch_tiles(const Geo& g, int map, int out[3])
 {
     auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
     auto span = [&](int d) {
         const int n = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
-        return g.per[d] ? n : n - 2;
+        return std::max(1, g.per[d] ? n : n - 2);
     };
-    switch (kind) {
-    case MK_NODE: out[0] = (int)((g.N + 127) / 128); out[1] = 1; out[2] = 1; break;  // flat node runs
-    case MK_VISC: out[0] = cdiv(g.nx, 32); out[1] = cdiv(g.ny, 8); out[2] = cdiv(g.nz, kBatchTZ); break;
-    case MK_SX: out[0] = cdiv(span(0), kBatchBX); out[1] = g.ny; out[2] = g.nz; break;
-    case MK_T1: out[0] = cdiv(g.nx, 32); out[1] = g.nz; out[2] = cdiv(span(1), kBatchTL); break;
-    default: out[0] = cdiv(g.nx, 32); out[1] = g.ny; out[2] = cdiv(span(2), kBatchTL); break;
+    const int kind = map == MAP_NODE ? -1 : (map - 1) / kBatchVariants, var = (map - 1) % kBatchVariants;
+    if (kind < 0) {
+        out[0] = (int)((g.N + 127) / 128); out[1] = 1; out[2] = 1;  // flat node runs
+    } else if (kind == KIND_VISC) {
+        if (var < 2) { out[0] = cdiv(g.nx, 32); out[1] = cdiv(g.ny, 8); out[2] = cdiv(g.nz, var == 0 ? 32 : 64); }
+        else { out[0] = cdiv(g.nx, 32); out[1] = cdiv(g.ny, 4); out[2] = g.nz; }
+    } else if (kind == KIND_SX) {
+        out[0] = var == 2 ? 1 : cdiv(span(0), var == 0 ? 64 : 128); out[1] = g.ny; out[2] = g.nz;
+    } else {
+        const int d = kind == KIND_T1 ? 1 : 2;
+        out[0] = cdiv(g.nx, 32); out[1] = d == 1 ? g.nz : g.ny;
+        out[2] = cdiv(span(d), var == 0 ? 16 : (var == 1 ? 32 : kBatchWS));
     }
 }
 
 template <class R>
 static cudaError_t batch_kernel_attrs()
 {
-    cudaError_t e = cudaFuncSetAttribute(kb_visc_flux25<R, kBatchTZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)visc25_smem_bytes<R>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, kBatchTL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem_bytes<R, kBatchTL>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tile_smem_bytes<R, kBatchTL>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, kBatchTL>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL>,
-                                 cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    const auto dyn = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const auto carve = cudaFuncAttributePreferredSharedMemoryCarveout;
+    const int maxs = (int)cudaSharedmemCarveoutMaxShared;
+    cudaError_t e = cudaFuncSetAttribute(kb_visc_flux25<R, 32>, dyn, (int)visc25_smem_bytes<R>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_visc_flux25<R, 64>, dyn, (int)visc25_smem_bytes<R>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 16>, dyn, (int)tile_smem_bytes<R, 16>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 16>, dyn, (int)tile_smem_bytes<R, 16>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 32>, dyn, (int)tile_smem_bytes<R, 32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, dyn, (int)tile_smem_bytes<R, 32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM>, dyn, (int)walk_smem_bytes<R>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK>, dyn, (int)walk_smem_bytes<R>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 16>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 16>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 32>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK>, carve, maxs);
     return e;
 }
 
@@ -964,17 +1198,24 @@ static int persistent_grid(K kernel, int threads, size_t smem, int items)
 }
 
 template <class R>
-static void batch_grids(cfd_ctx* ctx, const int totals[MK_COUNT])
+static void batch_grids(cfd_ctx* ctx, const int totals[MAP_COUNT])
 {
     const bool mixed = sizeof(R) == sizeof(float);
-    ctx->map_grid[MK_NODE] = mixed ? persistent_grid(kb_prim_mixed, 128, 0, totals[MK_NODE])
-                                   : persistent_grid(kb_prim<double>, 128, 0, totals[MK_NODE]);
-    ctx->map_grid[MK_VISC] = persistent_grid(kb_visc_flux25<R, kBatchTZ>, 256, visc25_smem_bytes<R>(), totals[MK_VISC]);
-    ctx->map_grid[MK_SX] = persistent_grid(kb_sweep_x<R, kBatchBX, EP_STORE>, kBatchBX, 0, totals[MK_SX]);
-    ctx->map_grid[MK_T1] = persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, kBatchTL>, 256, tile_smem_bytes<R, kBatchTL>(),
-                                           totals[MK_T1]);
-    ctx->map_grid[MK_T2] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL>, 256,
-                                           tile_smem_bytes<R, kBatchTL>(), totals[MK_T2]);
+    int* mg = ctx->map_grid;
+    mg[MAP_NODE] = mixed ? persistent_grid(kb_prim_mixed, 128, 0, totals[MAP_NODE])
+                         : persistent_grid(kb_prim<double>, 128, 0, totals[MAP_NODE]);
+    mg[MAP_VISC + 0] = persistent_grid(kb_visc_flux25<R, 32>, 256, visc25_smem_bytes<R>(), totals[MAP_VISC + 0]);
+    mg[MAP_VISC + 1] = persistent_grid(kb_visc_flux25<R, 64>, 256, visc25_smem_bytes<R>(), totals[MAP_VISC + 1]);
+    mg[MAP_VISC + 2] = persistent_grid(kb_visc_flux_tiles<R>, 128, 0, totals[MAP_VISC + 2]);
+    mg[MAP_SX + 0] = persistent_grid(kb_sweep_x<R, 64, EP_STORE>, 64, 0, totals[MAP_SX + 0]);
+    mg[MAP_SX + 1] = persistent_grid(kb_sweep_x<R, 128, EP_STORE>, 128, 0, totals[MAP_SX + 1]);
+    mg[MAP_SX + 2] = persistent_grid(kb_sweep_xw<R, EP_STORE>, XW, 0, totals[MAP_SX + 2]);
+    mg[MAP_T1 + 0] = persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, 16>, 256, tile_smem_bytes<R, 16>(), totals[MAP_T1 + 0]);
+    mg[MAP_T1 + 1] = persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, 32>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T1 + 1]);
+    mg[MAP_T1 + 2] = persistent_grid(kb_sweep_w<R, 1, EP_ACCUM>, 256, walk_smem_bytes<R>(), totals[MAP_T1 + 2]);
+    mg[MAP_T2 + 0] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 16>, 256, tile_smem_bytes<R, 16>(), totals[MAP_T2 + 0]);
+    mg[MAP_T2 + 1] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T2 + 1]);
+    mg[MAP_T2 + 2] = persistent_grid(kb_sweep_w<R, 2, EP_FINAL_RK>, 256, walk_smem_bytes<R>(), totals[MAP_T2 + 2]);
 }
 
 static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids, const double* const* metrics,
@@ -1020,6 +1261,7 @@ static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids
             double* Uout = s == 2 ? sb->b.U : sb->b.Uk;
             tbl[b] = make_args(sb, Uin, sb->b.U, Uout, nullptr, ra[s], rb[s]);
             tbl[b].dt = ctx->dt;
+            tbl[b].seg_len = kBatchWS;
         }
         CU(cudaMalloc(&ctx->d_tbl[s], nb * sizeof(SweepArgs)));
         CU(cudaMemcpyAsync(ctx->d_tbl[s], tbl.data(), nb * sizeof(SweepArgs), cudaMemcpyHostToDevice, ctx->stream));
@@ -1027,9 +1269,9 @@ static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids
     }
     // work-list maps: prefix sums of tiles and per-block tile grids per kernel kind
     const int per_kind = (nb + 1) + 3 * nb;
-    std::vector<int> h((size_t)MK_COUNT * per_kind);
-    int totals[MK_COUNT];
-    for (int k = 0; k < MK_COUNT; ++k) {
+    std::vector<int> h((size_t)MAP_COUNT * per_kind);
+    int totals[MAP_COUNT];
+    for (int k = 0; k < MAP_COUNT; ++k) {
         int* pre = h.data() + (size_t)k * per_kind;
         int* gd = pre + nb + 1;
         pre[0] = 0;
@@ -1042,7 +1284,7 @@ static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids
     CU(cudaMalloc(&ctx->d_maps, h.size() * sizeof(int)));
     CU(cudaMemcpyAsync(ctx->d_maps, h.data(), h.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     for (int s = 0; s < 3; ++s)
-        for (int k = 0; k < MK_COUNT; ++k) {
+        for (int k = 0; k < MAP_COUNT; ++k) {
             int* pre = ctx->d_maps + (size_t)k * per_kind;
             ctx->maps[s][k] = BatchMap{ctx->d_tbl[s], pre, pre + nb + 1, nb};
         }
@@ -1155,6 +1397,43 @@ extern "C" cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_gri
     return CFD_OK;
 }
 
+// one persistent launch of kernel kind `kind` (KIND_*) in variant `var` for
+// stage s of the ensemble
+template <class R>
+static cfd_status launch_batch_kind(cfd_ctx* ctx, int s, int kind, int var)
+{
+    const cudaStream_t st = ctx->stream;
+    const BatchMap* m = ctx->maps[s];
+    const int* mg = ctx->map_grid;
+    switch (kind) {
+    case KIND_VISC:
+        if (var == 0) kb_visc_flux25<R, 32><<<mg[MAP_VISC], 256, visc25_smem_bytes<R>(), st>>>(m[MAP_VISC]);
+        else if (var == 1) kb_visc_flux25<R, 64><<<mg[MAP_VISC + 1], 256, visc25_smem_bytes<R>(), st>>>(m[MAP_VISC + 1]);
+        else kb_visc_flux_tiles<R><<<mg[MAP_VISC + 2], dim3(32, 4), 0, st>>>(m[MAP_VISC + 2]);
+        break;
+    case KIND_SX:
+        if (var == 0) kb_sweep_x<R, 64, EP_STORE><<<mg[MAP_SX], 64, 0, st>>>(m[MAP_SX]);
+        else if (var == 1) kb_sweep_x<R, 128, EP_STORE><<<mg[MAP_SX + 1], 128, 0, st>>>(m[MAP_SX + 1]);
+        else kb_sweep_xw<R, EP_STORE><<<mg[MAP_SX + 2], XW, 0, st>>>(m[MAP_SX + 2]);
+        break;
+    case KIND_T1:
+        if (var == 0) kb_sweep_t<R, 1, EP_ACCUM, 16><<<mg[MAP_T1], 256, tile_smem_bytes<R, 16>(), st>>>(m[MAP_T1]);
+        else if (var == 1)
+            kb_sweep_t<R, 1, EP_ACCUM, 32><<<mg[MAP_T1 + 1], 256, tile_smem_bytes<R, 32>(), st>>>(m[MAP_T1 + 1]);
+        else kb_sweep_w<R, 1, EP_ACCUM><<<mg[MAP_T1 + 2], 256, walk_smem_bytes<R>(), st>>>(m[MAP_T1 + 2]);
+        break;
+    default:
+        if (var == 0)
+            kb_sweep_t<R, 2, EP_FINAL_RK, 16><<<mg[MAP_T2], 256, tile_smem_bytes<R, 16>(), st>>>(m[MAP_T2]);
+        else if (var == 1)
+            kb_sweep_t<R, 2, EP_FINAL_RK, 32><<<mg[MAP_T2 + 1], 256, tile_smem_bytes<R, 32>(), st>>>(m[MAP_T2 + 1]);
+        else kb_sweep_w<R, 2, EP_FINAL_RK><<<mg[MAP_T2 + 2], 256, walk_smem_bytes<R>(), st>>>(m[MAP_T2 + 2]);
+        break;
+    }
+    LAUNCH_CHECK();
+    return CFD_OK;
+}
+
 template <class R>
 static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
 {
@@ -1162,31 +1441,26 @@ static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
     const cudaStream_t st = ctx->stream;
     const BatchMap* m = ctx->maps[s];
     if (ev) cudaEventRecord(ev[0], st);
-    if (mixed) kb_prim_mixed<<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
-    else kb_prim<double><<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
+    if (mixed) kb_prim_mixed<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+    else kb_prim<double><<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
     LAUNCH_CHECK();
     if (ev) cudaEventRecord(ev[1], st);
     if (mixed || ctx->prm.scheme == CFD_HYBRID) {
-        if (mixed) kb_sensor32<<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
-        else kb_sensor<<<ctx->map_grid[MK_NODE], 128, 0, st>>>(m[MK_NODE]);
+        if (mixed) kb_sensor32<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+        else kb_sensor<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
         LAUNCH_CHECK();
     }
     if (ev) cudaEventRecord(ev[2], st);
     if (ctx->ph.viscous) {
-        kb_visc_flux25<R, kBatchTZ><<<ctx->map_grid[MK_VISC], 256, visc25_smem_bytes<R>(), st>>>(m[MK_VISC]);
-        LAUNCH_CHECK();
+        cfd_status sv = launch_batch_kind<R>(ctx, s, KIND_VISC, ctx->bvar[KIND_VISC]);
+        if (sv != CFD_OK) return sv;
     }
     if (ev) cudaEventRecord(ev[3], st);
-    kb_sweep_x<R, kBatchBX, EP_STORE><<<ctx->map_grid[MK_SX], kBatchBX, 0, st>>>(m[MK_SX]);
-    LAUNCH_CHECK();
-    if (ev) cudaEventRecord(ev[4], st);
-    kb_sweep_t<R, 1, EP_ACCUM, kBatchTL><<<ctx->map_grid[MK_T1], 256, tile_smem_bytes<R, kBatchTL>(), st>>>(m[MK_T1]);
-    LAUNCH_CHECK();
-    if (ev) cudaEventRecord(ev[5], st);
-    kb_sweep_t<R, 2, EP_FINAL_RK, kBatchTL><<<ctx->map_grid[MK_T2], 256, tile_smem_bytes<R, kBatchTL>(), st>>>(
-        m[MK_T2]);
-    LAUNCH_CHECK();
-    if (ev) cudaEventRecord(ev[6], st);
+    for (int kind = KIND_SX; kind <= KIND_T2; ++kind) {
+        cfd_status sk = launch_batch_kind<R>(ctx, s, kind, ctx->bvar[kind]);
+        if (sk != CFD_OK) return sk;
+        if (ev) cudaEventRecord(ev[3 + kind], st);
+    }
     // boundary conditions of blocks with non-periodic faces, at the stage time
     const double tfrac[3] = {1.0, 0.5, 1.0};
     for (cfd_ctx* sb : ctx->sub) {
@@ -1212,6 +1486,82 @@ static cfd_status launch_halo(cfd_ctx* ctx, int which)
         LAUNCH_CHECK();
     }
     return CFD_OK;
+}
+
+// Ensemble autotuner: times every variant of each kernel kind on the live
+// work lists of a stage-1 evaluation and keeps the fastest.  Trial runs write
+// only stage buffers; the classes the mixed recovery reads next are saved and
+// restored around them.
+template <class R>
+static cfd_status batch_autotune_t(cfd_ctx* ctx)
+{
+    for (cfd_ctx* sb : ctx->sub)
+        CU(cudaMemcpyAsync(sb->b.cls_tune, sb->b.cls, sb->g.N, cudaMemcpyDeviceToDevice, ctx->stream));
+    cfd_status st = enqueue_batch_stage<R>(ctx, 0, nullptr);
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    for (int kind = 0; kind < KIND_COUNT && st == CFD_OK; ++kind) {
+        if (kind == KIND_VISC && !ctx->ph.viscous) continue;
+        float best = 1e30f;
+        for (int var = 0; var < kBatchVariants && st == CFD_OK; ++var) {
+            for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, ctx->stream);
+                st = launch_batch_kind<R>(ctx, 0, kind, var);
+            }
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, CFD_ECUDA, "ensemble autotune timing");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == CFD_OK && ms < best) {
+                best = ms;
+                ctx->bvar[kind] = var;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (cfd_ctx* sb : ctx->sub)
+        CU(cudaMemcpyAsync(sb->b.cls, sb->b.cls_tune, sb->g.N, cudaMemcpyDeviceToDevice, ctx->stream));
+    return st;
+}
+
+static cfd_status batch_autotune(cfd_ctx* ctx)
+{
+    if (ctx->tuned) return CFD_OK;
+    const std::string key = batch_tune_key(ctx);
+    std::vector<int> v;
+    if (tune_lookup(key, KIND_COUNT, &v) && *std::min_element(v.begin(), v.end()) >= 0 &&
+        *std::max_element(v.begin(), v.end()) < kBatchVariants) {
+        for (int k = 0; k < KIND_COUNT; ++k) ctx->bvar[k] = v[k];
+        ctx->tuned = true;
+        ctx->graph_valid = false;
+        return CFD_OK;
+    }
+    cfd_status st = ctx->prm.precision == CFD_FP32_BULK ? batch_autotune_t<float>(ctx) : batch_autotune_t<double>(ctx);
+    if (st != CFD_OK) return st;
+    ctx->tuned = true;
+    ctx->graph_valid = false;
+    tune_store(key, std::vector<int>(ctx->bvar, ctx->bvar + KIND_COUNT));
+    return CFD_OK;
+}
+
+// ensemble variants in the (kind, param) vocabulary of cfd_set_sweep_variant
+static void batch_variant_out(int dir, int var, int* kind, int* param)
+{
+    static const int visc[3][2] = {{2, 32}, {1, 64}, {3, 0}};
+    static const int xi[3][2] = {{0, 64}, {0, 128}, {1, 0}};
+    static const int eta[3][2] = {{1, 16}, {1, 32}, {2, kBatchWS}};
+    const int(*t)[2] = dir == 0 ? visc : (dir == 3 ? xi : eta);
+    *kind = t[var][0];
+    *param = t[var][1];
+}
+
+static int batch_variant_in(int dir, int kind, int param)
+{
+    if (dir == 0) return kind == 2 ? 0 : (kind == 1 ? 1 : (kind == 3 ? 2 : -1));
+    if (dir == 3) return kind == 1 ? 2 : (kind == 0 && param == 64 ? 0 : (kind == 0 && param == 128 ? 1 : -1));
+    return kind == 2 ? 2 : (kind == 1 && param == 16 ? 0 : (kind == 1 && param == 32 ? 1 : -1));
 }
 
 static cfd_status enqueue_batch_step(cfd_ctx* ctx)
@@ -1300,8 +1650,8 @@ extern "C" cfd_status cfd_step(cfd_ctx* ctx, double dt, int nsteps)
     if (nsteps == 0) return CFD_OK;
     k_set_scalar<<<1, 32, 0, ctx->stream>>>(ctx->dt, dt);
     LAUNCH_CHECK();
-    if (ctx->sub.empty()) {
-        cfd_status st = autotune(ctx);
+    {
+        cfd_status st = ctx->sub.empty() ? autotune(ctx) : batch_autotune(ctx);
         if (st != CFD_OK) return st;
     }
     if (!ctx->graph_valid) {

@@ -14,6 +14,8 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda.h>  // CUtensorMap (tensor-memory-accelerator descriptors); no driver calls here
+
 #include "weno_coeffs.cuh"
 
 namespace cfdk {
@@ -411,6 +413,28 @@ struct MlpArgs {
     unsigned long long* fallbacks;  // count of nodes that fell back to the plain sensor
 };
 
+// the seven features of one field along one direction from the values at
+// line positions m-3 .. m+3 (one routine for every kernel that builds them,
+// so that they agree bit for bit)
+__device__ __forceinline__ void mlp_feature_line(const float v[7], float* o)
+{
+    const float inv = 1.0f / v[3];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) o[t] = (v[t + 1] - v[t]) * inv;
+    const float v2 = v[3] + v[3];
+    // a ratio in [-1, 1] for positive p and rho: the fast division's few
+    // units of rounding are far below the bf16 rounding of the inputs
+    o[6] = __fdividef((v[2] - v2) + v[4], (v[2] + v2) + v[4]);
+}
+
+// line position m + t (t = -3..3) with periodic wrap or clamping at the ends
+__device__ __forceinline__ int mlp_pos(int m, int t, int n, int per)
+{
+    int mm = m + t;
+    if (per) return wrapi(mm, n);
+    return mm < 0 ? 0 : (mm >= n ? n - 1 : mm);
+}
+
 template <class RT>
 __device__ __forceinline__ void mlp_features(const SweepArgs& A, int i, int j, int k, long long n, float f[MLP_IN])
 {
@@ -425,34 +449,24 @@ __device__ __forceinline__ void mlp_features(const SweepArgs& A, int i, int j, i
         const int m = pos[d];
         long long off[7];
 #pragma unroll
-        for (int t = 0; t < 7; ++t) {
-            int mm = m + t - 3;
-            if (g.per[d]) mm = wrapi(mm, nd[d]);
-            else mm = mm < 0 ? 0 : (mm >= nd[d] ? nd[d] - 1 : mm);
-            off[t] = (long long)(mm - m) * st[d];
-        }
+        for (int t = 0; t < 7; ++t) off[t] = (long long)(mlp_pos(m, t - 3, nd[d], g.per[d]) - m) * st[d];
 #pragma unroll
         for (int fld = 0; fld < 2; ++fld) {
             const RT* q = P + (fld == 0 ? 4 * N : 0) + n;
             float v[7];
 #pragma unroll
             for (int t = 0; t < 7; ++t) v[t] = (float)q[off[t]];
-            const float inv = 1.0f / v[3];
-            float* o = f + (2 * d + fld) * 7;
-#pragma unroll
-            for (int t = 0; t < 6; ++t) o[t] = (v[t + 1] - v[t]) * inv;
-            o[6] = (v[2] - 2.0f * v[3] + v[4]) / (v[2] + 2.0f * v[3] + v[4]);
+            mlp_feature_line(v, f + (2 * d + fld) * 7);
         }
     }
 }
 
+// two floats to a pair of bf16 (round to nearest even), lo in the low half
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
-    const uint32_t a = __float_as_uint(lo), b = __float_as_uint(hi);
-    // round to nearest even
-    const uint32_t ra = (a + 0x7FFFu + ((a >> 16) & 1u)) >> 16;
-    const uint32_t rb = (b + 0x7FFFu + ((b >> 16) & 1u)) >> 16;
-    return ra | (rb << 16);
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
 }
 
 __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2])
@@ -487,7 +501,8 @@ __device__ __forceinline__ int plain_class(const SweepArgs& A, int i, int j, int
 
 constexpr int MLP_ROW = 56;  // bf16 row stride of the feature tile (conflict-free fragment loads)
 
-// 128 nodes along x per CTA (4 warps x 32 rows); grid (x-chunks of 128, ny, nz)
+// Persistent: each CTA stages the weights once and then walks tiles of 128
+// consecutive x nodes of one (j, k) row (4 warps x 32 rows per tile).
 template <class RT>
 __global__ void __launch_bounds__(128) k_sensor_mlp(SweepArgs A, MlpArgs W)
 {
@@ -497,143 +512,187 @@ __global__ void __launch_bounds__(128) k_sensor_mlp(SweepArgs A, MlpArgs W)
     __shared__ __align__(16) uint16_t sw3[8 * 40];
     __shared__ float sb[32 + 32 + 8];
     __shared__ unsigned char sbad[128];
+    __shared__ float srow[2][128 + 6];   // p and rho of the x-row segment with a 3-node halo
+    __shared__ long long soff[2][7];     // element offsets of the eta / zeta positions j-3..j+3, k-3..k+3
+    __shared__ int scls[128];
     const Geo& g = A.g;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int i = blockIdx.x * 128 + t, j = blockIdx.y, k = blockIdx.z;
-    const long long n = (long long)i + (long long)g.nx * ((long long)j + (long long)g.ny * k);
-    const bool own = i < g.nx;
-    // weights and biases to shared memory
+    const long long N = g.N;
+    const RT* Pp = (const RT*)A.P + 4 * N;
+    const RT* Pr = (const RT*)A.P;
+    // weights and biases to shared memory, once per CTA
     for (int e = t; e < 32 * MLP_KP; e += 128) sw1[(e / MLP_KP) * MLP_ROW + e % MLP_KP] = W.w1[e];
     for (int e = t; e < 32 * 32; e += 128) sw2[(e / 32) * 40 + e % 32] = W.w2[e];
     for (int e = t; e < 8 * 32; e += 128) sw3[(e / 32) * 40 + e % 32] = W.w3[e];
     for (int e = t; e < 72; e += 128) sb[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
-    // features of this thread's node
-    {
-        float f[MLP_IN];
-        bool bad = !own;
-        if (own) {
-            mlp_features<RT>(A, i, j, k, n, f);
-#pragma unroll
-            for (int e = 0; e < MLP_IN; ++e) bad |= !isfinite(f[e]);
+    const int nxc = (g.nx + 127) / 128;
+    const long long ntiles = (long long)nxc * g.ny * g.nz;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i0 = (int)(tile % nxc) * 128;
+        const long long rest = tile / nxc;
+        const int j = (int)(rest % g.ny), k = (int)(rest / g.ny);
+        const int i = i0 + t;
+        const long long rowb = (long long)g.nx * ((long long)j + (long long)g.ny * k);
+        const long long n = (long long)i + rowb;
+        const bool own = i < g.nx;
+        __syncthreads();  // the previous tile's shared arrays are consumed
+        // the row segment (x positions i0-3 .. i0+130, wrapped or clamped) and
+        // the offsets of the other two directions, which the tile shares
+        for (int e = t; e < 128 + 6; e += 128) {
+            const int xx = mlp_pos(i0 - 3, e, g.nx, g.per[0]);
+            srow[0][e] = (float)Pp[rowb + xx];
+            srow[1][e] = (float)Pr[rowb + xx];
         }
-        uint32_t* row = reinterpret_cast<uint32_t*>(sx + t * MLP_ROW);
-#pragma unroll
-        for (int e = 0; e < MLP_KP; e += 2) {
-            const float a = (!bad && e < MLP_IN) ? f[e] : 0.0f;
-            const float b = (!bad && e + 1 < MLP_IN) ? f[e + 1] : 0.0f;
-            row[e / 2] = pack_bf16x2(a, b);
+        if (t < 14) {
+            const int d = 1 + t / 7, tt = t % 7 - 3;
+            const int m = d == 1 ? j : k;
+            const long long st = d == 1 ? (long long)g.nx : (long long)g.nx * g.ny;
+            soff[d - 1][tt + 3] = (long long)(mlp_pos(m, tt, d == 1 ? g.ny : g.nz, g.per[d]) - m) * st;
         }
-        sbad[t] = bad;
-    }
-    __syncthreads();
-    const int gid = lane >> 2, tig = lane & 3;
-    int cls_row[2][2];  // [m-tile][row half] class (-1: use the plain sensor)
+        __syncthreads();
+        // features of this thread's node: xi from the staged row, eta and zeta
+        // from coalesced loads at the shared offsets
+        {
+            float f[MLP_IN];
+            bool bad = !own;
+            if (own) {
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = warp * 32 + mt * 16 + gid;  // rows r0 and r0 + 8
-        // layer 1: [16 x 48] x [48 x 32]
-        float h1[4][4];
+                for (int fld = 0; fld < 2; ++fld) {
+                    float v[7];
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+                    for (int tt = 0; tt < 7; ++tt) v[tt] = srow[fld][t + tt];
+                    mlp_feature_line(v, f + fld * 7);
+                    const RT* q = (fld == 0 ? Pp : Pr) + n;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) h1[nt][e] = 0.0f;
+                    for (int d = 1; d < 3; ++d) {
 #pragma unroll
-        for (int ks = 0; ks < 3; ++ks) {
-            uint32_t a[4];
-            const int c = ks * 16 + tig * 2;
-            a[0] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c);
-            a[1] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c);
-            a[2] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c + 8);
-            a[3] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c + 8);
+                        for (int tt = 0; tt < 7; ++tt) v[tt] = (float)q[soff[d - 1][tt]];
+                        mlp_feature_line(v, f + (2 * d + fld) * 7);
+                    }
+                }
+                // one test for all 42: x * 0 is 0 for finite x and NaN otherwise
+                float z = 0.0f;
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                uint32_t b[2];
-                const int nn = nt * 8 + gid;
-                b[0] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c);
-                b[1] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c + 8);
-                mma_bf16_16816(h1[nt], a, b);
+                for (int e = 0; e < MLP_IN; ++e) z = fmaf(f[e], 0.0f, z);
+                bad = !(z == 0.0f);
             }
-        }
-        // bias + ReLU, and the accumulator layout becomes the next A operand
-        uint32_t a2[2][4];
+            uint32_t* row = reinterpret_cast<uint32_t*>(sx + t * MLP_ROW);
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const float bb0 = sb[nt * 8 + tig * 2], bb1 = sb[nt * 8 + tig * 2 + 1];
-            const uint32_t lo = pack_bf16x2(fmaxf(h1[nt][0] + bb0, 0.0f), fmaxf(h1[nt][1] + bb1, 0.0f));
-            const uint32_t hi = pack_bf16x2(fmaxf(h1[nt][2] + bb0, 0.0f), fmaxf(h1[nt][3] + bb1, 0.0f));
-            a2[nt >> 1][(nt & 1) * 2 + 0] = lo;
-            a2[nt >> 1][(nt & 1) * 2 + 1] = hi;
-        }
-        // layer 2: [16 x 32] x [32 x 32]
-        float h2[4][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) h2[nt][e] = 0.0f;
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            const int c = ks * 16 + tig * 2;
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                uint32_t b[2];
-                const int nn = nt * 8 + gid;
-                b[0] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c);
-                b[1] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c + 8);
-                mma_bf16_16816(h2[nt], a2[ks], b);
+            for (int e = 0; e < MLP_KP; e += 2) {
+                const float a = (!bad && e < MLP_IN) ? f[e] : 0.0f;
+                const float b = (!bad && e + 1 < MLP_IN) ? f[e + 1] : 0.0f;
+                row[e / 2] = pack_bf16x2(a, b);
             }
+            sbad[t] = bad;
         }
-        uint32_t a3[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const float bb0 = sb[32 + nt * 8 + tig * 2], bb1 = sb[32 + nt * 8 + tig * 2 + 1];
-            const uint32_t lo = pack_bf16x2(fmaxf(h2[nt][0] + bb0, 0.0f), fmaxf(h2[nt][1] + bb1, 0.0f));
-            const uint32_t hi = pack_bf16x2(fmaxf(h2[nt][2] + bb0, 0.0f), fmaxf(h2[nt][3] + bb1, 0.0f));
-            a3[nt >> 1][(nt & 1) * 2 + 0] = lo;
-            a3[nt >> 1][(nt & 1) * 2 + 1] = hi;
-        }
-        // layer 3: [16 x 32] x [32 x 8] (3 logits used)
-        float lg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            const int c = ks * 16 + tig * 2;
-            uint32_t b[2];
-            b[0] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c);
-            b[1] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c + 8);
-            mma_bf16_16816(lg, a3[ks], b);
-        }
-        // logits of row r0 (lg[0..1]) and r0+8 (lg[2..3]) sit in columns 2 tig, 2 tig + 1:
-        // gather columns 0, 1, 2 at tig == 0
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const float c0 = __shfl_sync(0xffffffffu, lg[2 * half], lane & ~3);
-            const float c1 = __shfl_sync(0xffffffffu, lg[2 * half + 1], lane & ~3);
-            const float c2 = __shfl_sync(0xffffffffu, lg[2 * half], (lane & ~3) + 1);
-            const float l0 = c0 + sb[64], l1 = c1 + sb[65], l2 = c2 + sb[66];
-            const float mx = fmaxf(l0, fmaxf(l1, l2));
-            const float z = __expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx);
-            const int arg = l0 >= l1 ? (l0 >= l2 ? 0 : 2) : (l1 >= l2 ? 1 : 2);
-            cls_row[mt][half] = (1.0f / z >= W.conf_min && isfinite(z)) ? arg : -1;
-        }
-    }
-    __syncthreads();
-    // one writer per row: lane with tig == 0 owns rows r0 and r0 + 8 of each m-tile
-    __shared__ int scls[128];
-    if (tig == 0) {
+        __syncthreads();
+        const int gid = lane >> 2, tig = lane & 3;
+        int cls_row[2][2];  // [m-tile][row half] class (-1: use the plain sensor)
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = warp * 32 + mt * 16 + gid;
-            scls[r0] = cls_row[mt][0];
-            scls[r0 + 8] = cls_row[mt][1];
+            const int r0 = warp * 32 + mt * 16 + gid;  // rows r0 and r0 + 8
+            // layer 1: [16 x 48] x [48 x 32]
+            float h1[4][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) h1[nt][e] = 0.0f;
+#pragma unroll
+            for (int ks = 0; ks < 3; ++ks) {
+                uint32_t a[4];
+                const int c = ks * 16 + tig * 2;
+                a[0] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c);
+                a[1] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c);
+                a[2] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c + 8);
+                a[3] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c + 8);
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    uint32_t b[2];
+                    const int nn = nt * 8 + gid;
+                    b[0] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c);
+                    b[1] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c + 8);
+                    mma_bf16_16816(h1[nt], a, b);
+                }
+            }
+            // bias + ReLU, and the accumulator layout becomes the next A operand
+            uint32_t a2[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const float bb0 = sb[nt * 8 + tig * 2], bb1 = sb[nt * 8 + tig * 2 + 1];
+                const uint32_t lo = pack_bf16x2(fmaxf(h1[nt][0] + bb0, 0.0f), fmaxf(h1[nt][1] + bb1, 0.0f));
+                const uint32_t hi = pack_bf16x2(fmaxf(h1[nt][2] + bb0, 0.0f), fmaxf(h1[nt][3] + bb1, 0.0f));
+                a2[nt >> 1][(nt & 1) * 2 + 0] = lo;
+                a2[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            }
+            // layer 2: [16 x 32] x [32 x 32]
+            float h2[4][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) h2[nt][e] = 0.0f;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int c = ks * 16 + tig * 2;
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    uint32_t b[2];
+                    const int nn = nt * 8 + gid;
+                    b[0] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c);
+                    b[1] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c + 8);
+                    mma_bf16_16816(h2[nt], a2[ks], b);
+                }
+            }
+            uint32_t a3[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const float bb0 = sb[32 + nt * 8 + tig * 2], bb1 = sb[32 + nt * 8 + tig * 2 + 1];
+                const uint32_t lo = pack_bf16x2(fmaxf(h2[nt][0] + bb0, 0.0f), fmaxf(h2[nt][1] + bb1, 0.0f));
+                const uint32_t hi = pack_bf16x2(fmaxf(h2[nt][2] + bb0, 0.0f), fmaxf(h2[nt][3] + bb1, 0.0f));
+                a3[nt >> 1][(nt & 1) * 2 + 0] = lo;
+                a3[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            }
+            // layer 3: [16 x 32] x [32 x 8] (3 logits used)
+            float lg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                const int c = ks * 16 + tig * 2;
+                uint32_t b[2];
+                b[0] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c);
+                b[1] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c + 8);
+                mma_bf16_16816(lg, a3[ks], b);
+            }
+            // logits of row r0 (lg[0..1]) and r0+8 (lg[2..3]) sit in columns 2 tig, 2 tig + 1:
+            // gather columns 0, 1, 2 at tig == 0
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const float c0 = __shfl_sync(0xffffffffu, lg[2 * half], lane & ~3);
+                const float c1 = __shfl_sync(0xffffffffu, lg[2 * half + 1], lane & ~3);
+                const float c2 = __shfl_sync(0xffffffffu, lg[2 * half], (lane & ~3) + 1);
+                const float l0 = c0 + sb[64], l1 = c1 + sb[65], l2 = c2 + sb[66];
+                const float mx = fmaxf(l0, fmaxf(l1, l2));
+                const float z = __expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx);
+                const int arg = l0 >= l1 ? (l0 >= l2 ? 0 : 2) : (l1 >= l2 ? 1 : 2);
+                cls_row[mt][half] = (1.0f / z >= W.conf_min && isfinite(z)) ? arg : -1;
+            }
         }
-    }
-    __syncthreads();
-    if (own) {
-        int c = scls[t];
-        if (c < 0 || sbad[t]) {
-            c = plain_class<RT>(A, i, j, k, n);
-            if (W.fallbacks) atomicAdd(W.fallbacks, 1ull);
+        // one writer per row: lane with tig == 0 owns rows r0 and r0 + 8 of each m-tile
+        if (tig == 0) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r0 = warp * 32 + mt * 16 + gid;
+                scls[r0] = cls_row[mt][0];
+                scls[r0 + 8] = cls_row[mt][1];
+            }
         }
-        A.cls_io[n] = (uint8_t)c;
+        __syncthreads();
+        if (own) {
+            int c = scls[t];
+            if (c < 0 || sbad[t]) {
+                c = plain_class<RT>(A, i, j, k, n);
+                if (W.fallbacks) atomicAdd(W.fallbacks, 1ull);
+            }
+            A.cls_io[n] = (uint8_t)c;
+        }
     }
 }
 
@@ -2135,6 +2194,325 @@ constexpr size_t stream_smem_bytes()
 }
 
 // ---------------------------------------------------------------------------
+// TMA-staged walking eta / zeta sweep (FP32-bulk form).  The same walk and the
+// same arithmetic as sweep_w_body, but the rows a chunk splits are fetched by
+// the tensor-memory accelerator (cp.async.bulk.tensor, one 32-node row of a
+// field per copy) into a ring of NBUF staging buffers, NBUF - 1 row groups
+// ahead of the warps that split them; completion is signalled on one mbarrier
+// per buffer.  The node operands of the epilogue (R; U and U^n in the RK
+// variant) are loaded into registers one chunk ahead.  Every wait is bounded:
+// a wait that gives up sets bit 3 of the error word, the block waits (again
+// bounded) for the copies it issued and returns.
+// ---------------------------------------------------------------------------
+struct TmaRowMaps {
+    CUtensorMap p4;   // P as [7][nz][ny][nx] float, box 32 x 1 x 1 x 4 (rho, u, v, w)
+    CUtensorMap p1;   // the same tensor, box 32 x 1 x 1 x 1 (c)
+    CUtensorMap fv;   // Fv as [12][nz][ny][nx] float, box 32 x 1 x 1 x 4
+    CUtensorMap cls;  // classes as [nz][ny][nx] uint8, box 32 x 1 x 1
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit)
+{
+    for (unsigned it = 0; it < limit; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// staging layout of one row (bytes): P rho,u,v,w [4][32] at 0, c [32] at
+// 512, Fv [4][32] at 640, classes [32] at 1152; 1280 per row, 8 rows a group
+constexpr int TW_NBUF = 4, TW_ROW = 1280, TW_GROUP = 8 * TW_ROW;
+constexpr unsigned TW_WAIT_LIMIT = 1u << 22;
+
+constexpr size_t walk_tma_smem_bytes()
+{
+    return (size_t)TW_NBUF * TW_GROUP + walk_smem_bytes<float>() + 64;  // + mbarriers and the abort flag
+}
+
+template <int DIR, int EP>
+__device__ __forceinline__ void sweep_wt_body(const SweepArgs& A, const TmaRowMaps& maps, uint3 vb)
+{
+    using R = float;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* stage = smem_raw;                                   // [NBUF][8][1280]
+    R* sf = reinterpret_cast<R*>(smem_raw + TW_NBUF * TW_GROUP);        // rings as in sweep_w_body
+    R* ss = sf + WS_RING * 10 * 32;
+    R* sv = ss + WS_RING * 32;
+    R* sh = sv + WV_RING * 4 * 32;
+    uint8_t* sc = reinterpret_cast<uint8_t*>(sh + WS_RING * 5 * 32);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sc + WS_RING * 32);   // [NBUF]
+    int& s_abort = *reinterpret_cast<int*>(bars + TW_NBUF);
+    const Geo& g = A.g;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nx = g.nx;
+    const int n = DIR == 1 ? g.ny : g.nz;
+    const long long stride = DIR == 1 ? (long long)nx : (long long)nx * g.ny;
+    const int per = g.per[DIR];
+    const int lo = per ? 0 : 1, hi = per ? n : n - 1;
+    const int x0 = vb.x * 32;
+    const int i = x0 + lane;
+    const bool lane_ok = i < nx;
+    const int o = vb.y;
+    const int S = A.seg_len;
+    const int ms = lo + (int)vb.z * S;
+    if (ms >= hi) return;
+    const int me = min(ms + S, hi);
+    const long long base = DIR == 1 ? (long long)i + (long long)nx * g.ny * o : (long long)i + (long long)nx * o;
+    const R eps = pk<R>(A.ph.eps, A.ph.epsf);
+    // row groups: group gi holds walk positions q = 8 gi .. 8 gi + 7 (line
+    // positions ms - 4 + q); positions beyond me + 3 are never needed
+    const int ngroups = (me + 3 - (ms - 4)) / 8 + 1;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < TW_NBUF; ++b) mbar_init(&bars[b], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto row_valid = [&](int m) { return (per || (m >= 0 && m < n)) && m <= me + 3; };
+    // warp 0 issues the copies of group gi into buffer gi % NBUF: lane 4 r + t
+    // copies piece t of row r (t: 0 rho..w, 1 c, 2 viscous fluxes, 3 classes)
+    auto issue = [&](int gi) {
+        if (gi >= ngroups) return;
+        uint64_t* bar = &bars[gi % TW_NBUF];
+        unsigned bytes = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            if (row_valid(ms - 4 + 8 * gi + r)) bytes += 640u + (A.Fv ? 512u : 0u) + (A.cls ? 32u : 0u);
+        if (lane == 0) {
+            if (bytes) mbar_arrive_expect_tx(bar, bytes);
+            else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+        }
+        __syncwarp();
+        const int r = lane >> 2, t = lane & 3;
+        const int m = ms - 4 + 8 * gi + r;
+        if (!row_valid(m)) return;
+        const int mm = per ? wrapi(m, n) : m;
+        const int cy = DIR == 1 ? mm : o, cz = DIR == 1 ? o : mm;
+        unsigned char* dst = stage + (size_t)(gi % TW_NBUF) * TW_GROUP + (size_t)r * TW_ROW;
+        if (t == 0) tma_load_4d(dst, &maps.p4, x0, cy, cz, 0, bar);
+        else if (t == 1) tma_load_4d(dst + 512, &maps.p1, x0, cy, cz, 6, bar);
+        else if (t == 2) { if (A.Fv) tma_load_4d(dst + 640, &maps.fv, x0, cy, cz, 4 * DIR, bar); }
+        else if (A.cls) tma_load_3d(dst + 1152, &maps.cls, x0, cy, cz, bar);
+    };
+    // wait for group gi; on a timeout every thread learns it at the next barrier
+    auto wait_group = [&](int gi) {
+        if (!mbar_wait_bounded(&bars[gi % TW_NBUF], (unsigned)((gi / TW_NBUF) & 1), TW_WAIT_LIMIT)) {
+            atomicOr(A.err, 8);
+            s_abort = 1;
+        }
+    };
+    // drain: wait (bounded) for every group issued and not yet consumed
+    auto drain = [&](int first_unconsumed, int last_issued) {
+        if (threadIdx.x == 0)
+            for (int gi = first_unconsumed; gi <= last_issued && gi < ngroups; ++gi)
+                mbar_wait_bounded(&bars[gi % TW_NBUF], (unsigned)((gi / TW_NBUF) & 1), TW_WAIT_LIMIT);
+        __syncthreads();
+    };
+    // split the row of group gi that this warp owns into the rings
+    auto split_row = [&](int gi) {
+        const int m = ms - 4 + 8 * gi + w;
+        const int q = 8 * gi + w;
+        const unsigned char* src = stage + (size_t)(gi % TW_NBUF) * TW_GROUP + (size_t)w * TW_ROW;
+        const R* sp = reinterpret_cast<const R*>(src);
+        R fp[5], fm[5], sg = (R)0, fvv[4] = {(R)0, (R)0, (R)0, (R)0};
+        uint8_t c = 0;
+        bool ok = lane_ok && row_valid(m);
+        const int mm = per ? wrapi(m, n) : m;
+        if (ok) ok = in_range(A.err, base + (long long)mm * stride, g.N);
+        if (ok) {
+            const long long nn = base + (long long)mm * stride;
+            const long long mi = midx(g, i, DIR == 1 ? mm : o, nn);
+            NodePrim<R> pr{sp[lane], sp[32 + lane], sp[64 + lane], sp[96 + lane], sp[128 + lane]};
+            sg = split_prim<R>(A, DIR, pr, mi, fp, fm);
+            if (A.cls) c = src[1152 + lane];
+            if (A.Fv) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) fvv[e] = sp[160 + 32 * e + lane];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) fp[e] = fm[e] = (R)0;
+        }
+        R* f = sf + (size_t)(q & (WS_RING - 1)) * 10 * 32 + lane;
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            f[e * 32] = fp[e];
+            f[(5 + e) * 32] = fm[e];
+        }
+        ss[(q & (WS_RING - 1)) * 32 + lane] = sg;
+        sc[(q & (WS_RING - 1)) * 32 + lane] = c;
+        if (A.Fv) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) sv[((q & (WV_RING - 1)) * 4 + e) * 32 + lane] = fvv[e];
+        }
+    };
+    auto face = [&](int jf) {
+        const int q0 = jf - 3 - (ms - 4);
+        int cm = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) cm = max(cm, (int)sc[((q0 + b) & (WS_RING - 1)) * 32 + lane]);
+        int mp, mm;
+        const int use = face_use(A.ph, per, n, jf, cm, &mp, &mm);
+        const R isc = use && lane_ok ? face_iscale<R>(ss[((q0 + 3) & (WS_RING - 1)) * 32 + lane],
+                                                      ss[((q0 + 4) & (WS_RING - 1)) * 32 + lane])
+                                     : (R)0;
+        R* out = sh + (size_t)((jf - ms + 1) & (WS_RING - 1)) * 5 * 32 + lane;
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            R p8[8], m8[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const R* f = sf + (size_t)((q0 + b) & (WS_RING - 1)) * 10 * 32 + lane;
+                p8[b] = f[e * 32];
+                m8[b] = f[(5 + e) * 32];
+            }
+            out[e * 32] = face_flux<R>(use, p8, m8, eps, isc, mp, mm);
+        }
+    };
+    // epilogue operands of node m (R; U, U^n for the RK variant), in registers
+    struct NodeOps {
+        R r[5];
+        double u[5], un[5];
+    };
+    auto load_ops = [&](int m, NodeOps& op) {
+        if (!(m < me && lane_ok)) return;
+        const int mm = per ? wrapi(m, n) : m;
+        const long long nn = base + (long long)mm * stride;
+        if (!in_range(A.err, nn, g.N)) return;
+        const long long N = g.N;
+        if (EP == EP_ACCUM || EP == EP_FINAL_RK || EP == EP_FINAL_RHS) {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) op.r[e] = ((const R*)A.R)[e * N + nn];
+        }
+        if (EP == EP_FINAL_RK) {
+            const bool bnd = is_bnd(g, i, DIR == 1 ? mm : o, DIR == 1 ? o : mm);
+            if (!bnd) {
+#pragma unroll
+                for (int e = 0; e < 5; ++e) {
+                    op.u[e] = A.U[e * N + nn];
+                    op.un[e] = A.rk_a != 0.0 ? A.Un[e * N + nn] : 0.0;
+                }
+            }
+        }
+    };
+    // the epilogue of sweep_w_body on preloaded operands
+    auto finish = [&](int m, const R val[5], const NodeOps& op) {
+        const int mm = per ? wrapi(m, n) : m;
+        const long long nn = base + (long long)mm * stride;
+        if (!in_range(A.err, nn, g.N)) return;
+        const long long N = g.N;
+        const int jj = DIR == 1 ? mm : o, kk = DIR == 1 ? o : mm;
+        R* Racc = (R*)A.R;
+        if (EP == EP_ACCUM) {
+#pragma unroll
+            for (int e = 0; e < 5; ++e) Racc[e * N + nn] = op.r[e] + val[e];
+        } else {
+            const bool bnd = is_bnd(g, i, jj, kk);
+            const double J = metv(g, M_J, midx(g, i, jj, nn));
+            if (EP == EP_FINAL_RHS) {
+#pragma unroll
+                for (int e = 0; e < 5; ++e) A.Lout[e * N + nn] = bnd ? 0.0 : J * (double)(op.r[e] + val[e]);
+            } else {
+                if (bnd) return;
+                const double dt = *A.dt;
+#pragma unroll
+                for (int e = 0; e < 5; ++e) {
+                    const double L = J * (double)(op.r[e] + val[e]);
+                    A.Uout[e * N + nn] = mad(A.rk_a, op.un[e], A.rk_b * mad(dt, L, op.u[e]));
+                }
+            }
+        }
+    };
+
+    // prologue: groups 0 .. NBUF-1 in flight, group 0 split, face ms - 1/2
+    if (w == 0)
+        for (int gi = 0; gi < TW_NBUF; ++gi) issue(gi);
+    NodeOps ops;
+    load_ops(ms + w, ops);
+    wait_group(0);
+    __syncthreads();
+    if (s_abort) { drain(0, TW_NBUF - 1); return; }
+    split_row(0);
+    __syncthreads();
+    if (w == 0) issue(TW_NBUF);  // buffer 0 is free again
+    if (w == 0) face(ms - 1);
+    int gi = 1;
+    for (int m0 = ms; m0 < me; m0 += 8, ++gi) {
+        NodeOps next;
+        load_ops(m0 + 8 + w, next);  // operands of the next chunk's node, in flight during this chunk
+        // (A) the positions m0+4 .. m0+11 (group gi)
+        if (gi < ngroups) wait_group(gi);
+        __syncthreads();
+        if (s_abort) { drain(gi, gi + TW_NBUF - 1); return; }
+        if (gi < ngroups) split_row(gi);
+        __syncthreads();
+        if (w == 0) issue(gi + TW_NBUF);  // group gi's buffer is consumed
+        // (B) face m0 + w + 1/2
+        if (m0 + w <= me - 1) face(m0 + w);
+        __syncthreads();
+        // (C) node m0 + w
+        const int m = m0 + w;
+        if (m < me && lane_ok) {
+            const R* f0 = sh + (size_t)((m - ms) & (WS_RING - 1)) * 5 * 32 + lane;
+            const R* f1 = sh + (size_t)((m - ms + 1) & (WS_RING - 1)) * 5 * 32 + lane;
+            R val[5];
+#pragma unroll
+            for (int e = 0; e < 5; ++e) val[e] = -(f1[e * 32] - f0[e * 32]);
+            if (A.Fv) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    val[e + 1] += dcentral_tile<R>(A.ph.vorder, per, n, m, [&](int mq) {
+                        return sv[(((mq - (ms - 4)) & (WV_RING - 1)) * 4 + e) * 32 + lane];
+                    });
+            }
+            finish(m, val, ops);
+        }
+        ops = next;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // boundary conditions on the conserved state (reading R12), one direction per
 // launch, faces lo and hi; applied in the order xi, eta, zeta.
 // ---------------------------------------------------------------------------
@@ -2337,6 +2715,11 @@ template <class R, int EP>
 __global__ void __launch_bounds__(XW) k_sweep_xw(SweepArgs A, int seg_len) { sweep_xw_body<R, EP>(A, blockIdx, seg_len); }
 template <class R, int DIR, int EP>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_sweep_w(SweepArgs A) { sweep_w_body<R, DIR, EP>(A, blockIdx); }
+template <int DIR, int EP>
+__global__ void __launch_bounds__(256, 2) k_sweep_wt(SweepArgs A, const __grid_constant__ TmaRowMaps maps)
+{
+    sweep_wt_body<DIR, EP>(A, maps, blockIdx);
+}
 
 // ---------------------------------------------------------------------------
 // ... and persistent batched launches over an ensemble of uneven blocks: one
@@ -2403,12 +2786,24 @@ __global__ void kb_sensor(BatchMap m) { BATCH_LOOP(sensor_body<true>, false, tru
 __global__ void kb_sensor32(BatchMap m) { BATCH_LOOP(sensor32_body<true>, false, true) }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((visc25_body<R, TZ>), true, false) }
+template <class R>
+__global__ void __launch_bounds__(128) kb_visc_flux_tiles(BatchMap m) { BATCH_LOOP((visc_node_body<R, 4>), false, false) }
 template <class R, int BX, int EP>
 __global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m) { BATCH_LOOP((sweep_x_body<R, BX, EP>), true, false) }
+// walking xi sweep over whole lines (items: one x-line of one block)
+template <class R, int EP>
+__device__ __forceinline__ void sweep_xw_line(const SweepArgs& A, uint3 vb) { sweep_xw_body<R, EP>(A, vb, 1 << 30); }
+template <class R, int EP>
+__global__ void __launch_bounds__(XW) kb_sweep_xw(BatchMap m) { BATCH_LOOP((sweep_xw_line<R, EP>), true, false) }
 template <class R, int DIR, int EP, int TL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (TL == 16 ? 4 : 3) : 1) kb_sweep_t(BatchMap m)
 {
     BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true, false)
+}
+template <class R, int DIR, int EP>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) kb_sweep_w(BatchMap m)
+{
+    BATCH_LOOP((sweep_w_body<R, DIR, EP>), true, false)
 }
 
 }  // namespace cfdk

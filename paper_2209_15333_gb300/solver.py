@@ -239,3 +239,8 @@ class BatchSolver(Solver):
         out = np.empty(self.shapes[block], dtype=np.uint8)
         L.check(L.lib().cfd_get_flags(self.ctx, block, C.c_void_p(out.ctypes.data), 0), self.ctx)
         return out
+
+    def batch_variants(self):
+        """The kernel variants the ensemble runs, as (kind, param) per
+        direction: viscous fluxes, xi, eta, zeta (cfd_get_sweep_variant)."""
+        return {name: self.sweep_variant(d) for name, d in (("visc", 0), ("xi", 3), ("eta", 1), ("zeta", 2))}

@@ -30,6 +30,11 @@ def case_list():
     out.append(("walking_segments", sh, cases.uniform_metrics(*sh), turbulence_field(sh, 83, amp=1.5),
                 dict(scheme=3, Re=200.0, Ma=0.5, theta1=0.004, theta2=0.012),
                 dict(bc_lo=(3, 3, 0), bc_hi=(3, 3, 0), variants=[(3, 1, 100), (1, 2, 13), (2, 2, 0)])))
+    # the FP32 walking eta/zeta sweeps staged by tensor-memory-accelerator copies
+    sh = (64, 21, 26)
+    out.append(("tma_walk_mixed", sh, cases.uniform_metrics(*sh), turbulence_field(sh, 84, amp=1.5),
+                dict(scheme=3, Re=200.0, Ma=0.5, theta1=0.004, theta2=0.012, precision=1),
+                dict(bc_lo=(0, 3, 0), bc_hi=(0, 3, 0), variants=[(1, 3, 8), (2, 3, 0)])))
     return out
 
 

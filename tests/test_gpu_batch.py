@@ -72,6 +72,38 @@ def test_batch_matches_single_block_contexts(orc, precision):
             assert field_rel_err(got[b], Uo) <= 1e-11
 
 
+# ensemble variants as (kind, param): viscous (dir 0), xi (dir 3), eta/zeta (dirs 1, 2)
+VISC_V = [(2, 32), (1, 64), (3, 0)]
+XI_V = [(0, 64), (0, 128), (1, 0)]
+ETA_V = [(1, 16), (1, 32), (2, 64)]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_variants_bit_identical(precision):
+    """Every ensemble kernel variant the autotuner may pick (2.5-D viscous
+    fluxes with 32 / 64 planes or 32 x 4 node tiles; xi in 64- / 128-node
+    segments or walking whole lines; eta and zeta in 16- / 32-node tiles or
+    walking 64-node segments) gives the same bits."""
+    from paper_2209_15333_gb300.solver import BatchSolver
+    mets, params, states = _blocks(precision)
+    outs = []
+    for v in ((0, 0, 0, 0), (1, 1, 1, 1), (2, 2, 2, 2), (2, 0, 1, 2), (0, 2, 2, 1)):
+        with BatchSolver(SHAPES, mets, params, bcs=BCS) as bs:
+            for b, U in enumerate(states):
+                bs.set_state(U, block=b)
+            bs.set_sweep_variant(0, *VISC_V[v[0]])
+            bs.set_sweep_variant(3, *XI_V[v[1]])
+            bs.set_sweep_variant(1, *ETA_V[v[2]])
+            bs.set_sweep_variant(2, *ETA_V[v[3]])
+            got = bs.batch_variants()
+            assert got == {"visc": VISC_V[v[0]], "xi": XI_V[v[1]], "eta": ETA_V[v[2]], "zeta": ETA_V[v[3]]}
+            bs.step(5e-4, 3)
+            outs.append([bs.get_state(block=b) for b in range(len(SHAPES))])
+    for o in outs[1:]:
+        for b in range(len(SHAPES)):
+            assert np.array_equal(o[b], outs[0][b]), b
+
+
 def test_batch_rejects_mismatched_blocks():
     from paper_2209_15333_gb300 import _lib
     from paper_2209_15333_gb300.solver import BatchSolver

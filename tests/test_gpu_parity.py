@@ -282,6 +282,45 @@ def test_sweep_variants_bit_identical(orc, precision):
         assert field_rel_err(outs[0][0], Lo) <= TOL
 
 
+@pytest.mark.parametrize("case", ["hybrid_viscous", "walled_inviscid_ud7"])
+def test_tma_staged_sweeps_bit_identical(case):
+    """The FP32 walking eta/zeta sweeps whose rows arrive by tensor-memory-
+    accelerator copies (kind 3; several segments, periodic and walled lines,
+    with and without classes and viscous fluxes) give the bits of the tiled
+    sweeps.  Pinning kind 3 succeeds only where the TMA kernel runs."""
+    from paper_2209_15333_gb300 import _lib as L
+    from paper_2209_15333_gb300.solver import Solver
+    if case == "hybrid_viscous":
+        sh, bc = (96, 21, 26), dict(bc_lo=(0, 3, 0), bc_hi=(0, 3, 0))
+        prm = dict(scheme=3, Re=150.0, theta1=0.004, theta2=0.012)
+    else:
+        sh, bc = (64, 40, 17), dict(bc_lo=(3, 1, 3), bc_hi=(3, 3, 3))
+        prm = dict(scheme=0, Re=0.0, T_wall=1.2)
+    met = cases.uniform_metrics(*sh)
+    U = turbulence_field(sh, 64)
+    outs = []
+    for kind, param in ((1, 16), (3, 0), (3, 8), (3, 13), (2, 0)):
+        with Solver(sh, met, precision=1, **bc, **prm) as s:
+            s.set_state(U)
+            for d in (1, 2):
+                s.set_sweep_variant(d, kind, param)
+            L_ = s.rhs()
+            s.step(1e-3, 2)
+            outs.append((L_, s.get_state()))
+    for L_, V in outs[1:]:
+        assert np.array_equal(L_, outs[0][0])
+        assert np.array_equal(V, outs[0][1])
+    # not available where rows are not 32-node multiples, nor in FP64
+    with Solver((40, 8, 8), cases.uniform_metrics(40, 8, 8), precision=1) as s:
+        with pytest.raises(L.CfdError) as e:
+            s.set_sweep_variant(1, 3, 0)
+        assert e.value.status == L.CFD_EUNSUPPORTED
+    with Solver((32, 8, 8), cases.uniform_metrics(32, 8, 8), precision=0) as s:
+        with pytest.raises(L.CfdError) as e:
+            s.set_sweep_variant(2, 3, 0)
+        assert e.value.status == L.CFD_EUNSUPPORTED
+
+
 @pytest.mark.parametrize("n", [(17, 9, 5), (16, 8, 4)])
 def test_pinned_host_state_round_trip(n):
     """State copies from and to pinned (device-mapped) host memory, which
