@@ -24,7 +24,9 @@
  *      WENO5 with the out-of-range sub-stencils given weight zero (Sec. 2.2.4).
  *  R11 viscous closures (Sec. 2.3): one-sided 2nd order at the boundary
  *      node, then 2nd/4th/6th-order central at the next three nodes.
- *  R12 boundary conditions (isothermal wall, inflow, extrapolation).
+ *  R12 boundary conditions (isothermal wall, inflow, extrapolation) and the
+ *      paper's undefined "non-reflecting" boundary as characteristic
+ *      extrapolation with frozen incoming waves (nonreflect_node below).
  *  R13 tau_ij = (mu/Re)(du_i/dx_j + du_j/dx_i - 2/3 delta_ij div u) (Eq. 13).
  *  R14 Theta_i = u_j tau_ij + k dT/dx_i (Eq. 12), k from Eq. 14.
  *  R15 Sutherland: mu = T^1.5 (1+S/T_ref)/(T+S/T_ref), S = 110.4 K (Eq. 15).
@@ -519,6 +521,50 @@ static double blowing_velocity(const orc_params* P, int i, int k, double t)
            cos(2.0 * pi * P->blow_m * z / P->blow_Lz) * sin(P->blow_omega * t);
 }
 
+/* Non-reflecting boundary (the paper names one for the ramp's outlet and top
+ * without defining it; this is the characteristic form of Thompson, J. Comput.
+ * Phys. 68 (1987), written as an update of the boundary node).  Linearise
+ * about the boundary node's current state (rho_b, c_b) with the outward unit
+ * normal n of the face.  The changes from the boundary node to the first
+ * interior node of the five characteristic variables
+ *     entropy        dp - c^2 drho        speed u_n
+ *     shear (x2)     dv - (dv.n) n        speed u_n
+ *     acoustic +     dp + rho c (dv.n)    speed u_n + c
+ *     acoustic -     dp - rho c (dv.n)    speed u_n - c
+ * are applied where the characteristic leaves the domain (speed > 0) and
+ * dropped where it enters: the boundary takes what the interior sends out and
+ * admits no incoming wave.  Supersonic outflow reduces to zeroth-order
+ * extrapolation.  met: metrics; nrm_row: 0, 3 or 6 (grad of xi, eta, zeta). */
+static void nonreflect_node(const orc_params* P, const double* met, double* U, long N, long n, long n1,
+                            int nrm_row, double sgn)
+{
+    double ob[7], o1[7];
+    node_prim(P, U, N, n, ob);
+    node_prim(P, U, N, n1, o1);
+    double g0 = met[(nrm_row + 0) * N + n], g1 = met[(nrm_row + 1) * N + n], g2 = met[(nrm_row + 2) * N + n];
+    double gn = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+    double nx = sgn * g0 / gn, ny = sgn * g1 / gn, nz = sgn * g2 / gn;
+    double rho = ob[0], c = sqrt(P->gamma * ob[4] / ob[0]);
+    double un = ob[1] * nx + ob[2] * ny + ob[3] * nz;
+    double drho = o1[0] - ob[0], du = o1[1] - ob[1], dv = o1[2] - ob[2], dw = o1[3] - ob[3];
+    double dp = o1[4] - ob[4];
+    double dvn = du * nx + dv * ny + dw * nz;
+    /* characteristic changes, each kept only if its wave leaves the domain */
+    double e_ent = dp - c * c * drho;
+    double e_tx = du - dvn * nx, e_ty = dv - dvn * ny, e_tz = dw - dvn * nz;
+    double e_ap = dp + rho * c * dvn;
+    double e_am = dp - rho * c * dvn;
+    if (!(un > 0.0)) { e_ent = 0.0; e_tx = 0.0; e_ty = 0.0; e_tz = 0.0; }
+    if (!(un + c > 0.0)) e_ap = 0.0;
+    if (!(un - c > 0.0)) e_am = 0.0;
+    /* back to primitive changes */
+    double dp2 = 0.5 * (e_ap + e_am);
+    double dvn2 = (e_ap - e_am) / (2.0 * rho * c);
+    double drho2 = (dp2 - e_ent) / (c * c);
+    store_prim(P, U, N, n, ob[0] + drho2, ob[1] + e_tx + dvn2 * nx, ob[2] + e_ty + dvn2 * ny,
+               ob[3] + e_tz + dvn2 * nz, ob[4] + dp2);
+}
+
 /* apply the boundary condition of face (d, side) to every node of the face */
 static void bc_face(const orc_params* P, const double* met, double* U, int d, int side, double t)
 {
@@ -542,6 +588,8 @@ static void bc_face(const orc_params* P, const double* met, double* U, int d, in
                 double o[7];
                 node_prim(P, U, N, n1, o);
                 store_prim(P, U, N, n, o[0], o[1], o[2], o[3], o[4]);
+            } else if (type == ORC_BC_NONREFLECT) {
+                nonreflect_node(P, met, U, N, n, n1, 3 * d, side ? 1.0 : -1.0);
             } else if (type == ORC_BC_INFLOW) {
                 if (!P->inflow) continue;
                 int jj = pos[1];

@@ -19,7 +19,7 @@
 extern "C" {
 #endif
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_INFLOW = 2, ORC_BC_OUTFLOW = 3 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_WALL = 1, ORC_BC_INFLOW = 2, ORC_BC_OUTFLOW = 3, ORC_BC_NONREFLECT = 5 };
 enum { ORC_SUTHERLAND = 0, ORC_POWER = 1 };
 enum { ORC_UD7 = 0, ORC_WENO5 = 1, ORC_WENO7 = 2, ORC_HYBRID = 3 };
 enum { ORC_METRIC_NODAL = 0, ORC_METRIC_FSP = 1 };

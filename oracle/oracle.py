@@ -9,7 +9,7 @@ import numpy as np
 
 from . import build as _build
 
-BC_PERIODIC, BC_WALL, BC_INFLOW, BC_OUTFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_WALL, BC_INFLOW, BC_OUTFLOW, BC_NONREFLECT = 0, 1, 2, 3, 5
 SUTHERLAND, POWER = 0, 1
 UD7, WENO5, WENO7, HYBRID = 0, 1, 2, 3
 METRIC_NODAL, METRIC_FSP = 0, 1
