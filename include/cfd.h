@@ -55,8 +55,15 @@ enum {
     CFD_BC_WALL_ISOTHERMAL = 1, /* u = 0 (+ blowing), T = T_wall, p_w = (4 p1 - p2)/3 */
     CFD_BC_INFLOW = 2,          /* Dirichlet from cfd_set_inflow (xi-low face) */
     CFD_BC_OUTFLOW_EXTRAP = 3,  /* zeroth-order extrapolation of primitives */
-    CFD_BC_HALO = 4             /* the first / last CFD_HALO_WIDTH layers are ghost layers that
+    CFD_BC_HALO = 4,            /* the first / last CFD_HALO_WIDTH layers are ghost layers that
                                    cfd_set_halo_links fills from a neighbouring block */
+    CFD_BC_NONREFLECT = 5       /* characteristic non-reflecting boundary (the ramp case's
+                                   "non-reflecting" outlet and top): linearised about the boundary
+                                   node with the outward face normal grad(d)/|grad(d)|, the changes
+                                   toward the first interior node of the entropy, shear and two
+                                   acoustic variables are taken where the wave leaves the domain
+                                   and dropped where it enters (Thompson 1987); supersonic outflow
+                                   is zeroth-order extrapolation */
 };
 
 /* ghost layers per HALO face: the viscous terms reach 8 nodes (a central
@@ -92,7 +99,12 @@ typedef struct {
     int scheme;                /* CFD_UD7, CFD_WENO5, CFD_WENO7, CFD_HYBRID */
     double theta1, theta2;     /* hybrid thresholds (paper: 0.02, 0.1) */
     int visc_order;            /* 6 or 8 */
-    int metric_mode;           /* CFD_METRIC_NODAL (paper) */
+    int metric_mode;           /* CFD_METRIC_NODAL (the paper: split fluxes with each node's own
+                                  metrics), or CFD_METRIC_FSP: free-stream preserving -- every
+                                  interface splits its eight stencil nodes with one interface
+                                  metric, the 8-point midpoint interpolation of alpha = grad(d)/J
+                                  (single-block contexts with periodic lines, component-wise
+                                  reconstruction; a test and robustness mode) */
     int precision;             /* CFD_FP64 or CFD_FP32_BULK */
     int sensor;                /* CFD_SENSOR_PLAIN or CFD_SENSOR_MLP */
     double weno_eps;           /* epsilon of the WENO weights (1e-6) */
@@ -116,7 +128,8 @@ void cfd_default_params(cfd_params* p);
  * stream: a cudaStream_t, or NULL for a stream the context creates.
  * Allocates every device buffer the step needs (about 40 doubles per node
  * in FP64).  Errors: EINVAL (sizes, BC pairs, params), ENOMEM, ECUDA,
- * EUNSUPPORTED (FSP metric mode, MLP sensor without weights).
+ * EUNSUPPORTED (FSP metric mode on non-periodic lines or with
+ * characteristic reconstruction).
  */
 cfd_status cfd_create(cfd_ctx** out, const cfd_grid* grid, const double* metrics,
                       int metrics_on_device, const cfd_params* params, void* stream);

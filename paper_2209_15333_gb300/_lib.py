@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("CFD_GB300_LIB") or os.path.join(HERE, "_build", "libcfd_gb300.so")
 
 CFD_OK, CFD_EINVAL, CFD_ENOMEM, CFD_ECUDA, CFD_ENONPHYS, CFD_ETIMEOUT, CFD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-BC_PERIODIC, BC_WALL_ISOTHERMAL, BC_INFLOW, BC_OUTFLOW_EXTRAP, BC_HALO = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_WALL_ISOTHERMAL, BC_INFLOW, BC_OUTFLOW_EXTRAP, BC_HALO, BC_NONREFLECT = 0, 1, 2, 3, 4, 5
 HALO_WIDTH = 8
 METRICS_3D, METRICS_2D, METRICS_UNIFORM = 0, 1, 2
 SUTHERLAND, POWER = 0, 1

@@ -238,7 +238,7 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
         if (n[d] < 1) return fail(ctx, CFD_EINVAL, "grid dimension < 1");
         for (int side = 0; side < 2; ++side) {
             int t = side ? gr->bc_hi[d] : gr->bc_lo[d];
-            if (t < 0 || t > 4) return fail(ctx, CFD_EINVAL, "unknown boundary condition");
+            if (t < 0 || t > 5) return fail(ctx, CFD_EINVAL, "unknown boundary condition");
         }
         bool plo = gr->bc_lo[d] == CFD_BC_PERIODIC, phi = gr->bc_hi[d] == CFD_BC_PERIODIC;
         if (plo != phi) return fail(ctx, CFD_EINVAL, "periodic must be set on both faces of a direction");
@@ -259,7 +259,15 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
     if (p->visc_law != CFD_SUTHERLAND && p->visc_law != CFD_POWER) return fail(ctx, CFD_EINVAL, "bad visc_law");
     if (p->visc_law == CFD_SUTHERLAND && !(p->T_ref > 0.0)) return fail(ctx, CFD_EINVAL, "T_ref must be > 0");
     if (!(p->weno_eps > 0.0)) return fail(ctx, CFD_EINVAL, "weno_eps must be > 0");
-    if (p->metric_mode != CFD_METRIC_NODAL) return fail(ctx, CFD_EUNSUPPORTED, "only the nodal metric mode");
+    if (p->metric_mode != CFD_METRIC_NODAL && p->metric_mode != CFD_METRIC_FSP)
+        return fail(ctx, CFD_EINVAL, "unknown metric mode");
+    if (p->metric_mode == CFD_METRIC_FSP) {
+        for (int d = 0; d < 3; ++d)
+            if (gr->bc_lo[d] != CFD_BC_PERIODIC)
+                return fail(ctx, CFD_EUNSUPPORTED, "the free-stream-preserving metric mode needs periodic lines");
+        if (p->recon_vars != CFD_RECON_COMPONENT)
+            return fail(ctx, CFD_EUNSUPPORTED, "the free-stream-preserving metric mode reconstructs component-wise");
+    }
     if (p->precision != CFD_FP64 && p->precision != CFD_FP32_BULK) return fail(ctx, CFD_EINVAL, "unknown precision");
     if (p->sensor != CFD_SENSOR_PLAIN && p->sensor != CFD_SENSOR_MLP) return fail(ctx, CFD_EINVAL, "unknown sensor");
     if (p->scheme == CFD_HYBRID && !(p->theta1 <= p->theta2)) return fail(ctx, CFD_EINVAL, "theta1 > theta2");
@@ -458,9 +466,36 @@ static cfd_status check_block(cfd_ctx* ctx, int block)
 // ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
-static cfd_status launch_bc(cfd_ctx* ctx, double* U, double tfrac, bool use_dt)
+static bool has_nonreflect(const Geo& g)
+{
+    for (int d = 0; d < 3; ++d)
+        if (g.bc_lo[d] == CFD_BC_NONREFLECT || g.bc_hi[d] == CFD_BC_NONREFLECT) return true;
+    return false;
+}
+
+// boundary nodes through the stage's RK combination (L = 0) before the
+// boundary conditions; only needed where a face is non-reflecting
+static cfd_status launch_bnd_rk(cfd_ctx* ctx, const Geo& g, double* U, const double* Uin, const double* Un, double a,
+                                double b)
+{
+    if (!Uin || !has_nonreflect(g)) return CFD_OK;
+    for (int d = 0; d < 3; ++d) {
+        if (g.per[d]) continue;
+        long long nface = d == 0 ? (long long)g.ny * g.nz : (d == 1 ? (long long)g.nx * g.nz : (long long)g.nx * g.ny);
+        k_bnd_rk<<<grid_for(2 * nface, 256), 256, 0, ctx->stream>>>(g, U, Uin, Un, a, b, d);
+        LAUNCH_CHECK();
+    }
+    return CFD_OK;
+}
+
+static cfd_status launch_bc(cfd_ctx* ctx, double* U, double tfrac, bool use_dt, const double* Uin = nullptr,
+                            const double* Un = nullptr, double a = 0.0, double b = 1.0)
 {
     const Geo& g = ctx->g;
+    {
+        cfd_status sr = launch_bnd_rk(ctx, g, U, Uin, Un, a, b);
+        if (sr != CFD_OK) return sr;
+    }
     for (int d = 0; d < 3; ++d) {
         if (g.per[d]) continue;
         long long nface = d == 0 ? (long long)g.ny * g.nz : (d == 1 ? (long long)g.nx * g.nz : (long long)g.nx * g.ny);
@@ -559,6 +594,20 @@ static cfd_status launch_xi(cfd_ctx* ctx, SweepArgs& A, int kind, int seg)
 template <class R, int EPF>
 static cfd_status launch_sweeps(cfd_ctx* ctx, SweepArgs& A, cudaEvent_t* ev = nullptr)
 {
+    if (ctx->prm.metric_mode == CFD_METRIC_FSP) {
+        // free-stream-preserving interface metrics: one thread per node and direction
+        const NodeLaunch nl = node_launch(ctx->g);
+        k_sweep_fsp<R, 0, EP_STORE><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+        LAUNCH_CHECK();
+        if (ev) cudaEventRecord(ev[1], ctx->stream);
+        k_sweep_fsp<R, 1, EP_ACCUM><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+        LAUNCH_CHECK();
+        if (ev) cudaEventRecord(ev[2], ctx->stream);
+        k_sweep_fsp<R, 2, EPF><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+        LAUNCH_CHECK();
+        if (ev) cudaEventRecord(ev[3], ctx->stream);
+        return CFD_OK;
+    }
     {
         cfd_status sx = launch_xi<R>(ctx, A, ctx->xi_kind, ctx->xi_seg);
         if (sx != CFD_OK) return sx;
@@ -650,7 +699,9 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
         k_prim<double><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
     LAUNCH_CHECK();
     if (ev) cudaEventRecord(ev[1], ctx->stream);
-    if (!ctx->forced && (mixed || ctx->prm.scheme == CFD_HYBRID)) {
+    const bool sensor = !ctx->forced && (mixed || ctx->prm.scheme == CFD_HYBRID);
+    const cudaStream_t sst = ctx->stream;
+    if (sensor) {
         if (ctx->prm.sensor == CFD_SENSOR_MLP) {
             if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
             // persistent: the SMs filled to the kernel's occupancy, each CTA
@@ -662,11 +713,11 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
             int sms = kSMs;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
             const int grid = (int)std::max(1LL, std::min(tiles, (long long)std::max(1, ps) * sms));
-            k_sensor_mlp<R><<<grid, 128, 0, ctx->stream>>>(A, ctx->mlp);
+            k_sensor_mlp<R><<<grid, 128, 0, sst>>>(A, ctx->mlp);
         } else if (mixed) {
-            k_sensor32<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+            k_sensor32<<<nl.grid, nl.block, 0, sst>>>(A);
         } else {
-            k_sensor<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+            k_sensor<<<nl.grid, nl.block, 0, sst>>>(A);
         }
         LAUNCH_CHECK();
     }
@@ -675,6 +726,7 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
         cfd_status st = launch_visc<R>(ctx, A, ctx->visc_kind);
         if (st != CFD_OK) return st;
     }
+
     if (ev) cudaEventRecord(ev[3], ctx->stream);
     return launch_sweeps<R, EPF>(ctx, A, ev ? ev + 3 : nullptr);
 }
@@ -901,6 +953,10 @@ static cfd_status autotune_t(cfd_ctx* ctx)
 static cfd_status autotune(cfd_ctx* ctx)
 {
     if (ctx->tuned) return CFD_OK;
+    if (ctx->prm.metric_mode == CFD_METRIC_FSP) {
+        ctx->tuned = true;  // its sweeps have one form
+        return CFD_OK;
+    }
     const std::string key = tune_key(ctx);
     std::vector<int> v;
     if (tune_lookup(key, 7, &v) && v[0] >= 0 && v[0] <= 3 && v[2] >= 0 && v[2] <= 3 && v[4] >= 0 && v[4] <= 3 &&
@@ -1382,6 +1438,8 @@ extern "C" cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_gri
                         "all blocks of a batch share precision, scheme, viscous/inviscid, visc_order and sensor");
         if (p.recon_vars != CFD_RECON_COMPONENT)
             return fail(nullptr, CFD_EUNSUPPORTED, "characteristic reconstruction: single-block contexts only");
+        if (p.metric_mode != CFD_METRIC_NODAL)
+            return fail(nullptr, CFD_EUNSUPPORTED, "the free-stream-preserving mode: single-block contexts only");
     }
     cfd_ctx* ctx = new (std::nothrow) cfd_ctx();
     if (!ctx) return fail(nullptr, CFD_ENOMEM, "host allocation");
@@ -1463,8 +1521,13 @@ static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
     }
     // boundary conditions of blocks with non-periodic faces, at the stage time
     const double tfrac[3] = {1.0, 0.5, 1.0};
+    const double ra[3] = {0.0, 0.75, 1.0 / 3.0}, rb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (cfd_ctx* sb : ctx->sub) {
         double* Uout = s == 2 ? sb->b.U : sb->b.Uk;
+        {
+            cfd_status sr = launch_bnd_rk(ctx, sb->g, Uout, s == 0 ? sb->b.U : sb->b.Uk, sb->b.U, ra[s], rb[s]);
+            if (sr != CFD_OK) return sr;
+        }
         for (int d = 0; d < 3; ++d) {
             if (sb->g.per[d]) continue;
             const Geo& g = sb->g;
@@ -1586,17 +1649,17 @@ static cfd_status enqueue_step(cfd_ctx* ctx)
     // stage 1: Uk = U + dt L(U)
     st = run_stage<EP_FINAL_RK>(ctx, ctx->b.U, ctx->b.U, ctx->b.Uk, nullptr, 0.0, 1.0);
     if (st != CFD_OK) return st;
-    st = launch_bc(ctx, ctx->b.Uk, 1.0, true);
+    st = launch_bc(ctx, ctx->b.Uk, 1.0, true, ctx->b.U, ctx->b.U, 0.0, 1.0);
     if (st != CFD_OK) return st;
     // stage 2: Uk = 3/4 U + 1/4 (Uk + dt L(Uk))
     st = run_stage<EP_FINAL_RK>(ctx, ctx->b.Uk, ctx->b.U, ctx->b.Uk, nullptr, 0.75, 0.25);
     if (st != CFD_OK) return st;
-    st = launch_bc(ctx, ctx->b.Uk, 0.5, true);
+    st = launch_bc(ctx, ctx->b.Uk, 0.5, true, ctx->b.Uk, ctx->b.U, 0.75, 0.25);
     if (st != CFD_OK) return st;
     // stage 3: U = 1/3 U + 2/3 (Uk + dt L(Uk))
     st = run_stage<EP_FINAL_RK>(ctx, ctx->b.Uk, ctx->b.U, ctx->b.U, nullptr, 1.0 / 3.0, 2.0 / 3.0);
     if (st != CFD_OK) return st;
-    st = launch_bc(ctx, ctx->b.U, 1.0, true);
+    st = launch_bc(ctx, ctx->b.U, 1.0, true, ctx->b.Uk, ctx->b.U, 1.0 / 3.0, 2.0 / 3.0);
     if (st != CFD_OK) return st;
     k_advance_time<<<1, 32, 0, ctx->stream>>>(ctx->t, ctx->dt);
     LAUNCH_CHECK();
@@ -1633,13 +1696,13 @@ static long long launches_per_step(const cfd_ctx* ctx)
         const bool sensor = ctx->prm.scheme == CFD_HYBRID || ctx->prm.precision == CFD_FP32_BULK;
         long long per_stage = 1 + 3 + (sensor ? 1 : 0) + (ctx->ph.viscous ? 1 : 0);
         for (const cfd_ctx* sb : ctx->sub)
-            for (int d = 0; d < 3; ++d) per_stage += sb->g.per[d] ? 0 : 1;
+            for (int d = 0; d < 3; ++d) per_stage += sb->g.per[d] ? 0 : (has_nonreflect(sb->g) ? 2 : 1);
         return 3 * per_stage + 1;
     }
     const bool sensor = !ctx->forced && (ctx->prm.scheme == CFD_HYBRID || ctx->prm.precision == CFD_FP32_BULK);
     long long per_stage = 1 + 3 + (sensor ? 1 : 0) + (ctx->ph.viscous ? 1 : 0);
     long long bc = 0;
-    for (int d = 0; d < 3; ++d) bc += ctx->g.per[d] ? 0 : 1;
+    for (int d = 0; d < 3; ++d) bc += ctx->g.per[d] ? 0 : (has_nonreflect(ctx->g) ? 2 : 1);
     return 3 * (per_stage + bc) + 1;
 }
 
@@ -1943,6 +2006,8 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
         return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc reconstructs component-wise only");
     if (params->sensor != CFD_SENSOR_PLAIN)
         return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc has no learned-sensor weights: plain sensor only");
+    if (params->metric_mode != CFD_METRIC_NODAL)
+        return fail(nullptr, CFD_EUNSUPPORTED, "cfd_rhs_noalloc evaluates the nodal metric mode only");
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > kMaxNodes)
         return fail(nullptr, CFD_ENOMEM, "cfd_rhs_noalloc: grid has more than CFD_NOALLOC_MAX_NODES nodes");

@@ -2513,6 +2513,94 @@ __device__ __forceinline__ void sweep_wt_body(const SweepArgs& A, const TmaRowMa
 }
 
 // ---------------------------------------------------------------------------
+// Free-stream-preserving metric mode (reading R17; periodic lines): the
+// metric vector of interface j+1/2 is the 8-point midpoint interpolation of
+// the nodal alpha = grad(d)/J over nodes j-3 .. j+4, and all eight stencil
+// nodes are split with that one frozen vector (so a uniform state gives the
+// same split flux at every stencil node and the flux difference telescopes);
+// the WENO indicators are scaled by its norm.  One thread per node computes
+// both of its faces -- a test and robustness mode, not tuned for speed.
+// ---------------------------------------------------------------------------
+// Lagrange weights of the polynomial through offsets -3 .. 4 evaluated at 1/2
+__device__ __forceinline__ double midpoint_weight(int l)
+{
+    double w = 1.0;
+    for (int q = 0; q < 8; ++q)
+        if (q != l) w *= (0.5 - (double)(q - 3)) / (double)(l - q);
+    return w;
+}
+
+template <class R, int DIR>
+__device__ __forceinline__ void fsp_face(const SweepArgs& A, long long base, long long stride, int n, int jf, int i,
+                                         int o, R out[5])
+{
+    const Geo& g = A.g;
+    R ai[3] = {(R)0, (R)0, (R)0};
+    long long nn[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        const int mm = wrapi(jf - 3 + l, n);
+        nn[l] = base + (long long)mm * stride;
+        const long long mi = midx(g, DIR == 0 ? mm : i, DIR == 1 ? mm : o, nn[l]);
+        const R w = (R)midpoint_weight(l);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) ai[e] = mad(w, metr<R>(g, M_ALPHA + 3 * DIR + e, mi), ai[e]);
+    }
+    const R sig = sqrt(mad(ai[2], ai[2], mad(ai[1], ai[1], ai[0] * ai[0])));
+    const R k1 = ai[0] / sig, k2 = ai[1] / sig, k3 = ai[2] / sig;
+    R fp8[5][8], fm8[5][8];
+    int cm = 0;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        const NodePrim<R> q = load_prim<R>(A, nn[l]);
+        R fp[5], fm[5];
+        sw_split<R>(A.ph, q.rho, q.u, q.v, q.w, q.c, k1, k2, k3, sig, fp, fm);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            fp8[e][l] = fp[e];
+            fm8[e][l] = fm[e];
+        }
+        if (A.cls) cm = max(cm, (int)A.cls[nn[l]]);
+    }
+    int mp, mm;
+    const int use = face_use(A.ph, 1, n, jf, cm, &mp, &mm);
+    const R isc = (R)1 / (sig * sig);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) out[e] = face_flux<R>(use, fp8[e], fm8[e], pk<R>(A.ph.eps, A.ph.epsf), isc, 0, 0);
+}
+
+template <class R, int DIR, int EP>
+__global__ void __launch_bounds__(128) k_sweep_fsp(SweepArgs A)
+{
+    const Geo& g = A.g;
+    const uint3 vb = blockIdx;
+    NODE_IJK(g)
+    {
+        const int pos[3] = {i, j, k};
+        const int len = DIR == 0 ? g.nx : (DIR == 1 ? g.ny : g.nz);
+        const long long stride = DIR == 0 ? 1 : (DIR == 1 ? (long long)g.nx : (long long)g.nx * g.ny);
+        const int m = pos[DIR];
+        const long long base = n - (long long)m * stride;  // node 0 of this line
+        R fl[5], fr[5];
+        // metric index of a line node: (m, j) for xi, (i, m) for eta, (i, j) for zeta
+        fsp_face<R, DIR>(A, base, stride, len, m - 1, i, j, fl);
+        fsp_face<R, DIR>(A, base, stride, len, m, i, j, fr);
+        R val[5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) val[e] = -(fr[e] - fl[e]);
+        if (A.Fv) {
+            const R* Fv = (const R*)A.Fv;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const R* f = Fv + (long long)(4 * DIR + r) * g.N + base;
+                val[r + 1] += dcentral<R>(A.ph.vorder, 1, len, m, [&](int q) { return __ldg(f + (long long)q * stride); });
+            }
+        }
+        epilogue<R, EP>(A, n, i, j, k, val);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // boundary conditions on the conserved state (reading R12), one direction per
 // launch, faces lo and hi; applied in the order xi, eta, zeta.
 // ---------------------------------------------------------------------------
@@ -2582,6 +2670,75 @@ __global__ void k_copy_mapped(double2* __restrict__ dst, const double2* __restri
     if (odd && blockIdx.x == 0 && threadIdx.x == 0) *dst1 = *src1;
 }
 
+// Non-reflecting boundary node n (neighbour n1 one node inward), outward
+// normal along sgn * grad(d) of the metrics at the node: the characteristic
+// changes toward the interior -- entropy dp - c^2 drho, shear dv - (dv.n)n,
+// acoustic dp +- rho c dv_n with speeds u_n, u_n, u_n +- c -- are taken where
+// the speed is positive (the wave leaves) and dropped where it enters
+// (Thompson 1987, as an update of the boundary node).
+__device__ __forceinline__ void nonreflect_node(const Geo& g, const Phys& ph, double* U, long long n, long long n1,
+                                                int i, int j, int d, double sgn)
+{
+    const long long N = g.N;
+    double ob[5], o1[5];
+    cons_prim(ph, U, N, n, ob);
+    cons_prim(ph, U, N, n1, o1);
+    const long long mi = midx(g, i, j, n);
+    const double g0 = metv(g, 3 * d, mi), g1 = metv(g, 3 * d + 1, mi), g2 = metv(g, 3 * d + 2, mi);
+    const double gn = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
+    const double nx = sgn * g0 / gn, ny = sgn * g1 / gn, nz = sgn * g2 / gn;
+    const double rho = ob[0], c = sqrt(ph.gamma * ob[4] / ob[0]);
+    const double un = ob[1] * nx + ob[2] * ny + ob[3] * nz;
+    const double drho = o1[0] - ob[0], du = o1[1] - ob[1], dv = o1[2] - ob[2], dw = o1[3] - ob[3];
+    const double dp = o1[4] - ob[4];
+    const double dvn = du * nx + dv * ny + dw * nz;
+    double e_ent = dp - c * c * drho;
+    double e_tx = du - dvn * nx, e_ty = dv - dvn * ny, e_tz = dw - dvn * nz;
+    double e_ap = dp + rho * c * dvn;
+    double e_am = dp - rho * c * dvn;
+    if (!(un > 0.0)) e_ent = e_tx = e_ty = e_tz = 0.0;
+    if (!(un + c > 0.0)) e_ap = 0.0;
+    if (!(un - c > 0.0)) e_am = 0.0;
+    const double dp2 = 0.5 * (e_ap + e_am);
+    const double dvn2 = (e_ap - e_am) / (2.0 * rho * c);
+    const double drho2 = (dp2 - e_ent) / (c * c);
+    put_prim(ph, U, N, n, ob[0] + drho2, ob[1] + e_tx + dvn2 * nx, ob[2] + e_ty + dvn2 * ny, ob[3] + e_tz + dvn2 * nz,
+             ob[4] + dp2);
+}
+
+// Boundary nodes through the RK combination with L = 0 (U_out = a U^n +
+// b U_in) before the boundary conditions of a stage, so that conditions that
+// start from the boundary node's own value (non-reflecting faces) see the
+// same value as in the update of interior nodes.  Face d of one launch skips
+// nodes that also lie on a non-periodic face of a lower direction, so every
+// node is combined once.
+__global__ void k_bnd_rk(Geo g, double* Uout, const double* Uin, const double* Un, double a, double b, int d)
+{
+    const long long N = g.N;
+    const int nd = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
+    const int ax = (d + 1) % 3, bx = (d + 2) % 3;
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    const int na = dims[ax], nb = dims[bx];
+    const long long nface = (long long)na * nb;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 2 * nface;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int side = (int)(e / nface);
+        const long long f = e % nface;
+        int pos[3];
+        pos[ax] = (int)(f % na);
+        pos[bx] = (int)(f / na);
+        pos[d] = side ? nd - 1 : 0;
+        if (side && nd == 1) continue;
+        bool owned = true;
+        for (int q = 0; q < d; ++q)
+            if (!g.per[q] && (pos[q] == 0 || pos[q] == dims[q] - 1)) owned = false;
+        if (!owned) continue;
+        const long long n = pos[0] + (long long)g.nx * (pos[1] + (long long)g.ny * pos[2]);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Uout[q * N + n] = mad(a, Un[q * N + n], b * Uin[q * N + n]);
+    }
+}
+
 __global__ void k_bc(Geo g, Phys ph, BCData bc, double* U, int d, const double* tptr, const double* dtptr,
                      double tfrac)
 {
@@ -2610,6 +2767,8 @@ __global__ void k_bc(Geo g, Phys ph, BCData bc, double* U, int d, const double* 
             double o[5];
             cons_prim(ph, U, N, n1, o);
             put_prim(ph, U, N, n, o[0], o[1], o[2], o[3], o[4]);
+        } else if (type == 5) {
+            nonreflect_node(g, ph, U, n, n1, pos[0], pos[1], d, side ? 1.0 : -1.0);
         } else if (type == 2) {
             if (!bc.inflow) continue;
             const int jj = pos[1];

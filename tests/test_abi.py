@@ -82,8 +82,13 @@ def test_more_validation_without_gpu(built):
 
     p = _lib.default_params()
     assert create(_lib.make_grid(0, 8, 8, metric_layout=_lib.METRICS_UNIFORM), p) == _lib.CFD_EINVAL   # empty
-    assert create(_lib.make_grid(8, 8, 8, bc_lo=(5, 0, 0), bc_hi=(5, 0, 0), metric_layout=_lib.METRICS_UNIFORM),
+    assert create(_lib.make_grid(8, 8, 8, bc_lo=(6, 0, 0), bc_hi=(6, 0, 0), metric_layout=_lib.METRICS_UNIFORM),
                   p) == _lib.CFD_EINVAL                                                               # unknown BC
+    q = _lib.default_params(metric_mode=2)
+    assert create(_lib.make_grid(8, 8, 8, metric_layout=_lib.METRICS_UNIFORM), q) == _lib.CFD_EINVAL  # unknown mode
+    q = _lib.default_params(metric_mode=_lib.METRIC_FSP)                                   # FSP needs periodic lines
+    g = _lib.make_grid(8, 8, 8, bc_lo=(3, 0, 0), bc_hi=(3, 0, 0), metric_layout=_lib.METRICS_UNIFORM)
+    assert create(g, q) == _lib.CFD_EUNSUPPORTED
     # a direction with ghost layers needs 2 * 8 + 1 nodes
     g = _lib.make_grid(16, 8, 8, bc_lo=(_lib.BC_HALO, 0, 0), bc_hi=(_lib.BC_HALO, 0, 0),
                        metric_layout=_lib.METRICS_UNIFORM)

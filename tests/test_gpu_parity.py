@@ -72,16 +72,19 @@ def rhs_case(name, orc):
         return s, c, M, U
     if name == "ramp_walls":
         return ramp_pair(orc)
+    if name == "ramp_nonreflect":
+        # the outlet and the top characteristic non-reflecting boundaries
+        return ramp_pair(orc, bc_hi=(5, 5, 0))
     raise KeyError(name)
 
 
-def ramp_pair(orc, nx=40, ny=24, nz=8, blowing=True):
+def ramp_pair(orc, nx=40, ny=24, nz=8, blowing=True, bc_hi=(3, 3, 0)):
     rc = cases.ramp_case(nx, ny, nz, 24.0, 2.9, Tw=2.8)
     bl = None
     if blowing:
         bl = dict(amp=0.05, x0=-15.0, x1=-10.0, omega=2.0, m=1, Lz=4.0, wall_x=rc["wall_x"], wall_z=rc["wall_z"])
     s, c, M = make_pair(orc, (nx, ny, nz), rc["metrics2d"], scheme="HYBRID", Re=2000.0, Ma=2.9, T_wall=2.8,
-                        visc_law=0, T_ref=108.1, bc_lo=(2, 1, 0), bc_hi=(3, 3, 0), inflow=rc["inflow"], blowing=bl)
+                        visc_law=0, T_ref=108.1, bc_lo=(2, 1, 0), bc_hi=bc_hi, inflow=rc["inflow"], blowing=bl)
     U = rc["U"].copy()
     # a smooth disturbance so that all terms are exercised
     rng = np.random.default_rng(11)
@@ -90,7 +93,7 @@ def ramp_pair(orc, nx=40, ny=24, nz=8, blowing=True):
 
 
 RHS_CASES = ["tgv32_ud7", "ragged_hybrid_v6", "ragged_weno5_inviscid", "ragged_weno7_sutherland", "wavy_3d_metrics",
-             "long_x_tiles", "two_d_nz1", "all_outflow_3d_metrics", "ramp_walls"]
+             "long_x_tiles", "two_d_nz1", "all_outflow_3d_metrics", "ramp_walls", "ramp_nonreflect"]
 
 
 @pytest.mark.parametrize("name", RHS_CASES)
@@ -149,8 +152,11 @@ def test_step_parity_hybrid(orc, forced):
     assert err <= TOL, err
 
 
-def test_step_parity_ramp_with_walls(orc):
-    s, c, M, U = ramp_pair(orc)
+@pytest.mark.parametrize("bc_hi", [(3, 3, 0), (5, 5, 0)])
+def test_step_parity_ramp_with_walls(orc, bc_hi):
+    """Walls, inflow, blowing and (second case) non-reflecting outlet and top:
+    5 RK3 steps against the oracle."""
+    s, c, M, U = ramp_pair(orc, bc_hi=bc_hi)
     with s:
         s.set_state(U)
         Ub = orc.apply_bc(c, M, U)
