@@ -400,6 +400,60 @@ __device__ __forceinline__ void sensor32_body(const SweepArgs& A, uint3 vb)
 //   (q_{m-1} - 2 q_m + q_{m+1}) / (q_{m-1} + 2 q_m + q_{m+1});
 // feature index (2 d + field) * 7 + t.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// mbarrier and tensor-memory-accelerator copies (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit)
+{
+    for (unsigned it = 0; it < limit; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+        "%4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr unsigned TW_WAIT_LIMIT = 1u << 22;  // polls of a bounded mbarrier wait (about 0.3 s)
+
 enum { MLP_IN = 42, MLP_H = 32, MLP_OUT = 3, MLP_KP = 48, MLP_NP = 8 };
 
 struct MlpArgs {
@@ -501,30 +555,178 @@ __device__ __forceinline__ int plain_class(const SweepArgs& A, int i, int j, int
 
 constexpr int MLP_ROW = 56;  // bf16 row stride of the feature tile (conflict-free fragment loads)
 
+// shared arrays of the learned sensor's CTA: the bf16 feature tile of 128
+// nodes, the weights, biases, and per-node flags and classes
+struct MlpSmem {
+    uint16_t sx[128 * MLP_ROW];
+    uint16_t sw1[32 * MLP_ROW];
+    uint16_t sw2[32 * 40];
+    uint16_t sw3[8 * 40];
+    float sb[32 + 32 + 8];
+    unsigned char sbad[128];
+    int scls[128];
+};
+
+__device__ __forceinline__ void mlp_stage_weights(MlpSmem& S, const MlpArgs& W)
+{
+    const int t = threadIdx.x;
+    for (int e = t; e < 32 * MLP_KP; e += 128) S.sw1[(e / MLP_KP) * MLP_ROW + e % MLP_KP] = W.w1[e];
+    for (int e = t; e < 32 * 32; e += 128) S.sw2[(e / 32) * 40 + e % 32] = W.w2[e];
+    for (int e = t; e < 8 * 32; e += 128) S.sw3[(e / 32) * 40 + e % 32] = W.w3[e];
+    for (int e = t; e < 72; e += 128) S.sb[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
+}
+
+// one node's 42 features as a bf16 row of the tile (all zero and flagged if
+// the node is not owned or a feature is not finite)
+__device__ __forceinline__ void mlp_put_row(MlpSmem& S, int t, bool own, const float f[MLP_IN])
+{
+    bool bad = !own;
+    if (own) {
+        // one test for all 42: x * 0 is 0 for finite x and NaN otherwise
+        float z = 0.0f;
+#pragma unroll
+        for (int e = 0; e < MLP_IN; ++e) z = fmaf(f[e], 0.0f, z);
+        bad = !(z == 0.0f);
+    }
+    uint32_t* row = reinterpret_cast<uint32_t*>(S.sx + t * MLP_ROW);
+#pragma unroll
+    for (int e = 0; e < MLP_KP; e += 2) {
+        const float a = (!bad && e < MLP_IN) ? f[e] : 0.0f;
+        const float b = (!bad && e + 1 < MLP_IN) ? f[e + 1] : 0.0f;
+        row[e / 2] = pack_bf16x2(a, b);
+    }
+    S.sbad[t] = bad;
+}
+
+// the three layers on the tensor cores for the tile's 128 rows, the classes
+// (plain-sensor fallback below conf_min) written for the owned nodes; starts
+// after a barrier that made the feature tile visible, ends with one
+template <class RT>
+__device__ __forceinline__ void mlp_classify(MlpSmem& S, const SweepArgs& A, const MlpArgs& W, int i, int j, int k,
+                                             long long n, bool own)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    int cls_row[2][2];  // [m-tile][row half] class (-1: use the plain sensor)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = warp * 32 + mt * 16 + gid;  // rows r0 and r0 + 8
+        // layer 1: [16 x 48] x [48 x 32]
+        float h1[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) h1[nt][e] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 3; ++ks) {
+            uint32_t a[4];
+            const int c = ks * 16 + tig * 2;
+            a[0] = *reinterpret_cast<const uint32_t*>(S.sx + r0 * MLP_ROW + c);
+            a[1] = *reinterpret_cast<const uint32_t*>(S.sx + (r0 + 8) * MLP_ROW + c);
+            a[2] = *reinterpret_cast<const uint32_t*>(S.sx + r0 * MLP_ROW + c + 8);
+            a[3] = *reinterpret_cast<const uint32_t*>(S.sx + (r0 + 8) * MLP_ROW + c + 8);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                uint32_t b[2];
+                const int nn = nt * 8 + gid;
+                b[0] = *reinterpret_cast<const uint32_t*>(S.sw1 + nn * MLP_ROW + c);
+                b[1] = *reinterpret_cast<const uint32_t*>(S.sw1 + nn * MLP_ROW + c + 8);
+                mma_bf16_16816(h1[nt], a, b);
+            }
+        }
+        // bias + ReLU, and the accumulator layout becomes the next A operand
+        uint32_t a2[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const float bb0 = S.sb[nt * 8 + tig * 2], bb1 = S.sb[nt * 8 + tig * 2 + 1];
+            a2[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16x2(fmaxf(h1[nt][0] + bb0, 0.0f), fmaxf(h1[nt][1] + bb1, 0.0f));
+            a2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2(fmaxf(h1[nt][2] + bb0, 0.0f), fmaxf(h1[nt][3] + bb1, 0.0f));
+        }
+        // layer 2: [16 x 32] x [32 x 32]
+        float h2[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) h2[nt][e] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int c = ks * 16 + tig * 2;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                uint32_t b[2];
+                const int nn = nt * 8 + gid;
+                b[0] = *reinterpret_cast<const uint32_t*>(S.sw2 + nn * 40 + c);
+                b[1] = *reinterpret_cast<const uint32_t*>(S.sw2 + nn * 40 + c + 8);
+                mma_bf16_16816(h2[nt], a2[ks], b);
+            }
+        }
+        uint32_t a3[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const float bb0 = S.sb[32 + nt * 8 + tig * 2], bb1 = S.sb[32 + nt * 8 + tig * 2 + 1];
+            a3[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16x2(fmaxf(h2[nt][0] + bb0, 0.0f), fmaxf(h2[nt][1] + bb1, 0.0f));
+            a3[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2(fmaxf(h2[nt][2] + bb0, 0.0f), fmaxf(h2[nt][3] + bb1, 0.0f));
+        }
+        // layer 3: [16 x 32] x [32 x 8] (3 logits used)
+        float lg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const int c = ks * 16 + tig * 2;
+            uint32_t b[2];
+            b[0] = *reinterpret_cast<const uint32_t*>(S.sw3 + gid * 40 + c);
+            b[1] = *reinterpret_cast<const uint32_t*>(S.sw3 + gid * 40 + c + 8);
+            mma_bf16_16816(lg, a3[ks], b);
+        }
+        // logits of row r0 (lg[0..1]) and r0+8 (lg[2..3]) sit in columns 2 tig, 2 tig + 1:
+        // gather columns 0, 1, 2 at tig == 0
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const float c0 = __shfl_sync(0xffffffffu, lg[2 * half], lane & ~3);
+            const float c1 = __shfl_sync(0xffffffffu, lg[2 * half + 1], lane & ~3);
+            const float c2 = __shfl_sync(0xffffffffu, lg[2 * half], (lane & ~3) + 1);
+            const float l0 = c0 + S.sb[64], l1 = c1 + S.sb[65], l2 = c2 + S.sb[66];
+            const float mx = fmaxf(l0, fmaxf(l1, l2));
+            const float z = __expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx);
+            const int arg = l0 >= l1 ? (l0 >= l2 ? 0 : 2) : (l1 >= l2 ? 1 : 2);
+            cls_row[mt][half] = (1.0f / z >= W.conf_min && isfinite(z)) ? arg : -1;
+        }
+    }
+    // one writer per row: lane with tig == 0 owns rows r0 and r0 + 8 of each m-tile
+    if (tig == 0) {
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = warp * 32 + mt * 16 + gid;
+            S.scls[r0] = cls_row[mt][0];
+            S.scls[r0 + 8] = cls_row[mt][1];
+        }
+    }
+    __syncthreads();
+    if (own) {
+        int c = S.scls[t];
+        if (c < 0 || S.sbad[t]) {
+            c = plain_class<RT>(A, i, j, k, n);
+            if (W.fallbacks) atomicAdd(W.fallbacks, 1ull);
+        }
+        A.cls_io[n] = (uint8_t)c;
+    }
+}
+
 // Persistent: each CTA stages the weights once and then walks tiles of 128
-// consecutive x nodes of one (j, k) row (4 warps x 32 rows per tile).
+// consecutive x nodes of one (j, k) row (4 warps x 32 rows per tile).  The
+// x-row segment is staged in shared memory; the eta and zeta values come from
+// coalesced loads at offsets the tile shares.
 template <class RT>
 __global__ void __launch_bounds__(128) k_sensor_mlp(SweepArgs A, MlpArgs W)
 {
-    __shared__ __align__(16) uint16_t sx[128 * MLP_ROW];
-    __shared__ __align__(16) uint16_t sw1[32 * MLP_ROW];
-    __shared__ __align__(16) uint16_t sw2[32 * 40];
-    __shared__ __align__(16) uint16_t sw3[8 * 40];
-    __shared__ float sb[32 + 32 + 8];
-    __shared__ unsigned char sbad[128];
+    __shared__ __align__(16) MlpSmem S;
     __shared__ float srow[2][128 + 6];   // p and rho of the x-row segment with a 3-node halo
     __shared__ long long soff[2][7];     // element offsets of the eta / zeta positions j-3..j+3, k-3..k+3
-    __shared__ int scls[128];
     const Geo& g = A.g;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int t = threadIdx.x;
     const long long N = g.N;
     const RT* Pp = (const RT*)A.P + 4 * N;
     const RT* Pr = (const RT*)A.P;
-    // weights and biases to shared memory, once per CTA
-    for (int e = t; e < 32 * MLP_KP; e += 128) sw1[(e / MLP_KP) * MLP_ROW + e % MLP_KP] = W.w1[e];
-    for (int e = t; e < 32 * 32; e += 128) sw2[(e / 32) * 40 + e % 32] = W.w2[e];
-    for (int e = t; e < 8 * 32; e += 128) sw3[(e / 32) * 40 + e % 32] = W.w3[e];
-    for (int e = t; e < 72; e += 128) sb[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
+    mlp_stage_weights(S, W);
     const int nxc = (g.nx + 127) / 128;
     const long long ntiles = (long long)nxc * g.ny * g.nz;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -536,8 +738,6 @@ __global__ void __launch_bounds__(128) k_sensor_mlp(SweepArgs A, MlpArgs W)
         const long long n = (long long)i + rowb;
         const bool own = i < g.nx;
         __syncthreads();  // the previous tile's shared arrays are consumed
-        // the row segment (x positions i0-3 .. i0+130, wrapped or clamped) and
-        // the offsets of the other two directions, which the tile shares
         for (int e = t; e < 128 + 6; e += 128) {
             const int xx = mlp_pos(i0 - 3, e, g.nx, g.per[0]);
             srow[0][e] = (float)Pp[rowb + xx];
@@ -550,149 +750,26 @@ __global__ void __launch_bounds__(128) k_sensor_mlp(SweepArgs A, MlpArgs W)
             soff[d - 1][tt + 3] = (long long)(mlp_pos(m, tt, d == 1 ? g.ny : g.nz, g.per[d]) - m) * st;
         }
         __syncthreads();
-        // features of this thread's node: xi from the staged row, eta and zeta
-        // from coalesced loads at the shared offsets
-        {
-            float f[MLP_IN];
-            bool bad = !own;
-            if (own) {
-#pragma unroll
-                for (int fld = 0; fld < 2; ++fld) {
-                    float v[7];
-#pragma unroll
-                    for (int tt = 0; tt < 7; ++tt) v[tt] = srow[fld][t + tt];
-                    mlp_feature_line(v, f + fld * 7);
-                    const RT* q = (fld == 0 ? Pp : Pr) + n;
-#pragma unroll
-                    for (int d = 1; d < 3; ++d) {
-#pragma unroll
-                        for (int tt = 0; tt < 7; ++tt) v[tt] = (float)q[soff[d - 1][tt]];
-                        mlp_feature_line(v, f + (2 * d + fld) * 7);
-                    }
-                }
-                // one test for all 42: x * 0 is 0 for finite x and NaN otherwise
-                float z = 0.0f;
-#pragma unroll
-                for (int e = 0; e < MLP_IN; ++e) z = fmaf(f[e], 0.0f, z);
-                bad = !(z == 0.0f);
-            }
-            uint32_t* row = reinterpret_cast<uint32_t*>(sx + t * MLP_ROW);
-#pragma unroll
-            for (int e = 0; e < MLP_KP; e += 2) {
-                const float a = (!bad && e < MLP_IN) ? f[e] : 0.0f;
-                const float b = (!bad && e + 1 < MLP_IN) ? f[e + 1] : 0.0f;
-                row[e / 2] = pack_bf16x2(a, b);
-            }
-            sbad[t] = bad;
-        }
-        __syncthreads();
-        const int gid = lane >> 2, tig = lane & 3;
-        int cls_row[2][2];  // [m-tile][row half] class (-1: use the plain sensor)
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = warp * 32 + mt * 16 + gid;  // rows r0 and r0 + 8
-            // layer 1: [16 x 48] x [48 x 32]
-            float h1[4][4];
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) h1[nt][e] = 0.0f;
-#pragma unroll
-            for (int ks = 0; ks < 3; ++ks) {
-                uint32_t a[4];
-                const int c = ks * 16 + tig * 2;
-                a[0] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c);
-                a[1] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c);
-                a[2] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c + 8);
-                a[3] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c + 8);
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    uint32_t b[2];
-                    const int nn = nt * 8 + gid;
-                    b[0] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c);
-                    b[1] = *reinterpret_cast<const uint32_t*>(sw1 + nn * MLP_ROW + c + 8);
-                    mma_bf16_16816(h1[nt], a, b);
-                }
-            }
-            // bias + ReLU, and the accumulator layout becomes the next A operand
-            uint32_t a2[2][4];
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const float bb0 = sb[nt * 8 + tig * 2], bb1 = sb[nt * 8 + tig * 2 + 1];
-                const uint32_t lo = pack_bf16x2(fmaxf(h1[nt][0] + bb0, 0.0f), fmaxf(h1[nt][1] + bb1, 0.0f));
-                const uint32_t hi = pack_bf16x2(fmaxf(h1[nt][2] + bb0, 0.0f), fmaxf(h1[nt][3] + bb1, 0.0f));
-                a2[nt >> 1][(nt & 1) * 2 + 0] = lo;
-                a2[nt >> 1][(nt & 1) * 2 + 1] = hi;
-            }
-            // layer 2: [16 x 32] x [32 x 32]
-            float h2[4][4];
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) h2[nt][e] = 0.0f;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const int c = ks * 16 + tig * 2;
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    uint32_t b[2];
-                    const int nn = nt * 8 + gid;
-                    b[0] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c);
-                    b[1] = *reinterpret_cast<const uint32_t*>(sw2 + nn * 40 + c + 8);
-                    mma_bf16_16816(h2[nt], a2[ks], b);
-                }
-            }
-            uint32_t a3[2][4];
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const float bb0 = sb[32 + nt * 8 + tig * 2], bb1 = sb[32 + nt * 8 + tig * 2 + 1];
-                const uint32_t lo = pack_bf16x2(fmaxf(h2[nt][0] + bb0, 0.0f), fmaxf(h2[nt][1] + bb1, 0.0f));
-                const uint32_t hi = pack_bf16x2(fmaxf(h2[nt][2] + bb0, 0.0f), fmaxf(h2[nt][3] + bb1, 0.0f));
-                a3[nt >> 1][(nt & 1) * 2 + 0] = lo;
-                a3[nt >> 1][(nt & 1) * 2 + 1] = hi;
-            }
-            // layer 3: [16 x 32] x [32 x 8] (3 logits used)
-            float lg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const int c = ks * 16 + tig * 2;
-                uint32_t b[2];
-                b[0] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c);
-                b[1] = *reinterpret_cast<const uint32_t*>(sw3 + gid * 40 + c + 8);
-                mma_bf16_16816(lg, a3[ks], b);
-            }
-            // logits of row r0 (lg[0..1]) and r0+8 (lg[2..3]) sit in columns 2 tig, 2 tig + 1:
-            // gather columns 0, 1, 2 at tig == 0
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const float c0 = __shfl_sync(0xffffffffu, lg[2 * half], lane & ~3);
-                const float c1 = __shfl_sync(0xffffffffu, lg[2 * half + 1], lane & ~3);
-                const float c2 = __shfl_sync(0xffffffffu, lg[2 * half], (lane & ~3) + 1);
-                const float l0 = c0 + sb[64], l1 = c1 + sb[65], l2 = c2 + sb[66];
-                const float mx = fmaxf(l0, fmaxf(l1, l2));
-                const float z = __expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx);
-                const int arg = l0 >= l1 ? (l0 >= l2 ? 0 : 2) : (l1 >= l2 ? 1 : 2);
-                cls_row[mt][half] = (1.0f / z >= W.conf_min && isfinite(z)) ? arg : -1;
-            }
-        }
-        // one writer per row: lane with tig == 0 owns rows r0 and r0 + 8 of each m-tile
-        if (tig == 0) {
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r0 = warp * 32 + mt * 16 + gid;
-                scls[r0] = cls_row[mt][0];
-                scls[r0 + 8] = cls_row[mt][1];
-            }
-        }
-        __syncthreads();
+        float f[MLP_IN];
         if (own) {
-            int c = scls[t];
-            if (c < 0 || sbad[t]) {
-                c = plain_class<RT>(A, i, j, k, n);
-                if (W.fallbacks) atomicAdd(W.fallbacks, 1ull);
+#pragma unroll
+            for (int fld = 0; fld < 2; ++fld) {
+                float v[7];
+#pragma unroll
+                for (int tt = 0; tt < 7; ++tt) v[tt] = srow[fld][t + tt];
+                mlp_feature_line(v, f + fld * 7);
+                const RT* q = (fld == 0 ? Pp : Pr) + n;
+#pragma unroll
+                for (int d = 1; d < 3; ++d) {
+#pragma unroll
+                    for (int tt = 0; tt < 7; ++tt) v[tt] = (float)q[soff[d - 1][tt]];
+                    mlp_feature_line(v, f + (2 * d + fld) * 7);
+                }
             }
-            A.cls_io[n] = (uint8_t)c;
         }
+        mlp_put_row(S, t, own, f);
+        __syncthreads();
+        mlp_classify<RT>(S, A, W, i, j, k, n, own);
     }
 }
 
@@ -2211,59 +2288,9 @@ struct TmaRowMaps {
     CUtensorMap cls;  // classes as [nz][ny][nx] uint8, box 32 x 1 x 1
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void* p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait for the phase with the given parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit)
-{
-    for (unsigned it = 0; it < limit; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if (it > 64) __nanosleep(64);
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-        "%4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-        : "memory");
-}
-
 // staging layout of one row (bytes): P rho,u,v,w [4][32] at 0, c [32] at
 // 512, Fv [4][32] at 640, classes [32] at 1152; 1280 per row, 8 rows a group
 constexpr int TW_NBUF = 4, TW_ROW = 1280, TW_GROUP = 8 * TW_ROW;
-constexpr unsigned TW_WAIT_LIMIT = 1u << 22;
 
 constexpr size_t walk_tma_smem_bytes()
 {

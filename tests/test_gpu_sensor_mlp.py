@@ -80,13 +80,19 @@ def test_features_match_definition(precision):
     assert np.abs(F - ref).max() <= tol * max(1.0, np.abs(ref).max())
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_mlp_classes_match_numpy_forward_pass(precision):
+# (precision, shape, x boundary): FP32 rows on 16-byte boundaries take the
+# TMA-staged kernel (a partial last tile and clamped line ends in the second
+# case), a ragged FP32 row and the FP64 form take the other kernel
+MLP_CASES = [(0, (40, 24, 20), 0), (1, (40, 24, 20), 0), (1, (132, 12, 10), 3), (1, (37, 16, 12), 3)]
+
+
+@pytest.mark.parametrize("precision,sh,xbc", MLP_CASES)
+def test_mlp_classes_match_numpy_forward_pass(precision, sh, xbc):
     from paper_2209_15333_gb300.solver import Solver
-    sh = (40, 24, 20)
     U = turbulence_field(sh, 92)
     W = random_weights(5)
-    with Solver(sh, cases.uniform_metrics(*sh), precision=precision, scheme=3, Re=100.0) as s:
+    with Solver(sh, cases.uniform_metrics(*sh), precision=precision, scheme=3, Re=100.0, bc_lo=(xbc, 0, 0),
+                bc_hi=(xbc, 0, 0)) as s:
         s.set_state(U)
         F = s.sensor_features()
         s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=0.0)
