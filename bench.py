@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--forms", default="fp64,mixed,mixed_learned")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-only", action="store_true", help="one profiled stage per form (ncu runs)")
+    ap.add_argument("--profile-only", action="store_true", help="one profiled stage and one step per form (ncu runs)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 48-block ensemble measurement")
     ap.add_argument("--no-ramp", action="store_true", help="skip the Mach 2.9 ramp workload")
     ap.add_argument("--ramp-scale", type=int, default=1, help="divide the ramp grid by this factor")
@@ -315,7 +315,9 @@ def run_form(args, form, U, met, params, world, local, dt):
         f = [int(x) for x in item.split(":")]
         s.set_sweep_variant(f[0], f[1], f[2] if len(f) > 2 else 0)
     if args.profile_only:
-        s.profile_stage(1)
+        s.profile_stage(1)   # one right-hand side, kernel by kernel
+        s.step(dt, 1)        # one RK3 step (the update epilogues)
+        s.sync(600.0)
         s.close()
         return None
     # accuracy: one RK3 step from the initial field

@@ -127,7 +127,9 @@ void cfd_default_params(cfd_params* p);
  * grid->metric_layout, host memory (metrics_on_device = 0) or device memory.
  * stream: a cudaStream_t, or NULL for a stream the context creates.
  * Allocates every device buffer the step needs (about 40 doubles per node
- * in FP64).  Errors: EINVAL (sizes, BC pairs, params), ENOMEM, ECUDA,
+ * in FP64).  Errors: EINVAL (sizes -- every dimension >= 1, >= 8 on a
+ * non-periodic line, ny and nz <= 65535, nx * ny < 2^31 -- BC pairs, params),
+ * ENOMEM, ECUDA,
  * EUNSUPPORTED (FSP metric mode on non-periodic lines or with
  * characteristic reconstruction).
  */
@@ -252,6 +254,23 @@ long long cfd_launch_count(const cfd_ctx* ctx);
    CFD_FP32_BULK (float), used as the ALU roofline denominator.  Runs a
    fixed-length kernel of a few milliseconds on its own stream. */
 cfd_status cfd_fma_peak(int precision, double* tflops);
+
+/* Device self-check, not a step of the method.  The mixed-precision form
+   converts between binary64 and binary32 with integer operations instead of
+   the hardware cvt (which takes the narrow FP64 pipe); this runs those
+   conversions against the hardware on the current device: float -> double on
+   all 2^32 float bit patterns, double -> float (round to nearest even) on
+   2^32 doubles from a fixed counter-based sequence that sweeps exponents
+   across and around float's range and forces the rounding edges.  counts
+   (host, CFD_CHECK_CONVERSIONS entries) receives: [0] floats checked,
+   [1] float->double results differing from the hardware (NaN for NaN counts
+   as equal), [2] doubles the integer path accepts, [3] their results
+   differing from the hardware, [4] doubles whose acceptance disagrees with
+   its range (zero, or 2^-126 <= |x| < 2^128).  A correct device gives
+   [1] = [3] = [4] = 0.  Takes a few tens of milliseconds; CFD_EINVAL for a
+   NULL counts, CFD_ECUDA on a CUDA error. */
+#define CFD_CHECK_CONVERSIONS 5
+cfd_status cfd_check_conversions(unsigned long long* counts);
 
 /* Instrumentation, not a step of the method: run `reps` right-hand-side
    evaluations of the current state without a graph, with CUDA events between

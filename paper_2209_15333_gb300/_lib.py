@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "CFD_OK", -1: "CFD_EINVAL", -2: "CFD_ENOMEM", -3: "CFD_ECUDA"
 EXPORTS = ["cfd_default_params", "cfd_create", "cfd_create_batch", "cfd_set_inflow", "cfd_set_blowing", "cfd_set_state",
            "cfd_get_state", "cfd_rhs", "cfd_step", "cfd_cfl_dt", "cfd_get_flags", "cfd_force_flags",
            "cfd_get_time", "cfd_set_time", "cfd_sync", "cfd_last_error", "cfd_launch_count", "cfd_fma_peak",
-           "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
+           "cfd_check_conversions", "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
            "cfd_set_sensor_mlp", "cfd_sensor_features", "cfd_sensor_fallbacks", "cfd_set_halo_links",
            "cfd_destroy"]
 
@@ -88,6 +88,7 @@ def lib():
         L.cfd_launch_count.argtypes = [vp]
         L.cfd_launch_count.restype = C.c_longlong
         L.cfd_fma_peak.argtypes = [C.c_int, dp]
+        L.cfd_check_conversions.argtypes = [C.POINTER(C.c_ulonglong)]
         L.cfd_profile_stage.argtypes = [vp, C.c_int, dp]
         L.cfd_set_sensor_mlp.argtypes = [vp, vp, vp, C.c_float]
         L.cfd_sensor_features.argtypes = [vp, C.c_int, vp, C.c_int]
@@ -110,6 +111,15 @@ def check(status, ctx=None):
     if status != CFD_OK:
         msg = lib().cfd_last_error(ctx).decode()
         raise CfdError(status, msg)
+
+
+def check_conversions():
+    """Device self-check of the integer-pipe binary64 <-> binary32
+    conversions (cfd_check_conversions): dict of the five counts."""
+    out = (C.c_ulonglong * 5)()
+    check(lib().cfd_check_conversions(out))
+    keys = ("floats", "f2d_mismatch", "doubles_ok", "d2f_mismatch", "ok_flag_wrong")
+    return dict(zip(keys, (int(v) for v in out)))
 
 
 def default_params(**kw):

@@ -249,6 +249,7 @@ static cfd_status validate(cfd_ctx* ctx, const cfd_grid* gr, const cfd_params* p
         if (gr->bc_hi[d] == CFD_BC_INFLOW) return fail(ctx, CFD_EINVAL, "inflow only on the xi-low face");
     }
     if (gr->ny > 65535 || gr->nz > 65535) return fail(ctx, CFD_EINVAL, "ny, nz must be <= 65535");
+    if ((long long)gr->nx * gr->ny >= (1LL << 31)) return fail(ctx, CFD_EINVAL, "nx * ny must be < 2^31");
     if (gr->metric_layout < 0 || gr->metric_layout > 2) return fail(ctx, CFD_EINVAL, "bad metric_layout");
     if (!(p->gamma > 1.0) || !(p->Ma > 0.0)) return fail(ctx, CFD_EINVAL, "gamma must be > 1 and Ma > 0");
     if (p->Re > 0.0 && !(p->Pr > 0.0)) return fail(ctx, CFD_EINVAL, "Pr must be > 0");
@@ -704,16 +705,31 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
     if (sensor) {
         if (ctx->prm.sensor == CFD_SENSOR_MLP) {
             if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
-            // persistent: the SMs filled to the kernel's occupancy, each CTA
-            // stages the weights once and walks 128-node row tiles
-            const long long tiles = (long long)((g.nx + 127) / 128) * g.ny * g.nz;
+            // 32 x 8 columns walking zeta; the walk length balances the
+            // waves of resident CTAs against the 7 planes each walk stages
+            // before its first output
+            const size_t smem = sizeof(MlpWalkSmem);
             static int per_sm[2] = {0, 0};
             int& ps = per_sm[sizeof(R) == 4];
-            if (!ps) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp<R>, 128, 0);
+            if (!ps) {
+                cudaFuncSetAttribute(k_sensor_mlp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp<R>, 256, smem);
+                ps = std::max(1, ps);
+            }
             int sms = kSMs;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->dev);
-            const int grid = (int)std::max(1LL, std::min(tiles, (long long)std::max(1, ps) * sms));
-            k_sensor_mlp<R><<<grid, 128, 0, sst>>>(A, ctx->mlp);
+            const long long cols = (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+            int tz = g.nz;
+            double best = 1e300;
+            for (int c : {8, 16, 32, 64}) {
+                const int cz = std::min(c, g.nz);
+                const long long ctas = cols * ((g.nz + cz - 1) / cz);
+                const long long waves = (ctas + (long long)ps * sms - 1) / ((long long)ps * sms);
+                const double cost = (double)waves * (cz + 0.3 * 7);
+                if (cost < best) best = cost, tz = cz;
+            }
+            const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + tz - 1) / tz);
+            k_sensor_mlp<R><<<grid, 256, smem, sst>>>(A, ctx->mlp, tz);
         } else if (mixed) {
             k_sensor32<<<nl.grid, nl.block, 0, sst>>>(A);
         } else {
@@ -1869,6 +1885,30 @@ extern "C" cfd_status cfd_fma_peak(int precision, double* tflops)
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
     if (e != cudaSuccess) return fail(ctx, CFD_ECUDA, std::string("fma probe: ") + cudaGetErrorString(e));
+    return CFD_OK;
+}
+
+extern "C" cfd_status cfd_check_conversions(unsigned long long* counts)
+{
+    if (!counts) return fail(nullptr, CFD_EINVAL, "bad argument to cfd_check_conversions");
+    int dev = 0, sms = 0;
+    cudaStream_t st = nullptr;
+    unsigned long long* out = nullptr;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&out, CFD_CHECK_CONVERSIONS * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, CFD_CHECK_CONVERSIONS * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        k_check_conversions<<<sms * 8, 256, 0, st>>>(out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, out, CFD_CHECK_CONVERSIONS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (out) cudaFree(out);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return fail(nullptr, CFD_ECUDA, std::string("conversion check: ") + cudaGetErrorString(e));
     return CFD_OK;
 }
 

@@ -72,12 +72,16 @@ struct BCData {
     const double* wall_z;  // [nz]
 };
 
-// periodic wrap for offsets of a few nodes (no integer division)
+// periodic wrap of a line position m into [0, n): one period either way
+// (selects, no loop) covers the stencil offsets of every line longer than
+// them; only a position more than one period out (a periodic line shorter
+// than the stencil) takes the integer division
 __device__ __forceinline__ int wrapi(int m, int n)
 {
-    while (m < 0) m += n;
-    while (m >= n) m -= n;
-    return m;
+    const int r = m < 0 ? m + n : (m >= n ? m - n : m);
+    if ((unsigned)r < (unsigned)n) return r;
+    const int q = m % n;
+    return q < 0 ? q + n : q;
 }
 
 __device__ __forceinline__ long long midx(const Geo& g, int i, int j, long long n)
@@ -217,6 +221,52 @@ __device__ __forceinline__ bool below_1e300(double x)
            (unsigned long long)__double_as_longlong(1e300);
 }
 
+// ---------------------------------------------------------------------------
+// binary64 <-> binary32 format conversions on the integer pipe (IEEE 754
+// field layouts: 1 sign, 11/8 exponent bits biased by 1023/127, 52/23
+// fraction bits).  A hardware cvt between the two formats takes a slot of
+// the narrow FP64 pipe; these take a handful of integer operations and give
+// the same bits (checked against the hardware over every float and a
+// structured sweep of doubles by cfd_check_conversions).
+// ---------------------------------------------------------------------------
+// float -> double, exact for every input (NaN stays NaN)
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const unsigned b = __float_as_uint(f), a = b & 0x7fffffffu;
+    unsigned hi, lo = b << 29;                         // the low 3 fraction bits
+    if (a - 0x00800000u < 0x7f000000u) {               // normal: exponent + (1023 - 127)
+        hi = (a >> 3) + (896u << 20);
+    } else if (a >= 0x7f800000u) {                     // infinity, NaN
+        hi = (a >> 3) | 0x7ff00000u;
+    } else if (a == 0u) {
+        hi = 0u;
+    } else {                                           // subnormal: normalise the fraction
+        const unsigned sh = (unsigned)__clz((int)a) - 8u, m = a << sh;
+        hi = ((m & 0x7fffffu) >> 3) + ((897u - sh) << 20);
+        lo = m << 29;
+    }
+    return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
+
+// double -> float, round to nearest even.  ok is true, and the result the
+// correctly rounded one, for zero and for every x whose float is normal or
+// overflows by rounding (2^-126 <= |x| < 2^128); elsewhere (subnormal
+// results, |x| >= 2^128, infinities, NaN) ok is false.
+__device__ __forceinline__ float d2f_rn_int(double x, bool& ok)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned ah = hi & 0x7fffffffu;
+    const unsigned t = __funnelshift_l(lo, ah - (896u << 20), 3);  // rebiased, fraction cut to 23 bits
+    const unsigned r = lo & 0x1fffffffu;                            // the 29 fraction bits cut off
+    const unsigned f = t + ((r + 0x0fffffffu + (t & 1u)) >> 29);   // half to even; may carry into the exponent
+    const bool zero = (ah | lo) == 0u;
+    ok = ah - (897u << 20) < (254u << 20) || zero;
+    return __uint_as_float((hi & 0x80000000u) | (zero ? 0u : f));
+}
+
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_exact(x); }
+
 template <class RT, bool FLAT = false>
 __device__ __forceinline__ void prim_body(const SweepArgs& A, uint3 vb)
 {
@@ -253,7 +303,10 @@ __device__ __forceinline__ void prim_body(const SweepArgs& A, uint3 vb)
 // Mixed precision: primitives in FP32 arithmetic, except within 4 nodes of a
 // wall and at nodes whose previous sensor class is not UD7 (shocks), where the
 // recovery runs in FP64 (catastrophic cancellation in E - rho|u|^2/2 is worst
-// there); stored as float in both cases.
+// there); stored as float in both cases.  The FP32 recovery rounds the
+// conserved variables to float on the integer pipe; a node with one of them
+// outside float's normal range (nonzero below 2^-126 or at least 2^128) takes
+// the FP64 recovery too.
 __device__ __forceinline__ bool near_wall(const Geo& g, int i, int j, int k)
 {
     const int pos[3] = {i, j, k};
@@ -279,7 +332,11 @@ __device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
     NODE_IJK_SEL(g, FLAT)
     {
         float rho, u, v, w, p, T, c;
-        if (cls_prev[n] != 0 || near_wall(g, i, j, k)) {
+        bool ok[5];
+        float q[5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) q[e] = d2f_rn_int(U[e * N + n], ok[e]);
+        if (cls_prev[n] != 0 || near_wall(g, i, j, k) || !(ok[0] && ok[1] && ok[2] && ok[3] && ok[4])) {
             double rd = U[n];
             double ri = 1.0 / rd;
             double ud = U[N + n] * ri, vd = U[2 * N + n] * ri, wd = U[3 * N + n] * ri;
@@ -288,12 +345,12 @@ __device__ __forceinline__ void prim_mixed_body(const SweepArgs& A, uint3 vb)
             rho = (float)rd; u = (float)ud; v = (float)vd; w = (float)wd; p = (float)pd; T = (float)Td;
             c = sqrtf(T) * ph.invMaf;
         } else {
-            rho = (float)U[n];
+            rho = q[0];
             float ri = 1.0f / rho;
-            u = (float)U[N + n] * ri;
-            v = (float)U[2 * N + n] * ri;
-            w = (float)U[3 * N + n] * ri;
-            p = ph.gm1f * mad(-0.5f * rho, mad(w, w, mad(v, v, u * u)), (float)U[4 * N + n]);
+            u = q[1] * ri;
+            v = q[2] * ri;
+            w = q[3] * ri;
+            p = ph.gm1f * mad(-0.5f * rho, mad(w, w, mad(v, v, u * u)), q[4]);
             T = ph.gMa2f * p * ri;
             c = sqrtf(T) * ph.invMaf;
         }
@@ -469,16 +526,20 @@ struct MlpArgs {
 
 // the seven features of one field along one direction from the values at
 // line positions m-3 .. m+3 (one routine for every kernel that builds them,
-// so that they agree bit for bit)
-__device__ __forceinline__ void mlp_feature_line(const float v[7], float* o)
+// so that they agree bit for bit); inv = 1 / v[3], the node's own value,
+// which its three lines share
+__device__ __forceinline__ void mlp_feature_line_inv(const float v[7], float inv, float* o)
 {
-    const float inv = 1.0f / v[3];
 #pragma unroll
     for (int t = 0; t < 6; ++t) o[t] = (v[t + 1] - v[t]) * inv;
     const float v2 = v[3] + v[3];
     // a ratio in [-1, 1] for positive p and rho: the fast division's few
     // units of rounding are far below the bf16 rounding of the inputs
     o[6] = __fdividef((v[2] - v2) + v[4], (v[2] + v2) + v[4]);
+}
+__device__ __forceinline__ void mlp_feature_line(const float v[7], float* o)
+{
+    mlp_feature_line_inv(v, 1.0f / v[3], o);
 }
 
 // line position m + t (t = -3..3) with periodic wrap or clamping at the ends
@@ -555,30 +616,27 @@ __device__ __forceinline__ int plain_class(const SweepArgs& A, int i, int j, int
 
 constexpr int MLP_ROW = 56;  // bf16 row stride of the feature tile (conflict-free fragment loads)
 
-// shared arrays of the learned sensor's CTA: the bf16 feature tile of 128
-// nodes, the weights, biases, and per-node flags and classes
-struct MlpSmem {
-    uint16_t sx[128 * MLP_ROW];
+// the network's weights and biases in shared memory (bf16 rows padded for
+// conflict-free B-fragment loads)
+struct MlpWeightsSmem {
     uint16_t sw1[32 * MLP_ROW];
     uint16_t sw2[32 * 40];
     uint16_t sw3[8 * 40];
     float sb[32 + 32 + 8];
-    unsigned char sbad[128];
-    int scls[128];
 };
 
-__device__ __forceinline__ void mlp_stage_weights(MlpSmem& S, const MlpArgs& W)
+__device__ __forceinline__ void mlp_stage_weights(MlpWeightsSmem& S, const MlpArgs& W)
 {
-    const int t = threadIdx.x;
-    for (int e = t; e < 32 * MLP_KP; e += 128) S.sw1[(e / MLP_KP) * MLP_ROW + e % MLP_KP] = W.w1[e];
-    for (int e = t; e < 32 * 32; e += 128) S.sw2[(e / 32) * 40 + e % 32] = W.w2[e];
-    for (int e = t; e < 8 * 32; e += 128) S.sw3[(e / 32) * 40 + e % 32] = W.w3[e];
-    for (int e = t; e < 72; e += 128) S.sb[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int e = t; e < 32 * MLP_KP; e += nt) S.sw1[(e / MLP_KP) * MLP_ROW + e % MLP_KP] = W.w1[e];
+    for (int e = t; e < 32 * 32; e += nt) S.sw2[(e / 32) * 40 + e % 32] = W.w2[e];
+    for (int e = t; e < 8 * 32; e += nt) S.sw3[(e / 32) * 40 + e % 32] = W.w3[e];
+    for (int e = t; e < 72; e += nt) S.sb[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
 }
 
-// one node's 42 features as a bf16 row of the tile (all zero and flagged if
-// the node is not owned or a feature is not finite)
-__device__ __forceinline__ void mlp_put_row(MlpSmem& S, int t, bool own, const float f[MLP_IN])
+// one node's 42 features as a bf16 row of a feature tile; the row is all
+// zero and true is returned if the node is not owned or a feature is not finite
+__device__ __forceinline__ bool mlp_put_row(uint16_t* row16, bool own, const float f[MLP_IN])
 {
     bool bad = !own;
     if (own) {
@@ -588,29 +646,29 @@ __device__ __forceinline__ void mlp_put_row(MlpSmem& S, int t, bool own, const f
         for (int e = 0; e < MLP_IN; ++e) z = fmaf(f[e], 0.0f, z);
         bad = !(z == 0.0f);
     }
-    uint32_t* row = reinterpret_cast<uint32_t*>(S.sx + t * MLP_ROW);
+    uint32_t* row = reinterpret_cast<uint32_t*>(row16);
 #pragma unroll
     for (int e = 0; e < MLP_KP; e += 2) {
         const float a = (!bad && e < MLP_IN) ? f[e] : 0.0f;
         const float b = (!bad && e + 1 < MLP_IN) ? f[e + 1] : 0.0f;
         row[e / 2] = pack_bf16x2(a, b);
     }
-    S.sbad[t] = bad;
+    return bad;
 }
 
-// the three layers on the tensor cores for the tile's 128 rows, the classes
-// (plain-sensor fallback below conf_min) written for the owned nodes; starts
-// after a barrier that made the feature tile visible, ends with one
-template <class RT>
-__device__ __forceinline__ void mlp_classify(MlpSmem& S, const SweepArgs& A, const MlpArgs& W, int i, int j, int k,
-                                             long long n, bool own)
+// The three layers on the tensor cores for the 32 rows of one warp's feature
+// tile sx (rows 0..31, stride MLP_ROW); every lane gets the class of row
+// `lane`, -1 where the top softmax probability is below conf_min (or not
+// finite).  Warp-synchronous: the caller orders the rows' writes before it
+// (__syncwarp) and any rewrite after it.
+__device__ __forceinline__ int mlp_classify_warp(const uint16_t* sx, const MlpWeightsSmem& S, float conf_min)
 {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int lane = threadIdx.x & 31;
     const int gid = lane >> 2, tig = lane & 3;
-    int cls_row[2][2];  // [m-tile][row half] class (-1: use the plain sensor)
+    int cls_row[2][2];  // [m-tile][row half]
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = warp * 32 + mt * 16 + gid;  // rows r0 and r0 + 8
+        const int r0 = mt * 16 + gid;  // rows r0 and r0 + 8
         // layer 1: [16 x 48] x [48 x 32]
         float h1[4][4];
 #pragma unroll
@@ -621,10 +679,10 @@ __device__ __forceinline__ void mlp_classify(MlpSmem& S, const SweepArgs& A, con
         for (int ks = 0; ks < 3; ++ks) {
             uint32_t a[4];
             const int c = ks * 16 + tig * 2;
-            a[0] = *reinterpret_cast<const uint32_t*>(S.sx + r0 * MLP_ROW + c);
-            a[1] = *reinterpret_cast<const uint32_t*>(S.sx + (r0 + 8) * MLP_ROW + c);
-            a[2] = *reinterpret_cast<const uint32_t*>(S.sx + r0 * MLP_ROW + c + 8);
-            a[3] = *reinterpret_cast<const uint32_t*>(S.sx + (r0 + 8) * MLP_ROW + c + 8);
+            a[0] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c);
+            a[1] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c);
+            a[2] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c + 8);
+            a[3] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c + 8);
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) {
                 uint32_t b[2];
@@ -678,7 +736,7 @@ __device__ __forceinline__ void mlp_classify(MlpSmem& S, const SweepArgs& A, con
             mma_bf16_16816(lg, a3[ks], b);
         }
         // logits of row r0 (lg[0..1]) and r0+8 (lg[2..3]) sit in columns 2 tig, 2 tig + 1:
-        // gather columns 0, 1, 2 at tig == 0
+        // every lane of the quad gathers columns 0, 1, 2 from its first two lanes
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             const float c0 = __shfl_sync(0xffffffffu, lg[2 * half], lane & ~3);
@@ -688,88 +746,124 @@ __device__ __forceinline__ void mlp_classify(MlpSmem& S, const SweepArgs& A, con
             const float mx = fmaxf(l0, fmaxf(l1, l2));
             const float z = __expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx);
             const int arg = l0 >= l1 ? (l0 >= l2 ? 0 : 2) : (l1 >= l2 ? 1 : 2);
-            cls_row[mt][half] = (1.0f / z >= W.conf_min && isfinite(z)) ? arg : -1;
+            cls_row[mt][half] = (1.0f / z >= conf_min && isfinite(z)) ? arg : -1;
         }
     }
-    // one writer per row: lane with tig == 0 owns rows r0 and r0 + 8 of each m-tile
-    if (tig == 0) {
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = warp * 32 + mt * 16 + gid;
-            S.scls[r0] = cls_row[mt][0];
-            S.scls[r0 + 8] = cls_row[mt][1];
-        }
-    }
-    __syncthreads();
-    if (own) {
-        int c = S.scls[t];
-        if (c < 0 || S.sbad[t]) {
-            c = plain_class<RT>(A, i, j, k, n);
-            if (W.fallbacks) atomicAdd(W.fallbacks, 1ull);
-        }
-        A.cls_io[n] = (uint8_t)c;
-    }
+    // row L was classified by the quad of lanes 4 (L mod 8) .. 4 (L mod 8) + 3
+    // as cls_row[L / 16][(L / 8) mod 2]
+    const int src = (lane & 7) * 4;
+    const int c00 = __shfl_sync(0xffffffffu, cls_row[0][0], src), c01 = __shfl_sync(0xffffffffu, cls_row[0][1], src);
+    const int c10 = __shfl_sync(0xffffffffu, cls_row[1][0], src), c11 = __shfl_sync(0xffffffffu, cls_row[1][1], src);
+    const int half = (lane >> 3) & 1;
+    return lane < 16 ? (half ? c01 : c00) : (half ? c11 : c10);
 }
 
-// Persistent: each CTA stages the weights once and then walks tiles of 128
-// consecutive x nodes of one (j, k) row (4 warps x 32 rows per tile).  The
-// x-row segment is staged in shared memory; the eta and zeta values come from
-// coalesced loads at offsets the tile shares.
+// Learned sensor, walking form.  A CTA of 8 warps owns a 32 x 8 (x, y) column
+// of nodes and walks zeta over `tz` planes.  p and rho of each plane, with a
+// 3-node x/y halo (38 x 14 values, periodic lines wrapped, others clamped as
+// the features define), are loaded once into a ring of 8 planes in shared
+// memory; the next plane's loads are issued before the current plane's
+// features and layers and stored into the ring after them.  The features of
+// plane z come from the ring: x and y lines from plane z, zeta lines from
+// planes z-3 .. z+3.  Warp w holds the nodes of y-row w and classifies its
+// own 32 feature rows, so the only CTA barrier per plane orders the ring:
+// plane z+4 overwrites plane z-4, whose last reader was plane z-1.
+constexpr int MW_X = 32 + 6, MW_Y = 8 + 6, MW_PL = MW_X * MW_Y;  // staged plane: 38 x 14
+constexpr int MW_RING = 8;
+
+struct MlpWalkSmem {
+    float ring[MW_RING][2][MW_PL];  // [plane mod 8][p, rho][hy * 38 + hx]
+    uint16_t sx[256 * MLP_ROW];     // bf16 feature rows, row = warp * 32 + lane
+    MlpWeightsSmem w;
+};
+
 template <class RT>
-__global__ void __launch_bounds__(128) k_sensor_mlp(SweepArgs A, MlpArgs W)
+__global__ void __launch_bounds__(256, 3) k_sensor_mlp(SweepArgs A, MlpArgs W, int tz)
 {
-    __shared__ __align__(16) MlpSmem S;
-    __shared__ float srow[2][128 + 6];   // p and rho of the x-row segment with a 3-node halo
-    __shared__ long long soff[2][7];     // element offsets of the eta / zeta positions j-3..j+3, k-3..k+3
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpWalkSmem& S = *reinterpret_cast<MlpWalkSmem*>(smem_raw);
     const Geo& g = A.g;
-    const int t = threadIdx.x;
-    const long long N = g.N;
+    const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long N = g.N, plane = (long long)nx * ny;
     const RT* Pp = (const RT*)A.P + 4 * N;
     const RT* Pr = (const RT*)A.P;
-    mlp_stage_weights(S, W);
-    const int nxc = (g.nx + 127) / 128;
-    const long long ntiles = (long long)nxc * g.ny * g.nz;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int i0 = (int)(tile % nxc) * 128;
-        const long long rest = tile / nxc;
-        const int j = (int)(rest % g.ny), k = (int)(rest / g.ny);
-        const int i = i0 + t;
-        const long long rowb = (long long)g.nx * ((long long)j + (long long)g.ny * k);
-        const long long n = (long long)i + rowb;
-        const bool own = i < g.nx;
-        __syncthreads();  // the previous tile's shared arrays are consumed
-        for (int e = t; e < 128 + 6; e += 128) {
-            const int xx = mlp_pos(i0 - 3, e, g.nx, g.per[0]);
-            srow[0][e] = (float)Pp[rowb + xx];
-            srow[1][e] = (float)Pr[rowb + xx];
-        }
-        if (t < 14) {
-            const int d = 1 + t / 7, tt = t % 7 - 3;
-            const int m = d == 1 ? j : k;
-            const long long st = d == 1 ? (long long)g.nx : (long long)g.nx * g.ny;
-            soff[d - 1][tt + 3] = (long long)(mlp_pos(m, tt, d == 1 ? g.ny : g.nz, g.per[d]) - m) * st;
-        }
-        __syncthreads();
-        float f[MLP_IN];
-        if (own) {
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
+    const int z0 = blockIdx.z * tz, z1 = min(z0 + tz, nz);
+    mlp_stage_weights(S.w, W);
+    // the staged positions of this thread (t, t + 256, t + 512 of the 532)
+    // and their offsets within a plane, the same for every plane
+    int poff[3];
 #pragma unroll
-            for (int fld = 0; fld < 2; ++fld) {
-                float v[7];
+    for (int r = 0; r < 3; ++r) {
+        const int e = t + 256 * r;
+        const int hy = e / MW_X, hx = e - hy * MW_X;
+        poff[r] = e < MW_PL ? mlp_pos(x0 - 3, hx, nx, g.per[0]) + nx * mlp_pos(y0 - 3, hy, ny, g.per[1]) : 0;
+    }
+    auto load_plane = [&](int z, float (&v)[3][2]) {
+        const long long base = (long long)mlp_pos(z, 0, nz, g.per[2]) * plane;
 #pragma unroll
-                for (int tt = 0; tt < 7; ++tt) v[tt] = srow[fld][t + tt];
-                mlp_feature_line(v, f + fld * 7);
-                const RT* q = (fld == 0 ? Pp : Pr) + n;
-#pragma unroll
-                for (int d = 1; d < 3; ++d) {
-#pragma unroll
-                    for (int tt = 0; tt < 7; ++tt) v[tt] = (float)q[soff[d - 1][tt]];
-                    mlp_feature_line(v, f + (2 * d + fld) * 7);
-                }
+        for (int r = 0; r < 3; ++r)
+            if (t + 256 * r < MW_PL) {
+                v[r][0] = (float)__ldg(Pp + base + poff[r]);
+                v[r][1] = (float)__ldg(Pr + base + poff[r]);
             }
+    };
+    auto store_plane = [&](int z, const float (&v)[3][2]) {
+        const int slot = z & (MW_RING - 1);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            if (t + 256 * r < MW_PL) {
+                S.ring[slot][0][t + 256 * r] = v[r][0];
+                S.ring[slot][1][t + 256 * r] = v[r][1];
+            }
+    };
+    // prologue: planes z0-3 .. z0+3
+    for (int z = z0 - 3; z <= z0 + 3; ++z) {
+        float v[3][2];
+        load_plane(z, v);
+        store_plane(z, v);
+    }
+    __syncthreads();
+    const int i = x0 + tx, j = y0 + ty;
+    const bool own = i < nx && j < ny;
+    const int ctr = (ty + 3) * MW_X + tx + 3;  // the node in a staged plane
+    uint16_t* sxw = S.sx + ty * 32 * MLP_ROW;   // this warp's feature rows
+    for (int z = z0; z < z1; ++z) {
+        // plane z+4 is read by the outputs up to z1-1 while z+4 <= z1+2
+        const bool more = z + 4 <= z1 + 2;
+        float nxt[3][2];
+        if (more) load_plane(z + 4, nxt);
+        float f[MLP_IN];
+#pragma unroll
+        for (int fld = 0; fld < 2; ++fld) {
+            const float* c = S.ring[z & (MW_RING - 1)][fld];
+            const float inv = 1.0f / c[ctr];
+            float v[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[q] = c[ctr + q - 3];
+            mlp_feature_line_inv(v, inv, f + fld * 7);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[q] = c[ctr + (q - 3) * MW_X];
+            mlp_feature_line_inv(v, inv, f + (2 + fld) * 7);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[q] = S.ring[(z + q - 3) & (MW_RING - 1)][fld][ctr];
+            mlp_feature_line_inv(v, inv, f + (4 + fld) * 7);
         }
-        mlp_put_row(S, t, own, f);
+        const bool bad = mlp_put_row(sxw + tx * MLP_ROW, own, f);
+        __syncwarp();
+        const int cls = mlp_classify_warp(sxw, S.w, W.conf_min);
+        if (own) {
+            const long long n = (long long)i + (long long)nx * ((long long)j + (long long)ny * z);
+            int c = cls;
+            if (c < 0 || bad) {
+                c = plain_class<RT>(A, i, j, z, n);
+                if (W.fallbacks) atomicAdd(W.fallbacks, 1ull);
+            }
+            A.cls_io[n] = (uint8_t)c;
+        }
+        if (more) store_plane(z + 4, nxt);
         __syncthreads();
-        mlp_classify<RT>(S, A, W, i, j, k, n, own);
     }
 }
 
@@ -1387,6 +1481,15 @@ __device__ __forceinline__ void visc25_body(const SweepArgs& A, uint3 vb)
 // epilogue modes
 enum { EP_STORE = 0, EP_ACCUM = 1, EP_FINAL_RHS = 2, EP_FINAL_RK = 3 };
 
+// RK3 update of one conserved variable, U_out = a U^n + b (U + dt J s), with s
+// the summed sweep residual (exact in FP64) and dtJ = dt J formed once per
+// node; the first stage (a = 0, b = 1) is a single FMA
+__device__ __forceinline__ double rk_combine(const SweepArgs& A, double dtJ, double s, double u, double un)
+{
+    const double y = mad(dtJ, s, u);
+    return A.rk_a == 0.0 && A.rk_b == 1.0 ? y : mad(A.rk_a, un, A.rk_b * y);
+}
+
 template <class R, int EP>
 __device__ __forceinline__ void epilogue(const SweepArgs& A, long long n, int i, int j, int k, const R val[5])
 {
@@ -1404,16 +1507,14 @@ __device__ __forceinline__ void epilogue(const SweepArgs& A, long long n, int i,
         const double J = metv(A.g, M_J, midx(A.g, i, j, n));
         if (EP == EP_FINAL_RHS) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) A.Lout[q * N + n] = bnd ? 0.0 : J * (double)(Racc[q * N + n] + val[q]);
+            for (int q = 0; q < 5; ++q) A.Lout[q * N + n] = bnd ? 0.0 : J * to_f64(Racc[q * N + n] + val[q]);
         } else {
             if (bnd) return;  // boundary nodes are set by the boundary conditions
-            const double dt = *A.dt;
+            const double dtJ = *A.dt * J;
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                double L = J * (double)(Racc[q * N + n] + val[q]);
-                double uk = A.U[q * N + n];
-                double un = A.rk_a != 0.0 ? A.Un[q * N + n] : 0.0;
-                A.Uout[q * N + n] = mad(A.rk_a, un, A.rk_b * mad(dt, L, uk));
+                const double un = A.rk_a != 0.0 ? A.Un[q * N + n] : 0.0;
+                A.Uout[q * N + n] = rk_combine(A, dtJ, to_f64(Racc[q * N + n] + val[q]), A.U[q * N + n], un);
             }
         }
     }
@@ -2479,15 +2580,13 @@ __device__ __forceinline__ void sweep_wt_body(const SweepArgs& A, const TmaRowMa
             const double J = metv(g, M_J, midx(g, i, jj, nn));
             if (EP == EP_FINAL_RHS) {
 #pragma unroll
-                for (int e = 0; e < 5; ++e) A.Lout[e * N + nn] = bnd ? 0.0 : J * (double)(op.r[e] + val[e]);
+                for (int e = 0; e < 5; ++e) A.Lout[e * N + nn] = bnd ? 0.0 : J * to_f64(op.r[e] + val[e]);
             } else {
                 if (bnd) return;
-                const double dt = *A.dt;
+                const double dtJ = *A.dt * J;
 #pragma unroll
-                for (int e = 0; e < 5; ++e) {
-                    const double L = J * (double)(op.r[e] + val[e]);
-                    A.Uout[e * N + nn] = mad(A.rk_a, op.un[e], A.rk_b * mad(dt, L, op.u[e]));
-                }
+                for (int e = 0; e < 5; ++e)
+                    A.Uout[e * N + nn] = rk_combine(A, dtJ, to_f64(op.r[e] + val[e]), op.u[e], op.un[e]);
             }
         }
     };
@@ -2866,6 +2965,63 @@ __global__ void k_fma_probe(T* out, int iters, T a, T b)
 #pragma unroll
     for (int r = 0; r < 8; ++r) s += x[r];
     if (s == (T)12345.678) out[0] = s;  // keeps the chains alive
+}
+
+// Self-check of the integer-pipe format conversions against the hardware
+// cvt: f2d_exact over every float bit pattern; d2f_rn_int over 2^32 doubles
+// drawn by SplitMix64 (Steele, Lea, Flood 2014) from their index, with
+// exponents swept across and around float's range and the 29 cut-off
+// fraction bits forced to the rounding edges (0, just below, at and just
+// above one half, all ones) in five of every eight.  out: [0] floats
+// checked, [1] float->double mismatches, [2] doubles with ok set, [3] their
+// mismatches, [4] doubles whose ok flag disagrees with the stated range.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_check_conversions(unsigned long long* out)
+{
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const double lo_ok = __longlong_as_double(0x3810000000000000ll);  // 2^-126
+    const double hi_ok = __longlong_as_double(0x47f0000000000000ll);  // 2^128
+    for (unsigned long long v = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; v < (1ull << 32);
+         v += stride) {
+        const float f = __uint_as_float((unsigned)v);
+        const double hw = (double)f, sw = f2d_exact(f);
+        c[0] += 1;
+        if (hw != hw ? sw == sw : __double_as_longlong(hw) != __double_as_longlong(sw)) c[1] += 1;
+
+        const unsigned long long h = splitmix64(v), r = splitmix64(v ^ 0x5851f42d4c957f2dull);
+        const unsigned sel = (unsigned)(h >> 55);
+        // exponent fields 893 .. 1152 (float's range and two beyond each end) or
+        // one of: zero/subnormal, smallest normal, largest finite, inf/NaN, 1.0,
+        // and three far outside float's range
+        const unsigned spec[8] = {0u, 1u, 2046u, 2047u, 1023u, 960u, 700u, 1300u};
+        const unsigned long long ex = sel < 260u ? 893u + sel : spec[sel & 7u];
+        unsigned long long fr = r & 0xfffffffffffffull;
+        const unsigned long long edge[5] = {0ull, 0x0fffffffull, 0x10000000ull, 0x10000001ull, 0x1fffffffull};
+        if ((v & 7u) < 5u) fr = (fr & ~0x1fffffffull) | edge[v & 7u];
+        const double x = __longlong_as_double((long long)(((h & 1ull) << 63) | (ex << 52) | fr));
+        bool ok;
+        const float s = d2f_rn_int(x, ok);
+        const bool want = x == 0.0 || (fabs(x) >= lo_ok && fabs(x) < hi_ok);
+        if (ok != want) c[4] += 1;
+        if (ok) {
+            c[2] += 1;
+            if (__float_as_uint(s) != __float_as_uint((float)x)) c[3] += 1;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        unsigned long long t = c[q];
+        for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(out + q, t);
+    }
 }
 
 __global__ void k_set_scalar(double* dst, double v)

@@ -86,6 +86,9 @@ def test_more_validation_without_gpu(built):
                   p) == _lib.CFD_EINVAL                                                               # unknown BC
     q = _lib.default_params(metric_mode=2)
     assert create(_lib.make_grid(8, 8, 8, metric_layout=_lib.METRICS_UNIFORM), q) == _lib.CFD_EINVAL  # unknown mode
+    # an x-y plane of 2^31 nodes or more (plane offsets are 32-bit)
+    assert create(_lib.make_grid(1 << 16, 1 << 15, 1, metric_layout=_lib.METRICS_UNIFORM), p) == _lib.CFD_EINVAL
+    assert b"nx * ny" in L.cfd_last_error(None)
     q = _lib.default_params(metric_mode=_lib.METRIC_FSP)                                   # FSP needs periodic lines
     g = _lib.make_grid(8, 8, 8, bc_lo=(3, 0, 0), bc_hi=(3, 0, 0), metric_layout=_lib.METRICS_UNIFORM)
     assert create(g, q) == _lib.CFD_EUNSUPPORTED

@@ -166,3 +166,21 @@ def test_mixed_is_deterministic(orc):
         s.step(1e-3, 5)
         B = s.get_state()
     assert np.array_equal(A, B)
+
+
+def test_integer_pipe_conversions_match_hardware():
+    """The mixed form rounds the FP64 state to float and widens float
+    residuals to double with integer operations; on the device they agree
+    bit for bit with the hardware conversion on every float and on 2^32
+    doubles that sweep float's exponent range and the rounding edges, and
+    the double -> float path accepts exactly zero and 2^-126 <= |x| < 2^128."""
+    from paper_2209_15333_gb300 import _lib
+    c = _lib.check_conversions()
+    print(c)
+    assert c["floats"] == 1 << 32
+    assert c["f2d_mismatch"] == 0
+    # about 260/512 of the draws fall in float's range (exponent sweep) and
+    # the special exponents add a few more
+    assert c["doubles_ok"] > 0.45 * (1 << 32)
+    assert c["d2f_mismatch"] == 0
+    assert c["ok_flag_wrong"] == 0

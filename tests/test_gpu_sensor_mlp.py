@@ -80,19 +80,36 @@ def test_features_match_definition(precision):
     assert np.abs(F - ref).max() <= tol * max(1.0, np.abs(ref).max())
 
 
-# (precision, shape, x boundary): FP32 rows on 16-byte boundaries take the
-# TMA-staged kernel (a partial last tile and clamped line ends in the second
-# case), a ragged FP32 row and the FP64 form take the other kernel
-MLP_CASES = [(0, (40, 24, 20), 0), (1, (40, 24, 20), 0), (1, (132, 12, 10), 3), (1, (37, 16, 12), 3)]
+def steep_field(sh, seed):
+    """turbulence_field with p and rho scaled by tanh steps across z and x
+    (width 1.5 nodes), so that the features of the finer lines still span
+    several classes of the random network"""
+    U = turbulence_field(sh, seed)
+    nx, ny, nz = sh
+    k = np.arange(nz)[:, None, None]
+    i = np.arange(nx)[None, None, :]
+    s = 1.0 + 0.25 * np.tanh((k - 0.5 * nz) / 1.5) + 0.15 * np.tanh((i - 0.4 * nx) / 1.5)
+    u, v, w = U[1] / U[0], U[2] / U[0], U[3] / U[0]
+    p = 0.4 * (U[4] - 0.5 * U[0] * (u * u + v * v + w * w))
+    return cases.conserved(U[0] * s, u, v, w, p * s, 1.4)
 
 
-@pytest.mark.parametrize("precision,sh,xbc", MLP_CASES)
-def test_mlp_classes_match_numpy_forward_pass(precision, sh, xbc):
+# (precision, shape, x and z boundaries): the kernel walks zeta in 32 x 8
+# (x, y) columns over segments of at most 64 planes; these shapes leave
+# partial columns in x and y and a ragged last segment, and the clamped x and
+# z line ends of non-periodic faces (3: outflow) fall inside a column or a
+# segment; the first case runs the FP64 form
+MLP_CASES = [(0, (40, 24, 20), 0, 0), (1, (40, 24, 20), 0, 0), (1, (132, 12, 10), 3, 0), (1, (37, 16, 12), 3, 0),
+             (1, (45, 13, 27), 0, 3), (1, (33, 9, 70), 3, 3)]
+
+
+@pytest.mark.parametrize("precision,sh,xbc,zbc", MLP_CASES)
+def test_mlp_classes_match_numpy_forward_pass(precision, sh, xbc, zbc):
     from paper_2209_15333_gb300.solver import Solver
-    U = turbulence_field(sh, 92)
+    U = turbulence_field(sh, 92) if zbc == 0 else steep_field(sh, 92)
     W = random_weights(5)
-    with Solver(sh, cases.uniform_metrics(*sh), precision=precision, scheme=3, Re=100.0, bc_lo=(xbc, 0, 0),
-                bc_hi=(xbc, 0, 0)) as s:
+    with Solver(sh, cases.uniform_metrics(*sh), precision=precision, scheme=3, Re=100.0, bc_lo=(xbc, 0, zbc),
+                bc_hi=(xbc, 0, zbc)) as s:
         s.set_state(U)
         F = s.sensor_features()
         s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=0.0)
