@@ -449,12 +449,24 @@ def run_ensemble(args, world):
     ms, launches = timed_steps(bs, stream, dt, args.steps, world)
     prof = bs.profile_stage(3)
     variants = bs.batch_variants() if hasattr(bs, "batch_variants") else None
+    # the same ensemble with the learned sensor (one batched launch per stage)
+    set_learned_sensor(bs)
+    for _ in range(args.warmup):
+        bs.step(dt, 1)
+    bs.sync(600.0)
+    bs.sensor_fallbacks()  # reset the counter
+    ms_l, launches_l = timed_steps(bs, stream, dt, args.steps, world)
+    learned = {"value": job_throughput(world, nodes, args.steps, ms_l * 1e-3), "unit": "point-stage/s",
+               "ms_per_step": ms_l / args.steps, "gpu_launches": launches_l,
+               "fallback_fraction": bs.sensor_fallbacks() / (3.0 * args.steps * nodes),
+               "kernel_ms": bs.profile_stage(3)}
     bs.close()
     return {"workload": "48 periodic isotropic-turbulence blocks, dims i.i.d. from {32,48,64,96,128}, "
                         "Mt in [0.3,0.7], hybrid, viscous, FP32 bulk / FP64 state",
             "nodes": nodes, "value": job_throughput(world, nodes, args.steps, ms * 1e-3), "unit": "point-stage/s",
             "ms_per_step": ms / args.steps, "gpu_launches": launches,
-            "launches_per_step": launches / max(1, args.steps), "kernel_ms": prof, "kernel_variants": variants}
+            "launches_per_step": launches / max(1, args.steps), "kernel_ms": prof, "kernel_variants": variants,
+            "learned_sensor": learned}
 
 
 def kernel_traffic(form, dom, variants, N, src_hash):

@@ -193,7 +193,9 @@ cfd_status cfd_set_blowing(cfd_ctx* ctx, double amp, double x0, double x1, doubl
  * the plain sensor's class.  weights_bf16: W1[32][42], W2[32][32],
  * W3[3][32] (row = output), as consecutive bf16 (uint16) arrays; biases:
  * b1[32], b2[32], b3[3] float.  NULL weights switch back to the plain
- * sensor.  Single-block contexts only (CFD_EUNSUPPORTED for ensembles).
+ * sensor.  On an ensemble the weights apply to every block: one launch per
+ * stage walks the zeta columns of all blocks, and cfd_sensor_fallbacks
+ * counts the fallbacks of the ensemble's steps over all blocks.
  */
 cfd_status cfd_set_sensor_mlp(cfd_ctx* ctx, const void* weights_bf16, const float* biases,
                               float conf_min);

@@ -28,6 +28,18 @@ constexpr int kSMs = 152;
 enum { KIND_VISC = 0, KIND_SX = 1, KIND_T1 = 2, KIND_T2 = 3, KIND_COUNT = 4 };
 constexpr int kBatchVariants = 3;
 constexpr int kBatchWS = 64;
+// work-list maps of an ensemble, one per kernel kind and variant (see
+// batch_tiles), and the learned sensor's zeta columns
+enum {
+    MAP_NODE = 0,
+    MAP_VISC = 1,  // + variant (3)
+    MAP_SX = 4,    // + variant (3)
+    MAP_T1 = 7,    // + variant (3)
+    MAP_T2 = 10,   // + variant (3)
+    MAP_MLP = 13,
+    MAP_COUNT = 14
+};
+constexpr int kBatchMlpTZ = 16;  // planes per zeta segment of the ensemble's learned sensor
 
 struct Bufs {
     double* U = nullptr;      // [5][N] state U^n
@@ -68,8 +80,8 @@ struct cfd_ctx {
     std::vector<cfd_ctx*> sub;
     SweepArgs* d_tbl[3] = {nullptr, nullptr, nullptr};  // per stage, [nb]
     int* d_maps = nullptr;                              // all prefix / gdim arrays
-    BatchMap maps[3][13];                               // [stage][kernel kind and variant]
-    int map_grid[13] = {};                              // persistent grid per map
+    BatchMap maps[3][MAP_COUNT];        // [stage][kernel kind and variant]
+    int map_grid[MAP_COUNT] = {};       // persistent grid per map
     int bvar[4] = {0, 0, 0, 0};                         // chosen variant per kind (viscous, xi, eta, zeta)
     // multi-block halo links: [0] between the U arrays, [1] between the Uk
     // arrays; per direction
@@ -1204,14 +1216,6 @@ extern "C" cfd_status cfd_rhs(cfd_ctx* ctx, int block, double* dUdt, int on_devi
 // xi sweep in segments of 64 / 128 nodes or walking whole lines; eta and zeta
 // sweeps in 16- / 32-node tiles or walking 64-node segments.  The autotuner
 // picks one variant per kind on the live ensemble (all give the same bits).
-enum {
-    MAP_NODE = 0,
-    MAP_VISC = 1,  // + variant (3)
-    MAP_SX = 4,    // + variant (3)
-    MAP_T1 = 7,    // + variant (3)
-    MAP_T2 = 10,   // + variant (3)
-    MAP_COUNT = 13
-};
 
 static void batch_tiles(const Geo& g, int map, int out[3])
 {
@@ -1220,6 +1224,10 @@ static void batch_tiles(const Geo& g, int map, int out[3])
         const int n = d == 0 ? g.nx : (d == 1 ? g.ny : g.nz);
         return std::max(1, g.per[d] ? n : n - 2);
     };
+    if (map == MAP_MLP) {  // 32 x 8 columns walking zeta segments
+        out[0] = cdiv(g.nx, 32); out[1] = cdiv(g.ny, 8); out[2] = cdiv(g.nz, kBatchMlpTZ);
+        return;
+    }
     const int kind = map == MAP_NODE ? -1 : (map - 1) / kBatchVariants, var = (map - 1) % kBatchVariants;
     if (kind < 0) {
         out[0] = (int)((g.N + 127) / 128); out[1] = 1; out[2] = 1;  // flat node runs
@@ -1255,6 +1263,7 @@ static cudaError_t batch_kernel_attrs()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, carve, maxs);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM>, carve, maxs);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp<R>, dyn, (int)sizeof(MlpWalkSmem));
     return e;
 }
 
@@ -1288,6 +1297,7 @@ static void batch_grids(cfd_ctx* ctx, const int totals[MAP_COUNT])
     mg[MAP_T2 + 0] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 16>, 256, tile_smem_bytes<R, 16>(), totals[MAP_T2 + 0]);
     mg[MAP_T2 + 1] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T2 + 1]);
     mg[MAP_T2 + 2] = persistent_grid(kb_sweep_w<R, 2, EP_FINAL_RK>, 256, walk_smem_bytes<R>(), totals[MAP_T2 + 2]);
+    mg[MAP_MLP] = persistent_grid(kb_sensor_mlp<R>, 256, sizeof(MlpWalkSmem), totals[MAP_MLP]);
 }
 
 static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids, const double* const* metrics,
@@ -1520,8 +1530,15 @@ static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
     LAUNCH_CHECK();
     if (ev) cudaEventRecord(ev[1], st);
     if (mixed || ctx->prm.scheme == CFD_HYBRID) {
-        if (mixed) kb_sensor32<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
-        else kb_sensor<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+        if (ctx->prm.sensor == CFD_SENSOR_MLP) {
+            if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
+            kb_sensor_mlp<R><<<ctx->map_grid[MAP_MLP], 256, sizeof(MlpWalkSmem), st>>>(m[MAP_MLP], ctx->mlp,
+                                                                                       kBatchMlpTZ);
+        } else if (mixed) {
+            kb_sensor32<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+        } else {
+            kb_sensor<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+        }
         LAUNCH_CHECK();
     }
     if (ev) cudaEventRecord(ev[2], st);
@@ -2152,7 +2169,15 @@ extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* pa
 extern "C" cfd_status cfd_set_sensor_mlp(cfd_ctx* ctx, const void* weights_bf16, const float* biases, float conf_min)
 {
     if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
-    if (!ctx->sub.empty()) return fail(ctx, CFD_EUNSUPPORTED, "the learned sensor is per single-block context");
+    // an ensemble: every block gets the weights (its per-block calls run on
+    // the block's own context), the ensemble's step uses its own copy
+    for (cfd_ctx* sb : ctx->sub) {
+        const cfd_status st = cfd_set_sensor_mlp(sb, weights_bf16, biases, conf_min);
+        if (st != CFD_OK) {
+            ctx->msg = sb->msg;
+            return st;
+        }
+    }
     if (!weights_bf16 || !biases) {
         ctx->mlp_on = false;
         ctx->prm.sensor = CFD_SENSOR_PLAIN;

@@ -634,128 +634,117 @@ __device__ __forceinline__ void mlp_stage_weights(MlpWeightsSmem& S, const MlpAr
     for (int e = t; e < 72; e += nt) S.sb[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
 }
 
-// one node's 42 features as a bf16 row of a feature tile; the row is all
-// zero and true is returned if the node is not owned or a feature is not finite
-__device__ __forceinline__ bool mlp_put_row(uint16_t* row16, bool own, const float f[MLP_IN])
+// four (two) 8 x 8 bf16 matrices from shared memory in the mma fragment
+// layout: lane L gives the address of row L mod 8 of matrix L / 8
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p)
 {
-    bool bad = !own;
-    if (own) {
-        // one test for all 42: x * 0 is 0 for finite x and NaN otherwise
-        float z = 0.0f;
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+// ReLU on a packed pair of bf16 (max with +0; a NaN gives 0)
+__device__ __forceinline__ uint32_t relu_bf16x2(uint32_t x)
+{
+    uint32_t r;
+    asm("max.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(0u));
+    return r;
+}
+
+// accumulator fragments of a [16 x 32] layer output, biases as the initial
+// value, to bf16 pairs with ReLU: the A fragments of the next layer
+__device__ __forceinline__ void mlp_hidden_init(float h[4][4], const float* bias)
+{
+    const int tig = threadIdx.x & 3;
 #pragma unroll
-        for (int e = 0; e < MLP_IN; ++e) z = fmaf(f[e], 0.0f, z);
-        bad = !(z == 0.0f);
+    for (int nt = 0; nt < 4; ++nt) {
+        const float2 b = *reinterpret_cast<const float2*>(bias + nt * 8 + tig * 2);
+        h[nt][0] = b.x, h[nt][1] = b.y, h[nt][2] = b.x, h[nt][3] = b.y;
     }
-    uint32_t* row = reinterpret_cast<uint32_t*>(row16);
+}
+__device__ __forceinline__ void mlp_hidden_pack(const float h[4][4], uint32_t a[2][4])
+{
 #pragma unroll
-    for (int e = 0; e < MLP_KP; e += 2) {
-        const float a = (!bad && e < MLP_IN) ? f[e] : 0.0f;
-        const float b = (!bad && e + 1 < MLP_IN) ? f[e + 1] : 0.0f;
-        row[e / 2] = pack_bf16x2(a, b);
+    for (int nt = 0; nt < 4; ++nt) {
+        a[nt >> 1][(nt & 1) * 2 + 0] = relu_bf16x2(pack_bf16x2(h[nt][0], h[nt][1]));
+        a[nt >> 1][(nt & 1) * 2 + 1] = relu_bf16x2(pack_bf16x2(h[nt][2], h[nt][3]));
     }
-    return bad;
 }
 
 // The three layers on the tensor cores for the 32 rows of one warp's feature
 // tile sx (rows 0..31, stride MLP_ROW); every lane gets the class of row
 // `lane`, -1 where the top softmax probability is below conf_min (or not
-// finite).  Warp-synchronous: the caller orders the rows' writes before it
-// (__syncwarp) and any rewrite after it.
+// finite).  Fragments come from shared memory by ldmatrix, biases enter as
+// the accumulators' initial values.  Warp-synchronous: the caller orders the
+// rows' writes before it (__syncwarp) and any rewrite after it.
 __device__ __forceinline__ int mlp_classify_warp(const uint16_t* sx, const MlpWeightsSmem& S, float conf_min)
 {
     const int lane = threadIdx.x & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    int cls_row[2][2];  // [m-tile][row half]
+    const int tig = lane & 3;
+    // ldmatrix row addresses: A (rows lane mod 16, k half lane / 16); B pairs
+    // of n-tiles (n row lane mod 8 + 8 (lane / 16), k half (lane / 8) mod 2);
+    // layer 3 (n row lane mod 8, k eighth lane / 8)
+    const uint16_t* arow = sx + (lane & 15) * MLP_ROW + (lane >> 4) * 8;
+    const int bn = (lane & 7) + ((lane >> 4) << 3), bk = ((lane >> 3) & 1) * 8;
+    const uint16_t* b1row = S.sw1 + bn * MLP_ROW + bk;
+    const uint16_t* b2row = S.sw2 + bn * 40 + bk;
+    // row L = 16 mt + 8 half + g: its logits 0, 1 sit in lg[2 half], lg[2 half + 1]
+    // of lane 4 g after m-tile mt, logit 2 in lg[2 half] of lane 4 g + 1
+    const int g4 = (lane & 7) * 4, my_mt = lane >> 4, half = (lane >> 3) & 1;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-        const int r0 = mt * 16 + gid;  // rows r0 and r0 + 8
         // layer 1: [16 x 48] x [48 x 32]
         float h1[4][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) h1[nt][e] = 0.0f;
+        mlp_hidden_init(h1, S.sb);
 #pragma unroll
         for (int ks = 0; ks < 3; ++ks) {
             uint32_t a[4];
-            const int c = ks * 16 + tig * 2;
-            a[0] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c);
-            a[1] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c);
-            a[2] = *reinterpret_cast<const uint32_t*>(sx + r0 * MLP_ROW + c + 8);
-            a[3] = *reinterpret_cast<const uint32_t*>(sx + (r0 + 8) * MLP_ROW + c + 8);
+            ldsm_x4(a, arow + mt * 16 * MLP_ROW + ks * 16);
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                uint32_t b[2];
-                const int nn = nt * 8 + gid;
-                b[0] = *reinterpret_cast<const uint32_t*>(S.sw1 + nn * MLP_ROW + c);
-                b[1] = *reinterpret_cast<const uint32_t*>(S.sw1 + nn * MLP_ROW + c + 8);
-                mma_bf16_16816(h1[nt], a, b);
+            for (int np = 0; np < 2; ++np) {
+                uint32_t b[4];
+                ldsm_x4(b, b1row + np * 16 * MLP_ROW + ks * 16);
+                mma_bf16_16816(h1[2 * np], a, b);
+                mma_bf16_16816(h1[2 * np + 1], a, b + 2);
             }
         }
-        // bias + ReLU, and the accumulator layout becomes the next A operand
         uint32_t a2[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const float bb0 = S.sb[nt * 8 + tig * 2], bb1 = S.sb[nt * 8 + tig * 2 + 1];
-            a2[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16x2(fmaxf(h1[nt][0] + bb0, 0.0f), fmaxf(h1[nt][1] + bb1, 0.0f));
-            a2[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2(fmaxf(h1[nt][2] + bb0, 0.0f), fmaxf(h1[nt][3] + bb1, 0.0f));
-        }
+        mlp_hidden_pack(h1, a2);
         // layer 2: [16 x 32] x [32 x 32]
         float h2[4][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) h2[nt][e] = 0.0f;
+        mlp_hidden_init(h2, S.sb + 32);
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
-            const int c = ks * 16 + tig * 2;
 #pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                uint32_t b[2];
-                const int nn = nt * 8 + gid;
-                b[0] = *reinterpret_cast<const uint32_t*>(S.sw2 + nn * 40 + c);
-                b[1] = *reinterpret_cast<const uint32_t*>(S.sw2 + nn * 40 + c + 8);
-                mma_bf16_16816(h2[nt], a2[ks], b);
+            for (int np = 0; np < 2; ++np) {
+                uint32_t b[4];
+                ldsm_x4(b, b2row + np * 16 * 40 + ks * 16);
+                mma_bf16_16816(h2[2 * np], a2[ks], b);
+                mma_bf16_16816(h2[2 * np + 1], a2[ks], b + 2);
             }
         }
         uint32_t a3[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const float bb0 = S.sb[32 + nt * 8 + tig * 2], bb1 = S.sb[32 + nt * 8 + tig * 2 + 1];
-            a3[nt >> 1][(nt & 1) * 2 + 0] = pack_bf16x2(fmaxf(h2[nt][0] + bb0, 0.0f), fmaxf(h2[nt][1] + bb1, 0.0f));
-            a3[nt >> 1][(nt & 1) * 2 + 1] = pack_bf16x2(fmaxf(h2[nt][2] + bb0, 0.0f), fmaxf(h2[nt][3] + bb1, 0.0f));
-        }
+        mlp_hidden_pack(h2, a3);
         // layer 3: [16 x 32] x [32 x 8] (3 logits used)
-        float lg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const float2 b3 = *reinterpret_cast<const float2*>(S.sb + 64 + tig * 2);
+        float lg[4] = {b3.x, b3.y, b3.x, b3.y};
+        uint32_t b[4];
+        ldsm_x4(b, S.sw3 + (lane & 7) * 40 + (lane >> 3) * 8);
+        mma_bf16_16816(lg, a3[0], b);
+        mma_bf16_16816(lg, a3[1], b + 2);
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            const int c = ks * 16 + tig * 2;
-            uint32_t b[2];
-            b[0] = *reinterpret_cast<const uint32_t*>(S.sw3 + gid * 40 + c);
-            b[1] = *reinterpret_cast<const uint32_t*>(S.sw3 + gid * 40 + c + 8);
-            mma_bf16_16816(lg, a3[ks], b);
-        }
-        // logits of row r0 (lg[0..1]) and r0+8 (lg[2..3]) sit in columns 2 tig, 2 tig + 1:
-        // every lane of the quad gathers columns 0, 1, 2 from its first two lanes
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const float c0 = __shfl_sync(0xffffffffu, lg[2 * half], lane & ~3);
-            const float c1 = __shfl_sync(0xffffffffu, lg[2 * half + 1], lane & ~3);
-            const float c2 = __shfl_sync(0xffffffffu, lg[2 * half], (lane & ~3) + 1);
-            const float l0 = c0 + S.sb[64], l1 = c1 + S.sb[65], l2 = c2 + S.sb[66];
-            const float mx = fmaxf(l0, fmaxf(l1, l2));
-            const float z = __expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx);
-            const int arg = l0 >= l1 ? (l0 >= l2 ? 0 : 2) : (l1 >= l2 ? 1 : 2);
-            cls_row[mt][half] = (1.0f / z >= conf_min && isfinite(z)) ? arg : -1;
+        for (int h = 0; h < 2; ++h) {
+            const float x0 = __shfl_sync(0xffffffffu, lg[2 * h], g4);
+            const float x1 = __shfl_sync(0xffffffffu, lg[2 * h + 1], g4);
+            const float x2 = __shfl_sync(0xffffffffu, lg[2 * h], g4 + 1);
+            if (mt == my_mt && h == half) c0 = x0, c1 = x1, c2 = x2;
         }
     }
-    // row L was classified by the quad of lanes 4 (L mod 8) .. 4 (L mod 8) + 3
-    // as cls_row[L / 16][(L / 8) mod 2]
-    const int src = (lane & 7) * 4;
-    const int c00 = __shfl_sync(0xffffffffu, cls_row[0][0], src), c01 = __shfl_sync(0xffffffffu, cls_row[0][1], src);
-    const int c10 = __shfl_sync(0xffffffffu, cls_row[1][0], src), c11 = __shfl_sync(0xffffffffu, cls_row[1][1], src);
-    const int half = (lane >> 3) & 1;
-    return lane < 16 ? (half ? c01 : c00) : (half ? c11 : c10);
+    const float mx = fmaxf(c0, fmaxf(c1, c2));
+    const float z = __expf(c0 - mx) + __expf(c1 - mx) + __expf(c2 - mx);
+    const int arg = c0 >= c1 ? (c0 >= c2 ? 0 : 2) : (c1 >= c2 ? 1 : 2);
+    return (1.0f / z >= conf_min && isfinite(z)) ? arg : -1;
 }
 
 // Learned sensor, walking form.  A CTA of 8 warps owns a 32 x 8 (x, y) column
@@ -763,7 +752,7 @@ __device__ __forceinline__ int mlp_classify_warp(const uint16_t* sx, const MlpWe
 // 3-node x/y halo (38 x 14 values, periodic lines wrapped, others clamped as
 // the features define), are loaded once into a ring of 8 planes in shared
 // memory; the next plane's loads are issued before the current plane's
-// features and layers and stored into the ring after them.  The features of
+// features and stored into the ring after them.  The features of
 // plane z come from the ring: x and y lines from plane z, zeta lines from
 // planes z-3 .. z+3.  Warp w holds the nodes of y-row w and classifies its
 // own 32 feature rows, so the only CTA barrier per plane orders the ring:
@@ -777,20 +766,20 @@ struct MlpWalkSmem {
     MlpWeightsSmem w;
 };
 
+// one column's walk (vb: column x, column y, zeta segment); the weights are
+// staged in S.w before the call
 template <class RT>
-__global__ void __launch_bounds__(256, 3) k_sensor_mlp(SweepArgs A, MlpArgs W, int tz)
+__device__ __forceinline__ void sensor_mlp_col(const SweepArgs& A, const MlpArgs& W, MlpWalkSmem& S, uint3 vb,
+                                               int tz)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    MlpWalkSmem& S = *reinterpret_cast<MlpWalkSmem*>(smem_raw);
     const Geo& g = A.g;
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const long long N = g.N, plane = (long long)nx * ny;
     const RT* Pp = (const RT*)A.P + 4 * N;
     const RT* Pr = (const RT*)A.P;
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
-    const int z0 = blockIdx.z * tz, z1 = min(z0 + tz, nz);
-    mlp_stage_weights(S.w, W);
+    const int x0 = vb.x * 32, y0 = vb.y * 8;
+    const int z0 = vb.z * tz, z1 = min(z0 + tz, nz);
     // the staged positions of this thread (t, t + 256, t + 512 of the 532)
     // and their offsets within a plane, the same for every plane
     int poff[3];
@@ -834,23 +823,46 @@ __global__ void __launch_bounds__(256, 3) k_sensor_mlp(SweepArgs A, MlpArgs W, i
         const bool more = z + 4 <= z1 + 2;
         float nxt[3][2];
         if (more) load_plane(z + 4, nxt);
-        float f[MLP_IN];
+        // the 42 features in order (direction, field, position), packed to
+        // bf16 pairs and stored 8 at a time as they are produced; one test of
+        // finiteness for all (x * 0 is 0 for finite x, NaN otherwise)
+        const float* c0 = S.ring[z & (MW_RING - 1)][0];
+        const float inv[2] = {1.0f / c0[ctr], 1.0f / c0[MW_PL + ctr]};
+        uint4* row = reinterpret_cast<uint4*>(sxw + tx * MLP_ROW);
+        float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        uint32_t w[4];
+        float lo = 0.0f;
 #pragma unroll
-        for (int fld = 0; fld < 2; ++fld) {
-            const float* c = S.ring[z & (MW_RING - 1)][fld];
-            const float inv = 1.0f / c[ctr];
-            float v[7];
+        for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int q = 0; q < 7; ++q) v[q] = c[ctr + q - 3];
-            mlp_feature_line_inv(v, inv, f + fld * 7);
+            for (int fld = 0; fld < 2; ++fld) {
+                const float* c = c0 + fld * MW_PL;
+                float v[7], o[7];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) v[q] = c[ctr + (q - 3) * MW_X];
-            mlp_feature_line_inv(v, inv, f + (2 + fld) * 7);
+                for (int q = 0; q < 7; ++q)
+                    v[q] = d == 0 ? c[ctr + q - 3]
+                                  : (d == 1 ? c[ctr + (q - 3) * MW_X]
+                                            : S.ring[(z + q - 3) & (MW_RING - 1)][fld][ctr]);
+                mlp_feature_line_inv(v, inv[fld], o);
 #pragma unroll
-            for (int q = 0; q < 7; ++q) v[q] = S.ring[(z + q - 3) & (MW_RING - 1)][fld][ctr];
-            mlp_feature_line_inv(v, inv, f + (4 + fld) * 7);
+                for (int q = 0; q < 7; ++q) {
+                    const int e = (2 * d + fld) * 7 + q;
+                    zc[e & 3] = fmaf(o[q], 0.0f, zc[e & 3]);
+                    if (e & 1) w[(e >> 1) & 3] = pack_bf16x2(lo, o[q]);
+                    else lo = o[q];
+                    if ((e & 7) == 7) row[e >> 3] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+        // features 42..47 are zero padding
+        w[1] = pack_bf16x2(lo, 0.0f);
+        row[5] = make_uint4(w[0], w[1], 0u, 0u);
+        // plane z+4 takes the slot of plane z-4 (no reader since the last barrier)
+        if (more) store_plane(z + 4, nxt);
+        const bool bad = !own || !((zc[0] + zc[1]) + (zc[2] + zc[3]) == 0.0f);
+        if (bad) {
+#pragma unroll
+            for (int q = 0; q < MLP_KP / 8; ++q) row[q] = make_uint4(0u, 0u, 0u, 0u);
         }
-        const bool bad = mlp_put_row(sxw + tx * MLP_ROW, own, f);
         __syncwarp();
         const int cls = mlp_classify_warp(sxw, S.w, W.conf_min);
         if (own) {
@@ -862,9 +874,17 @@ __global__ void __launch_bounds__(256, 3) k_sensor_mlp(SweepArgs A, MlpArgs W, i
             }
             A.cls_io[n] = (uint8_t)c;
         }
-        if (more) store_plane(z + 4, nxt);
         __syncthreads();
     }
+}
+
+template <class RT>
+__global__ void __launch_bounds__(256, 2) k_sensor_mlp(SweepArgs A, MlpArgs W, int tz)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpWalkSmem& S = *reinterpret_cast<MlpWalkSmem*>(smem_raw);
+    mlp_stage_weights(S.w, W);
+    sensor_mlp_col<RT>(A, W, S, blockIdx, tz);
 }
 
 // the 42 features of every node (for training data and tests), [42][N] float
@@ -2402,9 +2422,9 @@ template <int DIR, int EP>
 __device__ __forceinline__ void sweep_wt_body(const SweepArgs& A, const TmaRowMaps& maps, uint3 vb)
 {
     using R = float;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* stage = smem_raw;                                   // [NBUF][8][1280]
-    R* sf = reinterpret_cast<R*>(smem_raw + TW_NBUF * TW_GROUP);        // rings as in sweep_w_body
+    extern __shared__ __align__(128) unsigned char smem_tw[];
+    unsigned char* stage = smem_tw;                                    // [NBUF][8][1280]
+    R* sf = reinterpret_cast<R*>(smem_tw + TW_NBUF * TW_GROUP);         // rings as in sweep_w_body
     R* ss = sf + WS_RING * 10 * 32;
     R* sv = ss + WS_RING * 32;
     R* sh = sv + WV_RING * 4 * 32;
@@ -3126,6 +3146,17 @@ __global__ void kb_prim(BatchMap m) { BATCH_LOOP((prim_body<RT, true>), false, t
 __global__ void kb_prim_mixed(BatchMap m) { BATCH_LOOP(prim_mixed_body<true>, false, true) }
 __global__ void kb_sensor(BatchMap m) { BATCH_LOOP(sensor_body<true>, false, true) }
 __global__ void kb_sensor32(BatchMap m) { BATCH_LOOP(sensor32_body<true>, false, true) }
+// the learned sensor over an ensemble: items are (column x, column y, zeta
+// segment of tz planes) of every block; the weights are staged once per CTA
+template <class RT>
+__global__ void __launch_bounds__(256, 2) kb_sensor_mlp(BatchMap m, MlpArgs W, int tz)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpWalkSmem& S = *reinterpret_cast<MlpWalkSmem*>(smem_raw);
+    mlp_stage_weights(S.w, W);
+    auto body = [&](const SweepArgs& A, uint3 v) { sensor_mlp_col<RT>(A, W, S, v, tz); };
+    BATCH_LOOP(body, true, false)
+}
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((visc25_body<R, TZ>), true, false) }
 template <class R>

@@ -72,6 +72,46 @@ def test_batch_matches_single_block_contexts(orc, precision):
             assert field_rel_err(got[b], Uo) <= 1e-11
 
 
+def _mlp_weights(seed):
+    rng = np.random.default_rng(seed)
+    return (rng.normal(0, 10.0, (32, 42)), rng.normal(0, 0.5, (32, 32)), rng.normal(0, 0.5, (3, 32)),
+            rng.normal(0, 0.1, 32), rng.normal(0, 0.1, 32), rng.normal(0, 0.1, 3))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_learned_sensor_matches_single_block_contexts(precision):
+    """The learned sensor in an ensemble (one launch walks the zeta columns
+    of all blocks, with partial columns, clamped lines and ragged segments)
+    gives every block the classes, fallbacks and state of its own context."""
+    from paper_2209_15333_gb300.solver import BatchSolver, Solver
+    mets, params, states = _blocks(precision)
+    W = _mlp_weights(11)
+    dt = 5e-4
+    with BatchSolver(SHAPES, mets, params, bcs=BCS) as bs:
+        for b, U in enumerate(states):
+            bs.set_state(U, block=b)
+        bs.set_sensor_mlp(*W, conf_min=0.6)
+        bs.sensor_fallbacks()
+        bs.step(dt, 3)
+        got = [bs.get_state(block=b) for b in range(len(SHAPES))]
+        cls = [bs.flags(block=b) for b in range(len(SHAPES))]
+        fb = bs.sensor_fallbacks()
+    fb_ref = 0
+    kinds = set()
+    for b, sh in enumerate(SHAPES):
+        lo, hi = BCS[b]
+        with Solver(sh, mets[b], bc_lo=lo, bc_hi=hi, **params[b]) as s:
+            s.set_state(states[b])
+            s.set_sensor_mlp(*W, conf_min=0.6)
+            s.step(dt, 3)
+            assert np.array_equal(s.flags(), cls[b]), b
+            assert np.array_equal(s.get_state(), got[b]), b
+            fb_ref += s.sensor_fallbacks()
+        kinds |= set(np.unique(cls[b]).tolist())
+    assert fb == fb_ref and fb > 0
+    assert len(kinds) >= 2
+
+
 # ensemble variants as (kind, param): viscous (dir 0), xi (dir 3), eta/zeta (dirs 1, 2)
 VISC_V = [(2, 32), (1, 64), (3, 0)]
 XI_V = [(0, 64), (0, 128), (1, 0)]
