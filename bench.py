@@ -53,10 +53,11 @@ MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_
 # the new state (40 B); metrics are constant on the uniform box.
 ALG_BYTES_PER_POINT_STAGE = 40.0 + 80.0 / 3.0 + 40.0
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the full 256^3 workload, one launch of the named
-# kernel in the variant it ran in; valid only for the kernel sources with this
-# hash prefix.
-NCU_TRAFFIC = {"src": None, "fp64": {}, "mixed": {}}
+# dram__bytes_write.sum) on the full 256^3 workload ("nodes"), one launch of
+# each kernel per variant (dir:kind:param as cfd_get_sweep_variant reports
+# it; the RHS epilogue for zeta, as cfd_profile_stage runs it); valid only
+# for the kernel sources with hash prefix "src".
+NCU_TRAFFIC = {"src": None, "nodes": 256 ** 3, "fp64": {}, "mixed": {}}
 
 
 def parse():
@@ -351,7 +352,8 @@ def run_form(args, form, U, met, params, world, local, dt):
         s.get_state(out=host_out)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     prof = s.profile_stage(3)
-    variants = {"visc": s.sweep_variant(0), "eta": s.sweep_variant(1), "zeta": s.sweep_variant(2)}
+    variants = {"visc": s.sweep_variant(0), "xi": s.sweep_variant(3), "eta": s.sweep_variant(1),
+                "zeta": s.sweep_variant(2)}
     s.close()
     r = dict(value=value, ms=ms, launches=launches, clocks=clk, class_fraction=[float(x) for x in frac],
              e2e=job_throughput(world, N, args.steps, e2e_s), prof=prof, U1=U1, variants=variants)
@@ -469,14 +471,17 @@ def run_ensemble(args, world):
             "learned_sensor": learned}
 
 
-def kernel_traffic(form, dom, variants, N, src_hash):
+def kernel_traffic(form, dom, variant, N, src_hash):
+    """ncu DRAM bytes of one launch of kernel `dom` in the variant that ran,
+    scaled from the captured workload's nodes to N; None when the capture is
+    of other kernel sources or another variant."""
     tr = NCU_TRAFFIC
-    rec = tr.get(form, {}).get(dom)
-    if not tr["src"] or tr["src"] != src_hash or rec is None:
+    if not tr["src"] or tr["src"] != src_hash:
         return None
-    if rec.get("variant") is not None and list(rec["variant"]) != list(variants):
-        return None
-    return rec["bytes_per_launch"] * N / rec["nodes"]
+    for rec in tr.get("mixed" if form.startswith("mixed") else form, {}).get(dom, []):
+        if rec.get("variant") is None or variant is None or list(rec["variant"]) == list(variant):
+            return rec["bytes_per_launch"] * N / tr["nodes"]
+    return None
 
 
 def rooflines(form, r, N, peaks, fma, src_hash, world):
@@ -484,7 +489,7 @@ def rooflines(form, r, N, peaks, fma, src_hash, world):
     the whole-stage algorithmic fractions."""
     prof = r["prof"]
     dom = max(prof, key=prof.get)
-    ran = {"visc_flux": r["variants"]["visc"], "sweep_eta": r["variants"]["eta"],
+    ran = {"visc_flux": r["variants"]["visc"], "sweep_xi": r["variants"]["xi"], "sweep_eta": r["variants"]["eta"],
            "sweep_zeta": r["variants"]["zeta"]}.get(dom)
     traffic = kernel_traffic("fp64" if form == "fp64" else "mixed", dom, ran, N, src_hash)
     per_gpu = r["value"] / world

@@ -84,13 +84,19 @@ __device__ __forceinline__ int wrapi(int m, int n)
     return q < 0 ? q + n : q;
 }
 
+// a request of the 128-byte line holding p into L2 (no register, no wait)
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ long long midx(const Geo& g, int i, int j, long long n)
 {
     return g.mlayout == 0 ? n : (g.mlayout == 1 ? (long long)i + (long long)g.nx * j : 0LL);
 }
 
 // Index-bounds checks of the bounds-checked build (CFD_BOUNDS_CHECK): an
-// index outside [0, n) sets bit 2 of the error word and the access is
+// index outside [0, n) sets the flag 2 (bit 1) of the error word and the access is
 // skipped; the normal build compiles the check away.
 #ifdef CFD_BOUNDS_CHECK
 __device__ __forceinline__ bool in_range(int* err, long long i, long long n)
@@ -1406,6 +1412,18 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
             if (!inb) return;
         }
 #endif
+        // the plane that the CTAs one stencil reach further in zeta will
+        // read first (k + 5) requested into L2 now
+        if constexpr (YB > 0) {
+            const int kp = k + 5;
+            if (g.per[2] || kp < nz) {
+                const long long np = n + (long long)((g.per[2] ? wrapi(kp, nz) : kp) - k) * st[2];
+                if (in_range(A.err, np, N)) {
+#pragma unroll
+                    for (int var = 0; var < 4; ++var) prefetch_l2(P + (long long)(var < 3 ? var + 1 : 5) * N + np);
+                }
+            }
+        }
         // dq[var][d]: var = u, v, w, T (P rows 1, 2, 3, 5)
         R dq[4][3];
 #pragma unroll
@@ -1500,6 +1518,41 @@ __device__ __forceinline__ void visc25_body(const SweepArgs& A, uint3 vb)
 // ---------------------------------------------------------------------------
 // epilogue modes
 enum { EP_STORE = 0, EP_ACCUM = 1, EP_FINAL_RHS = 2, EP_FINAL_RK = 3 };
+
+
+// the epilogue's operands of node nn (the accumulator; U and U^n for the RK
+// update) requested into L2 ahead of the epilogue
+template <class R, int EP>
+__device__ __forceinline__ void prefetch_epilogue(const SweepArgs& A, long long nn)
+{
+    if (EP == EP_STORE) return;
+    const long long N = A.g.N;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        prefetch_l2((const R*)A.R + q * N + nn);
+        if (EP == EP_FINAL_RK) {
+            prefetch_l2(A.U + q * N + nn);
+            if (A.rk_a != 0.0) prefetch_l2(A.Un + q * N + nn);
+        }
+    }
+}
+
+// the inputs a sweep along direction d reads at node nn (rho, u, v, w, c,
+// the class, the viscous fluxes of d) requested into L2
+template <class R>
+__device__ __forceinline__ void prefetch_row_inputs(const SweepArgs& A, int d, long long nn)
+{
+    const long long N = A.g.N;
+    const R* P = (const R*)A.P;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) prefetch_l2(P + f * N + nn);
+    prefetch_l2(P + 6 * N + nn);
+    if (A.cls) prefetch_l2(A.cls + nn);
+    if (A.Fv) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) prefetch_l2((const R*)A.Fv + (long long)(4 * d + c) * N + nn);
+    }
+}
 
 // RK3 update of one conserved variable, U_out = a U^n + b (U + dt J s), with s
 // the summed sweep residual (exact in FP64) and dtJ = dt J formed once per
@@ -1882,6 +1935,18 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
     const long long base = DIR == 1 ? (long long)i + (long long)nx * g.ny * o : (long long)i + (long long)nx * o;
     const long long N = g.N;
     const R* Fv = (const R*)A.Fv;
+    // 0. the epilogue's operands of the tile's output nodes (the accumulator,
+    //    and U, U^n for the RK update) are requested into L2 now, so that the
+    //    epilogue at the end of the tile finds them there
+    if (EP != EP_STORE && lane_ok) {
+        for (int r = ty; r < TL; r += 8) {
+            const int m = m0 + r;
+            if (m >= hi) break;
+            const long long nn = base + (long long)(per ? wrapi(m, n) : m) * stride;
+            if (!in_range(A.err, nn, N)) break;
+            prefetch_epilogue<R, EP>(A, nn);
+        }
+    }
     // 1. split fluxes, classes and viscous fluxes of the tile rows.  Every
     //    thread first issues the loads of all its rows (NR per warp), then
     //    splits: the loads of a tile are in flight together.
@@ -2163,6 +2228,14 @@ __device__ __forceinline__ void sweep_xw_body(const SweepArgs& A, uint3 vb, int 
     };
     for (int m0 = ms; m0 < me; m0 += XW) {
         const bool first = m0 == ms;
+        // the next chunk's new rows requested into L2
+        {
+            const int mr = m0 + XW + 4 + t;
+            if (mr <= me + 3 && (per || mr < n)) {
+                const long long nn = row + (per ? wrapi(mr, n) : mr);
+                if (in_range(A.err, nn, g.N)) prefetch_row_inputs<R>(A, 0, nn);
+            }
+        }
         // new rows: line positions m0+4 .. m0+XW+3 (all XW+8 rows in the first
         // chunk); loaded and split before the barrier, stored after it
         RowVals<R> v, v2;
@@ -2355,6 +2428,18 @@ __device__ __forceinline__ void sweep_w_body(const SweepArgs& A, uint3 vb)
     __syncthreads();
     if (w == 0) face(ms - 1);
     for (int m0 = ms; m0 < me; m0 += 8) {
+        // the next chunk's new position and output node requested into L2
+        if (lane_ok) {
+            const int mr = m0 + 12 + w, mo = m0 + 8 + w;
+            if (mr <= me + 3 && (per || mr < n)) {
+                const long long nn = base + (long long)(per ? wrapi(mr, n) : mr) * stride;
+                if (in_range(A.err, nn, g.N)) prefetch_row_inputs<R>(A, DIR, nn);
+            }
+            if (mo < me) {
+                const long long nn = base + (long long)(per ? wrapi(mo, n) : mo) * stride;
+                if (in_range(A.err, nn, g.N)) prefetch_epilogue<R, EP>(A, nn);
+            }
+        }
         // (A) the new position m0 + 4 + w (needed up to me + 3)
         if (m0 + 4 + w <= me + 3) load_row(m0 + 4 + w);
         __syncthreads();
@@ -2399,7 +2484,7 @@ constexpr size_t stream_smem_bytes()
 // ahead of the warps that split them; completion is signalled on one mbarrier
 // per buffer.  The node operands of the epilogue (R; U and U^n in the RK
 // variant) are loaded into registers one chunk ahead.  Every wait is bounded:
-// a wait that gives up sets bit 3 of the error word, the block waits (again
+// a wait that gives up sets the flag 8 (bit 3) of the error word, the block waits (again
 // bounded) for the copies it issued and returns.
 // ---------------------------------------------------------------------------
 struct TmaRowMaps {

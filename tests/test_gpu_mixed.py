@@ -125,16 +125,17 @@ def test_mixed_ten_steps_error_vs_fp64_oracle(orc, name):
         assert err <= bound
 
 
-def test_mixed_ramp_with_walls(orc):
-    """Walls, inflow, extrapolation, 2-D metrics, Sutherland; FP64 recovery
-    near the wall and at flagged nodes."""
+@pytest.mark.parametrize("bc_hi", [(3, 3, 0), (5, 5, 0)])
+def test_mixed_ramp_with_walls(orc, bc_hi):
+    """Walls, inflow, extrapolation (or non-reflecting outlet and top), 2-D
+    metrics, Sutherland; FP64 recovery near the wall and at flagged nodes."""
     rc = cases.ramp_case(40, 24, 8, 24.0, 2.9, Tw=2.8)
     kw = dict(scheme="HYBRID", Re=2000.0, Ma=2.9, T_wall=2.8, visc_law=0, T_ref=108.1, bc_lo=(2, 1, 0),
-              bc_hi=(3, 3, 0), inflow=rc["inflow"])
+              bc_hi=bc_hi, inflow=rc["inflow"])
     s64, c, M = make_pair(orc, (40, 24, 8), rc["metrics2d"], **kw)
     s64.close()
     from paper_2209_15333_gb300.solver import Solver
-    s = Solver((40, 24, 8), rc["metrics2d"], bc_lo=(2, 1, 0), bc_hi=(3, 3, 0), precision=1, scheme=3, Re=2000.0,
+    s = Solver((40, 24, 8), rc["metrics2d"], bc_lo=(2, 1, 0), bc_hi=bc_hi, precision=1, scheme=3, Re=2000.0,
                Ma=2.9, T_wall=2.8, visc_law=0, T_ref=108.1)
     s.set_inflow(rc["inflow"])
     U = rc["U"].copy()

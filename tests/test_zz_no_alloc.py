@@ -110,6 +110,20 @@ def test_noalloc_matches_context_rhs_and_oracle_on_consecutive_calls(torch_cuda,
         assert field_rel_err(got, ora) <= TOL, name
 
 
+def test_noalloc_allocates_no_device_memory(torch_cuda, orc):
+    """After a first call (its one-time set-up, and the lazy loading of its
+    kernels), further calls leave the device's free memory unchanged (the
+    test's own buffers come back from torch's caching allocator)."""
+    shape, met, params, U, lo, hi = _case("ramp_walls", orc)
+    _noalloc(torch_cuda, shape, met, params, U, lo, hi)
+    torch_cuda.cuda.synchronize()
+    free0 = torch_cuda.cuda.mem_get_info()[0]
+    for _ in range(3):
+        _noalloc(torch_cuda, shape, met, params, U, lo, hi)
+    torch_cuda.cuda.synchronize()
+    assert torch_cuda.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_rejects_the_learned_sensor(torch_cuda):
     """The call holds no network weights: asking for the learned sensor is an
     error, not a silent switch to the plain sensor."""
