@@ -274,6 +274,18 @@ cfd_status cfd_fma_peak(int precision, double* tflops);
 #define CFD_CHECK_CONVERSIONS 5
 cfd_status cfd_check_conversions(unsigned long long* counts);
 
+/* Check entry, not a step of the method: the viscosity law of params
+   (visc_law: Sutherland, Eq. 15, or the power law T^visc_omega) evaluated on
+   the current device by the routine the viscous kernels use, in the
+   arithmetic of params->precision (FP64, or FP32 for CFD_FP32_BULK: T is
+   rounded to float first), at n temperatures.  T and mu are host arrays of
+   n doubles.  The power law is table-driven (2^(e omega) m_k^omega times a
+   binomial series in (m - m_k)/m_k, tables built from visc_omega on the
+   host); temperatures outside [2^-64, 2^64), non-positive or not finite
+   take exp(omega log T).  CFD_EINVAL for a bad argument or law, CFD_ECUDA
+   on a CUDA error. */
+cfd_status cfd_eval_viscosity(const cfd_params* params, const double* T, double* mu, int n);
+
 /* Instrumentation, not a step of the method: run `reps` right-hand-side
    evaluations of the current state without a graph, with CUDA events between
    the kernels on the context stream, and return the mean milliseconds per

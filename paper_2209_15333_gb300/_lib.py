@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "CFD_OK", -1: "CFD_EINVAL", -2: "CFD_ENOMEM", -3: "CFD_ECUDA"
 EXPORTS = ["cfd_default_params", "cfd_create", "cfd_create_batch", "cfd_set_inflow", "cfd_set_blowing", "cfd_set_state",
            "cfd_get_state", "cfd_rhs", "cfd_step", "cfd_cfl_dt", "cfd_get_flags", "cfd_force_flags",
            "cfd_get_time", "cfd_set_time", "cfd_sync", "cfd_last_error", "cfd_launch_count", "cfd_fma_peak",
-           "cfd_check_conversions", "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
+           "cfd_check_conversions", "cfd_eval_viscosity", "cfd_profile_stage", "cfd_rhs_noalloc", "cfd_set_sweep_variant", "cfd_get_sweep_variant",
            "cfd_set_sensor_mlp", "cfd_sensor_features", "cfd_sensor_fallbacks", "cfd_set_halo_links",
            "cfd_destroy"]
 
@@ -89,6 +89,7 @@ def lib():
         L.cfd_launch_count.restype = C.c_longlong
         L.cfd_fma_peak.argtypes = [C.c_int, dp]
         L.cfd_check_conversions.argtypes = [C.POINTER(C.c_ulonglong)]
+        L.cfd_eval_viscosity.argtypes = [C.POINTER(CfdParams), vp, vp, C.c_int]
         L.cfd_profile_stage.argtypes = [vp, C.c_int, dp]
         L.cfd_set_sensor_mlp.argtypes = [vp, vp, vp, C.c_float]
         L.cfd_sensor_features.argtypes = [vp, C.c_int, vp, C.c_int]
@@ -120,6 +121,16 @@ def check_conversions():
     check(lib().cfd_check_conversions(out))
     keys = ("floats", "f2d_mismatch", "doubles_ok", "d2f_mismatch", "ok_flag_wrong")
     return dict(zip(keys, (int(v) for v in out)))
+
+
+def eval_viscosity(T, **params):
+    """mu(T) on the device by the viscous kernels' routine (cfd_eval_viscosity)."""
+    import numpy as np
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    mu = np.empty_like(T)
+    p = default_params(**params)
+    check(lib().cfd_eval_viscosity(C.byref(p), C.c_void_p(T.ctypes.data), C.c_void_p(mu.ctypes.data), T.size))
+    return mu
 
 
 def default_params(**kw):

@@ -72,6 +72,7 @@ struct cfd_ctx {
     int visc_kind = 0;
     // learned sensor
     void* mlp_buf = nullptr;                    // w1, w2, w3 (bf16), b1, b2, b3 (f32), fallback counter
+    void* powtab_buf = nullptr;                 // the power law's tables (double, then float)
     MlpArgs mlp{};
     bool mlp_on = false;              // 0 node-parallel, 1 2.5-D TZ 64, 2 2.5-D TZ 32 (autotuned)
     bool tuned = false;
@@ -305,12 +306,56 @@ static void free_all(cfd_ctx* c)
     if (c->d_maps) cudaFree(c->d_maps);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void* ptrs[] = {c->b.U, c->b.Uk, c->b.P, c->b.Fv, c->b.R, c->b.cls, c->b.cls_tune, c->met, c->metf, c->err, c->dt, c->t,
-                    c->mlp_buf,
+                    c->mlp_buf, c->powtab_buf,
                     c->cflmax, c->inflow, c->wall_x, c->wall_z};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// Host side of the table-driven power law (power_law in the kernels): for
+// m_k = 1 + k/256, m_k^omega and 1/m_k; 2^(e omega) for e = -64 .. 63; the
+// binomial coefficients C(omega, j), j = 1..6 (FP64) and 1..3 (FP32).  The
+// table entries are evaluated in long double and rounded once.
+static void power_tables(double omega, std::vector<double>& td, std::vector<float>& tf, double pc[6],
+                         float pcf[3])
+{
+    td.assign(PT_COUNT, 0.0);
+    tf.assign(PT_COUNT, 0.0f);
+    const long double w = omega;
+    for (int k = 0; k < 256; ++k) {
+        const long double mk = 1.0L + (long double)k / 256.0L;
+        td[PT_M + k] = (double)powl(mk, w);
+        td[PT_INV + k] = 1.0 / (double)mk;
+        tf[PT_M + k] = (float)powl(mk, w);
+        tf[PT_INV + k] = (float)(1.0L / mk);
+    }
+    for (int e = -64; e < 64; ++e) {
+        td[PT_E + e + 64] = (double)exp2l((long double)e * w);
+        tf[PT_E + e + 64] = (float)exp2l((long double)e * w);
+    }
+    long double c = 1.0L;
+    for (int j = 1; j <= 6; ++j) {
+        c *= (w - (long double)(j - 1)) / (long double)j;
+        pc[j - 1] = (double)c;
+        if (j <= 3) pcf[j - 1] = (float)c;
+    }
+}
+
+static cfd_status build_power_tables(cfd_ctx* ctx)
+{
+    std::vector<double> td;
+    std::vector<float> tf;
+    power_tables(ctx->ph.omega, td, tf, ctx->ph.pc, ctx->ph.pcf);
+    const size_t bd = td.size() * sizeof(double), bf = tf.size() * sizeof(float);
+    CU(cudaMalloc(&ctx->powtab_buf, bd + bf));
+    CU(cudaMemcpyAsync(ctx->powtab_buf, td.data(), bd, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync((char*)ctx->powtab_buf + bd, tf.data(), bf, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->ph.powtab = (const double*)ctx->powtab_buf;
+    ctx->ph.powtabf = (const float*)((char*)ctx->powtab_buf + bd);
+    return CFD_OK;
 }
 
 // 1 when the metrics are one uniform diagonal matrix (a Cartesian box): the
@@ -328,6 +373,36 @@ static int diagonal_metrics(int layout, const double* metrics, int on_device)
         std::memcpy(m, metrics, sizeof(m));
     }
     return m[1] == 0.0 && m[2] == 0.0 && m[3] == 0.0 && m[5] == 0.0 && m[6] == 0.0 && m[7] == 0.0;
+}
+
+// On a uniform diagonal box, the central coefficients of the viscous order
+// times the metric d_x of each periodic direction (Geo::gfold, gsc): FP64
+// products in double, FP32 ones as the FP32 kernels would form them
+static void fold_metrics(Geo& g, int vorder, const double* metrics, int on_device)
+{
+    for (int d = 0; d < 3; ++d) g.gfold[d] = 0;
+    if (!g.diag) return;
+    double m[10];
+    if (on_device) {
+        if (cudaMemcpy(m, metrics, sizeof(m), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    } else {
+        std::memcpy(m, metrics, sizeof(m));
+    }
+    const double c8[4] = {672.0 / 840.0, -168.0 / 840.0, 32.0 / 840.0, -3.0 / 840.0};
+    const double c6[4] = {45.0 / 60.0, -9.0 / 60.0, 1.0 / 60.0, 0.0};
+    const double* c = vorder == 8 ? c8 : c6;
+    for (int d = 0; d < 3; ++d) {
+        if (!g.per[d]) continue;
+        g.gfold[d] = 1;
+        const double md = m[4 * d];
+        for (int k = 0; k < 4; ++k) {
+            g.gsc[d][k] = c[k] * md;
+            g.gscf[d][k] = (float)c[k] * (float)md;
+        }
+    }
 }
 
 static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double* metrics, int metrics_on_device,
@@ -378,6 +453,11 @@ static cfd_status create_inner(cfd_ctx* ctx, const cfd_grid* grid, const double*
     ph.eps = p.weno_eps;
     ph.vorder = p.visc_order;
     fill_float_consts(ph);
+    fold_metrics(g, ph.vorder, metrics, metrics_on_device);
+    if (ph.viscous && ph.visc_law == CFD_POWER) {
+        const cfd_status sp = build_power_tables(ctx);
+        if (sp != CFD_OK) return sp;
+    }
     ctx->real_size = p.precision == CFD_FP32_BULK ? sizeof(float) : sizeof(double);
 
     const long long N = g.N;
@@ -2048,6 +2128,46 @@ static void fill_phys(Phys& ph, const cfd_params& p)
 }
 
 }  // namespace noalloc
+
+extern "C" cfd_status cfd_eval_viscosity(const cfd_params* params, const double* T, double* mu, int n)
+{
+    if (!params || !T || !mu || n < 0) return fail(nullptr, CFD_EINVAL, "bad argument to cfd_eval_viscosity");
+    if (params->visc_law != CFD_SUTHERLAND && params->visc_law != CFD_POWER)
+        return fail(nullptr, CFD_EINVAL, "bad visc_law");
+    if (params->visc_law == CFD_SUTHERLAND && !(params->T_ref > 0.0))
+        return fail(nullptr, CFD_EINVAL, "T_ref must be > 0");
+    if (n == 0) return CFD_OK;
+    Phys ph;
+    noalloc::fill_phys(ph, *params);
+    fill_float_consts(ph);
+    std::vector<double> td;
+    std::vector<float> tf;
+    power_tables(ph.omega, td, tf, ph.pc, ph.pcf);
+    const size_t bd = td.size() * sizeof(double), bf = tf.size() * sizeof(float), bn = (size_t)n * sizeof(double);
+    char* buf = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&buf, bd + bf + 2 * bn);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf, td.data(), bd, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + bd, tf.data(), bf, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + bd + bf, T, bn, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        ph.powtab = (const double*)buf;
+        ph.powtabf = (const float*)(buf + bd);
+        const double* dT = (const double*)(buf + bd + bf);
+        double* dmu = (double*)(buf + bd + bf + bn);
+        const int blocks = (n + 255) / 256;
+        if (params->precision == CFD_FP32_BULK) k_eval_viscosity<float><<<blocks, 256, 0, st>>>(ph, dT, dmu, n);
+        else k_eval_viscosity<double><<<blocks, 256, 0, st>>>(ph, dT, dmu, n);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(mu, dmu, bn, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (buf) cudaFree(buf);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return fail(nullptr, CFD_ECUDA, std::string("viscosity evaluation: ") + cudaGetErrorString(e));
+    return CFD_OK;
+}
 
 extern "C" cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const double* metrics,
                                       const double* U, double* dUdt, void* stream)

@@ -29,6 +29,12 @@ struct Geo {
     int bc_lo[3], bc_hi[3];
     int mlayout;          // 0 3-D, 1 2-D, 2 uniform
     int diag;             // 1: every metric matrix is diagonal (uniform Cartesian box)
+    // on such a box, a periodic direction d (gfold[d]) takes its Cartesian
+    // derivative from the central stencil with the metric folded into the
+    // coefficients: gsc[d][k] = c_k d_x (FP64), gscf[d][k] (FP32)
+    int gfold[3];
+    double gsc[3][4];
+    float gscf[3][4];
     long long M;          // metric points
     const double* met;    // [31][M]
     const float* metf;    // [31][M] float mirror (FP32 kernels)
@@ -40,6 +46,12 @@ struct Phys {
     double Tw;
     int viscous, visc_law;
     double omega, suth_s;  // power exponent, S/T_ref
+    // the power law's tables (see power_law; null: exp(omega log T)) and the
+    // binomial coefficients C(omega, j) of its series
+    const double* powtab;
+    const float* powtabf;
+    double pc[6];
+    float pcf[3];
     int scheme;            // 0 UD7, 1 WENO5, 2 WENO7, 3 HYBRID
     int charrec;           // WENO faces reconstruct characteristic fields (Sec. 2.2.2)
     double th1, th2, eps;
@@ -1248,6 +1260,20 @@ __device__ __forceinline__ R dcentral(int order, int per, int n, int m, Ld f)
     return cen8<R>(d(1), d(2), d(3), d(4));
 }
 
+// Cartesian derivative along a folded direction d (Geo::gfold): the central
+// stencil of the viscous order with coefficients c_k d_x (one multiply per
+// derivative fewer than differentiating and then applying the metric)
+template <class R, class Ld>
+__device__ __forceinline__ R dcentral_folded(const Geo& g, int order, int d, int m, Ld f)
+{
+    R c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = sizeof(R) == 8 ? (R)g.gsc[d][k] : (R)g.gscf[d][k];
+    auto dd = [&](int k) { return f(m + k) - f(m - k); };
+    if (order == 8) return mad(c[3], dd(4), mad(c[2], dd(3), mad(c[1], dd(2), c[0] * dd(1))));
+    return mad(c[2], dd(3), mad(c[1], dd(2), c[0] * dd(1)));
+}
+
 // central derivative on a tile: f(m) takes unwrapped line positions, so the
 // periodic form needs no wrap (the tile rows already hold the wrapped nodes)
 template <class R, class Ld>
@@ -1264,21 +1290,77 @@ __device__ __forceinline__ R dcentral_tile(int order, int per, int n, int m, Ld 
 // ---------------------------------------------------------------------------
 // viscous fluxes at nodes (Eqs. 9-15 with readings R13-R15)
 // ---------------------------------------------------------------------------
+// Power law mu = T^omega, table-driven (a table method in the manner of
+// Tang, ACM TOMS 15, 1989).  With T = 2^e m, m in [1, 2), m_k = 1 + k/256 the
+// node below m (k = the top 8 fraction bits) and delta = (m - m_k)/m_k in
+// [0, 1/256):
+//     T^omega = 2^(e omega) m_k^omega (1 + delta)^omega,
+// the last factor by its binomial series to delta^6 (FP64; the next term is
+// below 2^-56) or delta^3 (FP32).  The exponent and k come from the bit
+// pattern (integer pipe); 2^(e omega) for e in [-64, 63], m_k^omega and 1/m_k
+// are tables built per context on the host; the FP64 form takes 10 FP64
+// operations where exp(omega log T) takes about 45.  Relative error a few
+// units of rounding (the two table entries, the series and three roundings).
+// Temperatures outside [2^-64, 2^64), non-positive or not finite, and
+// contexts without tables, take exp(omega log T).
+enum { PT_M = 0, PT_INV = 256, PT_E = 512, PT_COUNT = 640 };
+
+__device__ __forceinline__ double power_law(const Phys& ph, double T)
+{
+    const long long b = __double_as_longlong(T);
+    const int e = (int)(b >> 52) - 1023;
+    if (ph.powtab && (unsigned)(e + 64) < 128u) {
+        const double* t = ph.powtab;
+        const int k = (int)((b >> 44) & 0xff);
+        const double m = __longlong_as_double((b & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+        const double mk = __longlong_as_double(0x3ff0000000000000ll | ((long long)k << 44));
+        const double d = (m - mk) * __ldg(t + PT_INV + k);
+        double p = ph.pc[5];
+#pragma unroll
+        for (int j = 4; j >= 0; --j) p = mad(p, d, ph.pc[j]);
+        p = mad(p, d, 1.0);
+        return (p * __ldg(t + PT_M + k)) * __ldg(t + PT_E + e + 64);
+    }
+    return exp(ph.omega * log(T));
+}
+
+__device__ __forceinline__ float power_law(const Phys& ph, float T)
+{
+    const int b = __float_as_int(T);
+    const int e = (b >> 23) - 127;
+    if (ph.powtabf && (unsigned)(e + 64) < 128u) {
+        const float* t = ph.powtabf;
+        const int k = (b >> 15) & 0xff;
+        const float m = __int_as_float((b & 0x007fffff) | 0x3f800000);
+        const float mk = __int_as_float(0x3f800000 | (k << 15));
+        const float d = (m - mk) * __ldg(t + PT_INV + k);
+        float p = mad(mad(ph.pcf[2], d, ph.pcf[1]), d, ph.pcf[0]);
+        p = mad(p, d, 1.0f);
+        return (p * __ldg(t + PT_M + k)) * __ldg(t + PT_E + e + 64);
+    }
+    return powf(T, ph.omegaf);
+}
+
 __device__ __forceinline__ double viscosity(const Phys& ph, double T)
 {
-    // T^omega as exp(omega log T): relative error a few units of rounding for
-    // the temperatures of a flow (|omega log T| < 10), about half the FP64
-    // operations of the general pow
-    if (ph.visc_law == 1) return exp(ph.omega * log(T));
+    if (ph.visc_law == 1) return power_law(ph, T);
     double s = ph.suth_s;
     return T * sqrt(T) * (1.0 + s) / (T + s);
 }
 
 __device__ __forceinline__ float viscosity(const Phys& ph, float T)
 {
-    if (ph.visc_law == 1) return powf(T, ph.omegaf);
+    if (ph.visc_law == 1) return power_law(ph, T);
     float s = ph.suth_sf;
     return T * sqrtf(T) * (1.0f + s) / (T + s);
+}
+
+// mu(T) of n temperatures through the kernels' routine (a check of it)
+template <class R>
+__global__ void k_eval_viscosity(Phys ph, const double* T, double* mu, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) mu[t] = (double)viscosity(ph, (R)T[t]);
 }
 
 // Cartesian gradients q_x = xi_x q_xi + eta_x q_eta + zeta_x q_zeta, ... of
@@ -1290,12 +1372,13 @@ template <class R>
 __device__ __forceinline__ void cartesian_gradients(const Geo& g, long long mi, const R dq[4][3], R gr[4][3])
 {
     if (g.diag) {
+        // folded directions arrive as Cartesian derivatives already
         const R m0 = metr<R>(g, M_RAW + 0, mi), m1 = metr<R>(g, M_RAW + 4, mi), m2 = metr<R>(g, M_RAW + 8, mi);
 #pragma unroll
         for (int var = 0; var < 4; ++var) {
-            gr[var][0] = m0 * dq[var][0];
-            gr[var][1] = m1 * dq[var][1];
-            gr[var][2] = m2 * dq[var][2];
+            gr[var][0] = g.gfold[0] ? dq[var][0] : m0 * dq[var][0];
+            gr[var][1] = g.gfold[1] ? dq[var][1] : m1 * dq[var][1];
+            gr[var][2] = g.gfold[2] ? dq[var][2] : m2 * dq[var][2];
         }
         return;
     }
@@ -1432,8 +1515,9 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const int m = pos[d];
-                dq[var][d] = dcentral_tile<R>(ord, g.per[d], nd[d], m,
-                                              [&](int mm) { return __ldg(f + off[d][mm - m + 4]); });
+                auto ld = [&](int mm) { return __ldg(f + off[d][mm - m + 4]); };
+                dq[var][d] = g.gfold[d] ? dcentral_folded<R>(g, ord, d, m, ld)
+                                        : dcentral_tile<R>(ord, g.per[d], nd[d], m, ld);
             }
         }
         visc_node_flux<R>(g, ph, n, i, j, dq, P[5 * N + n], P[N + n], P[2 * N + n], P[3 * N + n], Fv);
@@ -1498,11 +1582,13 @@ __device__ __forceinline__ void visc25_body(const SweepArgs& A, uint3 vb)
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 const R* cf = c + f * 640;
-                dq[f][0] = dcentral_tile<R>(ord, g.per[0], nx, i, [&](int mm) { return cf[hy * 40 + hx + (mm - i)]; });
-                dq[f][1] = dcentral_tile<R>(ord, g.per[1], ny, j, [&](int mm) { return cf[(hy + (mm - j)) * 40 + hx]; });
-                dq[f][2] = dcentral_tile<R>(ord, g.per[2], nz, zc, [&](int mm) {
-                    return ring[(size_t)(((mm % 9) + 9) % 9) * PL + f * 640 + hy * 40 + hx];
-                });
+                auto lx = [&](int mm) { return cf[hy * 40 + hx + (mm - i)]; };
+                auto ly = [&](int mm) { return cf[(hy + (mm - j)) * 40 + hx]; };
+                auto lz = [&](int mm) { return ring[(size_t)(((mm % 9) + 9) % 9) * PL + f * 640 + hy * 40 + hx]; };
+                dq[f][0] = g.gfold[0] ? dcentral_folded<R>(g, ord, 0, i, lx) : dcentral_tile<R>(ord, g.per[0], nx, i, lx);
+                dq[f][1] = g.gfold[1] ? dcentral_folded<R>(g, ord, 1, j, ly) : dcentral_tile<R>(ord, g.per[1], ny, j, ly);
+                dq[f][2] = g.gfold[2] ? dcentral_folded<R>(g, ord, 2, zc, lz)
+                                      : dcentral_tile<R>(ord, g.per[2], nz, zc, lz);
             }
             const long long n = (long long)i + (long long)nx * ((long long)j + (long long)ny * zc);
             const R* cu = c;
