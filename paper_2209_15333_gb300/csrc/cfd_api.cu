@@ -376,8 +376,7 @@ static int diagonal_metrics(int layout, const double* metrics, int on_device)
 }
 
 // On a uniform diagonal box, the central coefficients of the viscous order
-// times the metric d_x of each periodic direction (Geo::gfold, gsc): FP64
-// products in double, FP32 ones as the FP32 kernels would form them
+// times the metric d_x of each periodic direction (Geo::gfold, gsc)
 static void fold_metrics(Geo& g, int vorder, const double* metrics, int on_device)
 {
     for (int d = 0; d < 3; ++d) g.gfold[d] = 0;
@@ -398,10 +397,7 @@ static void fold_metrics(Geo& g, int vorder, const double* metrics, int on_devic
         if (!g.per[d]) continue;
         g.gfold[d] = 1;
         const double md = m[4 * d];
-        for (int k = 0; k < 4; ++k) {
-            g.gsc[d][k] = c[k] * md;
-            g.gscf[d][k] = (float)c[k] * (float)md;
-        }
+        for (int k = 0; k < 4; ++k) g.gsc[d][k] = c[k] * md;
     }
 }
 

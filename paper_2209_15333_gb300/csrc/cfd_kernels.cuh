@@ -30,11 +30,10 @@ struct Geo {
     int mlayout;          // 0 3-D, 1 2-D, 2 uniform
     int diag;             // 1: every metric matrix is diagonal (uniform Cartesian box)
     // on such a box, a periodic direction d (gfold[d]) takes its Cartesian
-    // derivative from the central stencil with the metric folded into the
-    // coefficients: gsc[d][k] = c_k d_x (FP64), gscf[d][k] (FP32)
+    // derivative in the FP64 form from the central stencil with the metric
+    // folded into the coefficients: gsc[d][k] = c_k d_x
     int gfold[3];
     double gsc[3][4];
-    float gscf[3][4];
     long long M;          // metric points
     const double* met;    // [31][M]
     const float* metf;    // [31][M] float mirror (FP32 kernels)
@@ -943,12 +942,16 @@ __device__ __forceinline__ float pos_part(float x) { return fmaxf(x, 0.0f); }
 __device__ __forceinline__ float neg_part(float x) { return fminf(x, 0.0f); }
 
 template <class R>
+// axis = 0, 1, 2: k is that unit vector (the directions of a uniform
+// diagonal box), whose zero components cost nothing; -1: any k.  The FP64
+// form uses the axis form on such boxes (the FP64 pipe bounds it); in FP32
+// the second inlined copy costs more than the operations it saves.
 __device__ __forceinline__ void sw_split(const Phys& ph, R rho, R u, R v, R w, R c, R k1, R k2, R k3,
-                                         R sig, R fp[5], R fm[5])
+                                         R sig, R fp[5], R fm[5], int axis = -1)
 {
     const R gm1 = pk<R>(ph.gm1, ph.gm1f);
     const R gm1x2 = gm1 + gm1;
-    const R uk = mad(k3, w, mad(k2, v, k1 * u));
+    const R uk = axis == 0 ? u : (axis == 1 ? v : (axis == 2 ? w : mad(k3, w, mad(k2, v, k1 * u))));
     const R V = sig * uk;
     const R cs = c * sig;
     const R l4 = V - cs, l5 = V + cs;
@@ -965,9 +968,15 @@ __device__ __forceinline__ void sw_split(const Phys& ph, R rho, R u, R v, R w, R
         const R f0 = a * mad(gm1x2, l1, s);
         const R t = ac * dl;
         fp[0] = f0;
-        fp[1] = mad(u, f0, t * k1);
-        fp[2] = mad(v, f0, t * k2);
-        fp[3] = mad(w, f0, t * k3);
+        if (axis >= 0) {
+            fp[1] = axis == 0 ? mad(u, f0, t) : u * f0;
+            fp[2] = axis == 1 ? mad(v, f0, t) : v * f0;
+            fp[3] = axis == 2 ? mad(w, f0, t) : w * f0;
+        } else {
+            fp[1] = mad(u, f0, t * k1);
+            fp[2] = mad(v, f0, t * k2);
+            fp[3] = mad(w, f0, t * k3);
+        }
         fp[4] = mad(t, uk, a * mad(l1, gq, s * H));
     }
     {
@@ -978,9 +987,15 @@ __device__ __forceinline__ void sw_split(const Phys& ph, R rho, R u, R v, R w, R
         const R f0 = a * mad(gm1x2, l1, s);
         const R t = ac * dl;
         fm[0] = f0;
-        fm[1] = mad(u, f0, t * k1);
-        fm[2] = mad(v, f0, t * k2);
-        fm[3] = mad(w, f0, t * k3);
+        if (axis >= 0) {
+            fm[1] = axis == 0 ? mad(u, f0, t) : u * f0;
+            fm[2] = axis == 1 ? mad(v, f0, t) : v * f0;
+            fm[3] = axis == 2 ? mad(w, f0, t) : w * f0;
+        } else {
+            fm[1] = mad(u, f0, t * k1);
+            fm[2] = mad(v, f0, t * k2);
+            fm[3] = mad(w, f0, t * k3);
+        }
         fm[4] = mad(t, uk, a * mad(l1, gq, s * H));
     }
 }
@@ -1260,6 +1275,15 @@ __device__ __forceinline__ R dcentral(int order, int per, int n, int m, Ld f)
     return cen8<R>(d(1), d(2), d(3), d(4));
 }
 
+// whether direction d of the viscous derivatives is folded: FP64 only (the
+// FP64 pipe is what bounds that form; in FP32 the extra branches cost more
+// than the multiply they save)
+template <class R>
+__device__ __forceinline__ bool fold_dir(const Geo& g, int d)
+{
+    return sizeof(R) == 8 && g.gfold[d];
+}
+
 // Cartesian derivative along a folded direction d (Geo::gfold): the central
 // stencil of the viscous order with coefficients c_k d_x (one multiply per
 // derivative fewer than differentiating and then applying the metric)
@@ -1268,7 +1292,7 @@ __device__ __forceinline__ R dcentral_folded(const Geo& g, int order, int d, int
 {
     R c[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) c[k] = sizeof(R) == 8 ? (R)g.gsc[d][k] : (R)g.gscf[d][k];
+    for (int k = 0; k < 4; ++k) c[k] = (R)g.gsc[d][k];
     auto dd = [&](int k) { return f(m + k) - f(m - k); };
     if (order == 8) return mad(c[3], dd(4), mad(c[2], dd(3), mad(c[1], dd(2), c[0] * dd(1))));
     return mad(c[2], dd(3), mad(c[1], dd(2), c[0] * dd(1)));
@@ -1376,9 +1400,9 @@ __device__ __forceinline__ void cartesian_gradients(const Geo& g, long long mi, 
         const R m0 = metr<R>(g, M_RAW + 0, mi), m1 = metr<R>(g, M_RAW + 4, mi), m2 = metr<R>(g, M_RAW + 8, mi);
 #pragma unroll
         for (int var = 0; var < 4; ++var) {
-            gr[var][0] = g.gfold[0] ? dq[var][0] : m0 * dq[var][0];
-            gr[var][1] = g.gfold[1] ? dq[var][1] : m1 * dq[var][1];
-            gr[var][2] = g.gfold[2] ? dq[var][2] : m2 * dq[var][2];
+            gr[var][0] = fold_dir<R>(g, 0) ? dq[var][0] : m0 * dq[var][0];
+            gr[var][1] = fold_dir<R>(g, 1) ? dq[var][1] : m1 * dq[var][1];
+            gr[var][2] = fold_dir<R>(g, 2) ? dq[var][2] : m2 * dq[var][2];
         }
         return;
     }
@@ -1516,8 +1540,8 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
             for (int d = 0; d < 3; ++d) {
                 const int m = pos[d];
                 auto ld = [&](int mm) { return __ldg(f + off[d][mm - m + 4]); };
-                dq[var][d] = g.gfold[d] ? dcentral_folded<R>(g, ord, d, m, ld)
-                                        : dcentral_tile<R>(ord, g.per[d], nd[d], m, ld);
+                dq[var][d] = fold_dir<R>(g, d) ? dcentral_folded<R>(g, ord, d, m, ld)
+                                               : dcentral_tile<R>(ord, g.per[d], nd[d], m, ld);
             }
         }
         visc_node_flux<R>(g, ph, n, i, j, dq, P[5 * N + n], P[N + n], P[2 * N + n], P[3 * N + n], Fv);
@@ -1585,10 +1609,12 @@ __device__ __forceinline__ void visc25_body(const SweepArgs& A, uint3 vb)
                 auto lx = [&](int mm) { return cf[hy * 40 + hx + (mm - i)]; };
                 auto ly = [&](int mm) { return cf[(hy + (mm - j)) * 40 + hx]; };
                 auto lz = [&](int mm) { return ring[(size_t)(((mm % 9) + 9) % 9) * PL + f * 640 + hy * 40 + hx]; };
-                dq[f][0] = g.gfold[0] ? dcentral_folded<R>(g, ord, 0, i, lx) : dcentral_tile<R>(ord, g.per[0], nx, i, lx);
-                dq[f][1] = g.gfold[1] ? dcentral_folded<R>(g, ord, 1, j, ly) : dcentral_tile<R>(ord, g.per[1], ny, j, ly);
-                dq[f][2] = g.gfold[2] ? dcentral_folded<R>(g, ord, 2, zc, lz)
-                                      : dcentral_tile<R>(ord, g.per[2], nz, zc, lz);
+                dq[f][0] = fold_dir<R>(g, 0) ? dcentral_folded<R>(g, ord, 0, i, lx)
+                                             : dcentral_tile<R>(ord, g.per[0], nx, i, lx);
+                dq[f][1] = fold_dir<R>(g, 1) ? dcentral_folded<R>(g, ord, 1, j, ly)
+                                             : dcentral_tile<R>(ord, g.per[1], ny, j, ly);
+                dq[f][2] = fold_dir<R>(g, 2) ? dcentral_folded<R>(g, ord, 2, zc, lz)
+                                             : dcentral_tile<R>(ord, g.per[2], nz, zc, lz);
             }
             const long long n = (long long)i + (long long)nx * ((long long)j + (long long)ny * zc);
             const R* cu = c;
@@ -1714,7 +1740,8 @@ __device__ __forceinline__ R split_prim(const SweepArgs& A, int d, const NodePri
 {
     R k1 = metr<R>(A.g, M_K + 3 * d, mi), k2 = metr<R>(A.g, M_K + 3 * d + 1, mi),
       k3 = metr<R>(A.g, M_K + 3 * d + 2, mi), sg = metr<R>(A.g, M_SIG + d, mi);
-    sw_split<R>(A.ph, q.rho, q.u, q.v, q.w, q.c, k1, k2, k3, sg, fp, fm);
+    if (sizeof(R) == 8 && A.g.diag) sw_split<R>(A.ph, q.rho, q.u, q.v, q.w, q.c, k1, k2, k3, sg, fp, fm, d);
+    else sw_split<R>(A.ph, q.rho, q.u, q.v, q.w, q.c, k1, k2, k3, sg, fp, fm);
     return sg;
 }
 
@@ -1728,7 +1755,8 @@ __device__ __forceinline__ R node_split(const SweepArgs& A, int d, long long n, 
     R rho = P[n], u = P[N + n], v = P[2 * N + n], w = P[3 * N + n], c = P[6 * N + n];
     R k1 = metr<R>(A.g, M_K + 3 * d, mi), k2 = metr<R>(A.g, M_K + 3 * d + 1, mi),
       k3 = metr<R>(A.g, M_K + 3 * d + 2, mi), sg = metr<R>(A.g, M_SIG + d, mi);
-    sw_split<R>(A.ph, rho, u, v, w, c, k1, k2, k3, sg, fp, fm);
+    if (sizeof(R) == 8 && A.g.diag) sw_split<R>(A.ph, rho, u, v, w, c, k1, k2, k3, sg, fp, fm, d);
+    else sw_split<R>(A.ph, rho, u, v, w, c, k1, k2, k3, sg, fp, fm);
     return sg;
 }
 
