@@ -46,8 +46,11 @@ FORMS = {"fp64": dict(precision=0, learned=False), "mixed": dict(precision=1, le
 # operations (FMA = 2 flops; division, square root, power = 1):
 FP64_FLOPS = {"prim": 25, "sensor": 20, "visc_flux": 305, "sweep_xi": 247, "sweep_eta": 252, "sweep_zeta": 277}
 # compulsory bytes per node of each kernel in the FP32-bulk form (inputs read
-# once, outputs written once)
-MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_eta": 77, "sweep_zeta": 164}
+# once, outputs written once), in the form cfd_profile_stage times them: the
+# zeta sweep with the right-hand-side epilogue (P, class, Fv, R in; L out in
+# FP64); the learned sensor reads p and rho and writes the class
+MIXED_BYTES = {"prim": 69, "sensor": 5, "visc_flux": 64, "sweep_xi": 57, "sweep_eta": 77, "sweep_zeta": 97}
+MIXED_BYTES_LEARNED_SENSOR = 9
 # What one point-stage must move through HBM whatever the kernel design: read
 # the stage state (40 B), read U^n in stages 2-3 (26.7 B on average), write
 # the new state (40 B); metrics are constant on the uniform box.
@@ -57,7 +60,22 @@ ALG_BYTES_PER_POINT_STAGE = 40.0 + 80.0 / 3.0 + 40.0
 # each kernel per variant (dir:kind:param as cfd_get_sweep_variant reports
 # it; the RHS epilogue for zeta, as cfd_profile_stage runs it); valid only
 # for the kernel sources with hash prefix "src".
-NCU_TRAFFIC = {"src": None, "nodes": 256 ** 3, "fp64": {}, "mixed": {}}
+NCU_TRAFFIC = {
+    "src": "7375681bc613", "nodes": 256 ** 3,
+    "fp64": {"prim": [{"variant": None, "bytes_per_launch": 1554929408}],
+             "sensor": [{"variant": None, "bytes_per_launch": 145206016}],
+             "visc_flux": [{"variant": [3, 0], "bytes_per_launch": 2176536576}],
+             "sweep_xi": [{"variant": [1, 256], "bytes_per_launch": 1863582464}],
+             "sweep_eta": [{"variant": [2, 0], "bytes_per_launch": 2573337088}],
+             "sweep_zeta": [{"variant": [2, 64], "bytes_per_launch": 2699683840}]},
+    "mixed": {"prim": [{"variant": None, "bytes_per_launch": 1120322816}],
+              "sensor": [{"variant": None, "bytes_per_launch": 70767616}],
+              "visc_flux": [{"variant": [3, 0], "bytes_per_launch": 1029319680}],
+              "sweep_xi": [{"variant": [0, 0], "bytes_per_launch": 921103104}],
+              "sweep_eta": [{"variant": [1, 16], "bytes_per_launch": 1390636544}],
+              "sweep_zeta": [{"variant": [1, 16], "bytes_per_launch": 1886381312}]},
+    "mixed_learned": {"sensor": [{"variant": None, "bytes_per_launch": 147385344}]},
+}
 
 
 def parse():
@@ -478,7 +496,8 @@ def kernel_traffic(form, dom, variant, N, src_hash):
     tr = NCU_TRAFFIC
     if not tr["src"] or tr["src"] != src_hash:
         return None
-    for rec in tr.get("mixed" if form.startswith("mixed") else form, {}).get(dom, []):
+    recs = tr.get(form, {}).get(dom) or tr.get("mixed" if form.startswith("mixed") else form, {}).get(dom, [])
+    for rec in recs:
         if rec.get("variant") is None or variant is None or list(rec["variant"]) == list(variant):
             return rec["bytes_per_launch"] * N / tr["nodes"]
     return None
@@ -491,7 +510,7 @@ def rooflines(form, r, N, peaks, fma, src_hash, world):
     dom = max(prof, key=prof.get)
     ran = {"visc_flux": r["variants"]["visc"], "sweep_xi": r["variants"]["xi"], "sweep_eta": r["variants"]["eta"],
            "sweep_zeta": r["variants"]["zeta"]}.get(dom)
-    traffic = kernel_traffic("fp64" if form == "fp64" else "mixed", dom, ran, N, src_hash)
+    traffic = kernel_traffic(form, dom, ran, N, src_hash)
     per_gpu = r["value"] / world
     stage = {"hbm_bytes_per_point_stage": ALG_BYTES_PER_POINT_STAGE,
              "hbm_achieved_gbs": ALG_BYTES_PER_POINT_STAGE * per_gpu / 1e9,
@@ -513,8 +532,9 @@ def rooflines(form, r, N, peaks, fma, src_hash, world):
                 "traffic_kernel": dom,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_per_node": ALG_BYTES_PER_POINT_STAGE, "kernel_ms": prof}
-        kc = MIXED_BYTES[dom] * N / (prof[dom] * 1e-3) / 1e9
-        roof["kernel_compulsory"] = {"kernel": dom, "bytes_per_node": MIXED_BYTES[dom], "achieved_gbs": kc,
+        cb = MIXED_BYTES_LEARNED_SENSOR if (form == "mixed_learned" and dom == "sensor") else MIXED_BYTES[dom]
+        kc = cb * N / (prof[dom] * 1e-3) / 1e9
+        roof["kernel_compulsory"] = {"kernel": dom, "bytes_per_node": cb, "achieved_gbs": kc,
                                      "frac": kc / peaks["hbm_gbs"]}
     return roof, stage
 
