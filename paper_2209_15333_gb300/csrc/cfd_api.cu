@@ -599,12 +599,17 @@ template <class R>
 static cfd_status launch_visc(cfd_ctx* ctx, const SweepArgs& A, int kind)
 {
     const Geo& g = ctx->g;
+    // a periodic box with 8th-order viscous terms takes the instantiation
+    // without order and closure decisions
+    const bool p8 = g.per[0] && g.per[1] && g.per[2] && ctx->ph.vorder == 8;
     if (kind == 0) {
         const NodeLaunch nl = node_launch(g);
-        k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+        if (p8) k_visc_flux<R, 0, true><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+        else k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
     } else if (kind == 3) {
         dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
-        k_visc_flux<R, 4><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
+        if (p8) k_visc_flux<R, 4, true><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
+        else k_visc_flux<R, 4><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
     } else {
         const int tz = kind == 1 ? 64 : 32;
         dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + tz - 1) / tz);

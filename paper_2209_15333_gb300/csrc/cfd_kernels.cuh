@@ -1468,7 +1468,10 @@ __device__ __forceinline__ void visc_node_flux(const Geo& g, const Phys& ph, lon
 
 // YB > 0: CTAs of 32 x YB nodes in an x-y tile (the y neighbours of a tile's
 // nodes are shared through L1); YB = 0: CTAs along one x row.
-template <class R, int YB = 0>
+// P8: every direction periodic and the viscous order 8 (known at compile
+// time: the derivatives take the interior stencil with no order or closure
+// decisions; the same operations as the general path)
+template <class R, int YB = 0, bool P8 = false>
 __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
 {
     const Geo& g = A.g;
@@ -1540,8 +1543,14 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
             for (int d = 0; d < 3; ++d) {
                 const int m = pos[d];
                 auto ld = [&](int mm) { return __ldg(f + off[d][mm - m + 4]); };
-                dq[var][d] = fold_dir<R>(g, d) ? dcentral_folded<R>(g, ord, d, m, ld)
-                                               : dcentral_tile<R>(ord, g.per[d], nd[d], m, ld);
+                if constexpr (P8) {
+                    auto dd = [&](int kk) { return ld(m + kk) - ld(m - kk); };
+                    dq[var][d] = fold_dir<R>(g, d) ? dcentral_folded<R>(g, 8, d, m, ld)
+                                                   : cen8<R>(dd(1), dd(2), dd(3), dd(4));
+                } else {
+                    dq[var][d] = fold_dir<R>(g, d) ? dcentral_folded<R>(g, ord, d, m, ld)
+                                                   : dcentral_tile<R>(ord, g.per[d], nd[d], m, ld);
+                }
             }
         }
         visc_node_flux<R>(g, ph, n, i, j, dq, P[5 * N + n], P[N + n], P[2 * N + n], P[3 * N + n], Fv);
@@ -3261,8 +3270,8 @@ __global__ void k_prim(SweepArgs A) { prim_body<RT>(A, blockIdx); }
 __global__ void k_prim_mixed(SweepArgs A) { prim_mixed_body<false>(A, blockIdx); }
 __global__ void k_sensor(SweepArgs A) { sensor_body<false>(A, blockIdx); }
 __global__ void k_sensor32(SweepArgs A) { sensor32_body<false>(A, blockIdx); }
-template <class R, int YB = 0>
-__global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R, YB>(A, blockIdx); }
+template <class R, int YB = 0, bool P8 = false>
+__global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R, YB, P8>(A, blockIdx); }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<R, TZ>(A, blockIdx); }
 template <class R, int BX, int EP, bool CHAR = false>
