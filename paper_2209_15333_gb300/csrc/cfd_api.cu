@@ -648,10 +648,16 @@ static cfd_status launch_sweep_dir(cfd_ctx* ctx, SweepArgs& A, int kind, int par
             k_sweep_w<R, DIR, EP><<<grid, 256, walk_smem_bytes<R>(), ctx->stream>>>(A);
     } else {
         dim3 grid((g.nx + 31) / 32, nother, (hi - lo + param - 1) / param);
-        if (param == 16)
-            k_sweep_t<R, DIR, EP, 16><<<grid, 256, tile_smem_bytes<R, 16>(), ctx->stream>>>(A);
-        else
-            k_sweep_t<R, DIR, EP, 32><<<grid, 256, tile_smem_bytes<R, 32>(), ctx->stream>>>(A);
+        // FP32 on a periodic line with 8th-order viscous terms: the
+        // instantiation without order and closure decisions
+        const bool p8 = sizeof(R) == 4 && g.per[DIR] && ctx->ph.vorder == 8;
+        if (param == 16) {
+            if (p8) k_sweep_t<R, DIR, EP, 16, false, true><<<grid, 256, tile_smem_bytes<R, 16>(), ctx->stream>>>(A);
+            else k_sweep_t<R, DIR, EP, 16><<<grid, 256, tile_smem_bytes<R, 16>(), ctx->stream>>>(A);
+        } else {
+            if (p8) k_sweep_t<R, DIR, EP, 32, false, true><<<grid, 256, tile_smem_bytes<R, 32>(), ctx->stream>>>(A);
+            else k_sweep_t<R, DIR, EP, 32><<<grid, 256, tile_smem_bytes<R, 32>(), ctx->stream>>>(A);
+        }
     }
     LAUNCH_CHECK();
     return CFD_OK;
@@ -674,6 +680,11 @@ static cfd_status launch_xi(cfd_ctx* ctx, SweepArgs& A, int kind, int seg)
         if (nb == 32) k_sweep_x<R, 32, EP_STORE, true><<<grid, 32, 0, ctx->stream>>>(A);
         else if (nb == 64) k_sweep_x<R, 64, EP_STORE, true><<<grid, 64, 0, ctx->stream>>>(A);
         else k_sweep_x<R, 128, EP_STORE, true><<<grid, 128, 0, ctx->stream>>>(A);
+    } else if (sizeof(R) == 4 && g.per[0] && ctx->ph.vorder == 8) {
+        // FP32 periodic lines, 8th-order viscous terms (as for the tiles)
+        if (nb == 32) k_sweep_x<R, 32, EP_STORE, false, true><<<grid, 32, 0, ctx->stream>>>(A);
+        else if (nb == 64) k_sweep_x<R, 64, EP_STORE, false, true><<<grid, 64, 0, ctx->stream>>>(A);
+        else k_sweep_x<R, 128, EP_STORE, false, true><<<grid, 128, 0, ctx->stream>>>(A);
     } else if (nb == 32) {
         k_sweep_x<R, 32, EP_STORE><<<grid, 32, 0, ctx->stream>>>(A);
     } else if (nb == 64) {
@@ -739,6 +750,17 @@ static cudaError_t set_sweep_attrs()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tile_smem_bytes<R, 16>());
+    if (sizeof(R) == 4) {
+        const auto dyn = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        const auto carve = cudaFuncAttributePreferredSharedMemoryCarveout;
+        const int maxs = (int)cudaSharedmemCarveoutMaxShared;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16, false, true>, dyn,
+                                                       (int)tile_smem_bytes<R, 16>());
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 32, false, true>, dyn,
+                                                       (int)tile_smem_bytes<R, 32>());
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 16, false, true>, carve, maxs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_t<R, DIR, EP, 32, false, true>, carve, maxs);
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sweep_w<R, DIR, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)walk_smem_bytes<R>());

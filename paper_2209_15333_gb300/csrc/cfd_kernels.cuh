@@ -1311,6 +1311,20 @@ __device__ __forceinline__ R dcentral_tile(int order, int per, int n, int m, Ld 
     return dcentral<R>(order, 0, n, m, f);
 }
 
+// the central derivative of the viscous divergence in the sweeps; P8: the
+// swept line is periodic and the order 8, known at compile time (the same
+// operations without the order and closure decisions)
+template <class R, bool P8, class Ld>
+__device__ __forceinline__ R dvisc(int order, int per, int n, int m, Ld f)
+{
+    if constexpr (P8) {
+        auto d = [&](int k) { return f(m + k) - f(m - k); };
+        return cen8<R>(d(1), d(2), d(3), d(4));
+    } else {
+        return dcentral_tile<R>(order, per, n, m, f);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // viscous fluxes at nodes (Eqs. 9-15 with readings R13-R15)
 // ---------------------------------------------------------------------------
@@ -1771,7 +1785,7 @@ __device__ __forceinline__ R node_split(const SweepArgs& A, int d, long long n, 
 
 // xi sweep: one CTA per segment of BX nodes of one x-line, halo of 4 nodes.
 // CHAR: WENO faces reconstruct characteristic fields (Sec. 2.2.2).
-template <class R, int BX, int EP, bool CHAR = false>
+template <class R, int BX, int EP, bool CHAR = false, bool P8 = false>
 __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
 {
     __shared__ __align__(16) R sf[10][BX + 12];  // rows padded so a 12-value window never leaves a row
@@ -1916,7 +1930,7 @@ __device__ __forceinline__ void sweep_x_body(const SweepArgs& A, uint3 vb)
         if (A.Fv) {
 #pragma unroll
             for (int r = 0; r < 4; ++r)
-                val[r + 1] += dcentral_tile<R>(A.ph.vorder, per, n, i, [&](int mm) { return sv[r][mm - (i0 - 4)]; });
+                val[r + 1] += dvisc<R, P8>(A.ph.vorder, per, n, i, [&](int mm) { return sv[r][mm - (i0 - 4)]; });
         }
         epilogue<R, EP>(A, nn, i, j, k, val);
     }
@@ -2036,7 +2050,7 @@ __global__ void __launch_bounds__(128) k_sweep_s(SweepArgs A)
 // once (many loads in flight), faces are computed from shared memory, then
 // differenced.  The halo costs 8/TL extra splits -- cheap in FP32, where the
 // streaming form is latency-bound instead.
-template <class R, int DIR, int EP, int TL, bool CHAR = false>
+template <class R, int DIR, int EP, int TL, bool CHAR = false, bool P8 = false>
 __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
 {
     constexpr int ROWS = TL + 8;
@@ -2216,7 +2230,7 @@ __device__ __forceinline__ void sweep_t_body(const SweepArgs& A, uint3 vb)
             const int rowbase = m0 - 4;  // line position of tile row 0
 #pragma unroll
             for (int row = 0; row < 4; ++row)
-                val[row + 1] += dcentral_tile<R>(A.ph.vorder, per, n, m,
+                val[row + 1] += dvisc<R, P8>(A.ph.vorder, per, n, m,
                                                  [&](int mm) { return sv[((mm - rowbase) * 4 + row) * 32 + lane]; });
         }
         const int mm = per ? wrapi(m, n) : m;
@@ -3274,12 +3288,12 @@ template <class R, int YB = 0, bool P8 = false>
 __global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R, YB, P8>(A, blockIdx); }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<R, TZ>(A, blockIdx); }
-template <class R, int BX, int EP, bool CHAR = false>
-__global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A) { sweep_x_body<R, BX, EP, CHAR>(A, blockIdx); }
-template <class R, int DIR, int EP, int TL, bool CHAR = false>
+template <class R, int BX, int EP, bool CHAR = false, bool P8 = false>
+__global__ void __launch_bounds__(BX) k_sweep_x(SweepArgs A) { sweep_x_body<R, BX, EP, CHAR, P8>(A, blockIdx); }
+template <class R, int DIR, int EP, int TL, bool CHAR = false, bool P8 = false>
 __global__ void __launch_bounds__(256, CHAR ? 1 : (sizeof(R) == 4 ? (TL == 16 ? 4 : 3) : 1)) k_sweep_t(SweepArgs A)
 {
-    sweep_t_body<R, DIR, EP, TL, CHAR>(A, blockIdx);
+    sweep_t_body<R, DIR, EP, TL, CHAR, P8>(A, blockIdx);
 }
 template <class R, int EP>
 __global__ void __launch_bounds__(XW) k_sweep_xw(SweepArgs A, int seg_len) { sweep_xw_body<R, EP>(A, blockIdx, seg_len); }
