@@ -84,6 +84,7 @@ struct cfd_ctx {
     BatchMap maps[3][MAP_COUNT];        // [stage][kernel kind and variant]
     int map_grid[MAP_COUNT] = {};       // persistent grid per map
     int bvar[4] = {0, 0, 0, 0};                         // chosen variant per kind (viscous, xi, eta, zeta)
+    bool batch_p8 = false;  // every block periodic in every direction, 8th-order viscous terms
     // multi-block halo links: [0] between the U arrays, [1] between the Uk
     // arrays; per direction
     HaloLink* d_halo[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -595,21 +596,49 @@ static cfd_status launch_bc(cfd_ctx* ctx, double* U, double tfrac, bool use_dt, 
     return CFD_OK;
 }
 
+// the FP32 plain sensor rides in the node-flux kernels (kinds 0 and 3) of a
+// viscous hybrid stage instead of a launch of its own
+static bool sensor_fusable(const cfd_ctx* ctx)
+{
+    return ctx->prm.precision == CFD_FP32_BULK && ctx->ph.viscous && !ctx->forced &&
+           ctx->prm.sensor == CFD_SENSOR_PLAIN;
+}
+static bool sensor_fused(const cfd_ctx* ctx, int visc_kind)
+{
+    return sensor_fusable(ctx) && (visc_kind == 0 || visc_kind == 3);
+}
+
+template <class R, bool SENS>
+static void launch_visc_node(cfd_ctx* ctx, const SweepArgs& A, int kind, bool p8)
+{
+    const Geo& g = ctx->g;
+    if (kind == 0) {
+        const NodeLaunch nl = node_launch(g);
+        if (p8) k_visc_flux<R, 0, true, SENS><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+        else k_visc_flux<R, 0, false, SENS><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+    } else {
+        dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
+        if (p8) k_visc_flux<R, 4, true, SENS><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
+        else k_visc_flux<R, 4, false, SENS><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
+    }
+}
+
+// sens: the node-flux kernels (kinds 0, 3) also write the plain sensor's
+// classes (FP32 bulk only)
 template <class R>
-static cfd_status launch_visc(cfd_ctx* ctx, const SweepArgs& A, int kind)
+static cfd_status launch_visc(cfd_ctx* ctx, const SweepArgs& A, int kind, bool sens = false)
 {
     const Geo& g = ctx->g;
     // a periodic box with 8th-order viscous terms takes the instantiation
     // without order and closure decisions
     const bool p8 = g.per[0] && g.per[1] && g.per[2] && ctx->ph.vorder == 8;
-    if (kind == 0) {
-        const NodeLaunch nl = node_launch(g);
-        if (p8) k_visc_flux<R, 0, true><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
-        else k_visc_flux<R><<<nl.grid, nl.block, 0, ctx->stream>>>(A);
-    } else if (kind == 3) {
-        dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
-        if (p8) k_visc_flux<R, 4, true><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
-        else k_visc_flux<R, 4><<<grid, dim3(32, 4), 0, ctx->stream>>>(A);
+    if (kind == 0 || kind == 3) {
+        if constexpr (sizeof(R) == sizeof(float)) {
+            if (sens) launch_visc_node<R, true>(ctx, A, kind, p8);
+            else launch_visc_node<R, false>(ctx, A, kind, p8);
+        } else {
+            launch_visc_node<R, false>(ctx, A, kind, p8);
+        }
     } else {
         const int tz = kind == 1 ? 64 : 32;
         dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + tz - 1) / tz);
@@ -816,8 +845,9 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
     LAUNCH_CHECK();
     if (ev) cudaEventRecord(ev[1], ctx->stream);
     const bool sensor = !ctx->forced && (mixed || ctx->prm.scheme == CFD_HYBRID);
+    const bool fused = sensor && sensor_fused(ctx, ctx->visc_kind);
     const cudaStream_t sst = ctx->stream;
-    if (sensor) {
+    if (sensor && !fused) {
         if (ctx->prm.sensor == CFD_SENSOR_MLP) {
             if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
             // 32 x 8 columns walking zeta; the walk length balances the
@@ -854,7 +884,7 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
     }
     if (ev) cudaEventRecord(ev[2], ctx->stream);
     if (ctx->ph.viscous) {
-        cfd_status st = launch_visc<R>(ctx, A, ctx->visc_kind);
+        cfd_status st = launch_visc<R>(ctx, A, ctx->visc_kind, fused);
         if (st != CFD_OK) return st;
     }
 
@@ -977,9 +1007,12 @@ static std::string tune_key(const cfd_ctx* ctx)
 {
     const Geo& g = ctx->g;
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "single %d %d %d %d %d%d%d %d%d%d%d%d%d %d %d %d %d", ctx->prm.precision, g.nx,
+    // (the sensor kind decides whether the FP32 plain sensor rides in the
+    // viscous node kernels, which changes the viscous variants' costs)
+    std::snprintf(buf, sizeof(buf), "single %d %d %d %d %d%d%d %d%d%d%d%d%d %d %d %d %d %d", ctx->prm.precision, g.nx,
                   g.ny, g.nz, g.per[0], g.per[1], g.per[2], g.bc_lo[0], g.bc_lo[1], g.bc_lo[2], g.bc_hi[0],
-                  g.bc_hi[1], g.bc_hi[2], ctx->prm.scheme, ctx->ph.viscous, ctx->ph.charrec, g.mlayout);
+                  g.bc_hi[1], g.bc_hi[2], ctx->prm.scheme, ctx->ph.viscous, ctx->ph.charrec, g.mlayout,
+                  ctx->prm.sensor);
     return tune_prefix(ctx->dev) + buf;
 }
 
@@ -995,8 +1028,8 @@ static std::string batch_tune_key(const cfd_ctx* ctx)
         }
     }
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "batch %d %d %d %d %llx", ctx->prm.precision, (int)ctx->sub.size(),
-                  ctx->prm.scheme, (int)ctx->ph.viscous, h);
+    std::snprintf(buf, sizeof(buf), "batch %d %d %d %d %d %llx", ctx->prm.precision, (int)ctx->sub.size(),
+                  ctx->prm.scheme, (int)ctx->ph.viscous, ctx->prm.sensor, h);
     return tune_prefix(ctx->dev) + buf;
 }
 
@@ -1060,11 +1093,19 @@ static cfd_status autotune_t(cfd_ctx* ctx)
         }
     }
     if (ctx->ph.viscous) {
+        // where the FP32 plain sensor can ride in the node-flux kernels, the
+        // other variants are timed with the sensor launch they still need
+        const bool fusable = sensor_fusable(ctx);
         float best = 1e30f;
         for (int kind = 0; kind < 4 && st == CFD_OK; ++kind) {
             for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, ctx->stream);
-                st = launch_visc<R>(ctx, A, kind);
+                if (fusable && !sensor_fused(ctx, kind)) {
+                    const NodeLaunch nl = node_launch(ctx->g);
+                    k_sensor32<<<nl.grid, nl.block, 0, ctx->stream>>>(A);
+                    LAUNCH_CHECK();
+                }
+                st = launch_visc<R>(ctx, A, kind, sensor_fused(ctx, kind));
             }
             cudaEventRecord(e1, ctx->stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, CFD_ECUDA, "autotune timing");
@@ -1346,7 +1387,7 @@ static void batch_tiles(const Geo& g, int map, int out[3])
     }
 }
 
-template <class R>
+template <class R, bool P8>
 static cudaError_t batch_kernel_attrs()
 {
     const auto dyn = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -1354,18 +1395,22 @@ static cudaError_t batch_kernel_attrs()
     const int maxs = (int)cudaSharedmemCarveoutMaxShared;
     cudaError_t e = cudaFuncSetAttribute(kb_visc_flux25<R, 32>, dyn, (int)visc25_smem_bytes<R>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_visc_flux25<R, 64>, dyn, (int)visc25_smem_bytes<R>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 16>, dyn, (int)tile_smem_bytes<R, 16>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 16>, dyn, (int)tile_smem_bytes<R, 16>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 32>, dyn, (int)tile_smem_bytes<R, 32>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, dyn, (int)tile_smem_bytes<R, 32>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM>, dyn, (int)walk_smem_bytes<R>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK>, dyn, (int)walk_smem_bytes<R>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 16>, carve, maxs);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 16>, carve, maxs);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 32>, carve, maxs);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, carve, maxs);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM>, carve, maxs);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK>, carve, maxs);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 16, P8>, dyn, (int)tile_smem_bytes<R, 16>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 16, P8>, dyn, (int)tile_smem_bytes<R, 16>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 32, P8>, dyn, (int)tile_smem_bytes<R, 32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 32, P8>, dyn, (int)tile_smem_bytes<R, 32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM, P8>, dyn, (int)walk_smem_bytes<R>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK, P8>, dyn, (int)walk_smem_bytes<R>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 16, P8>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 16, P8>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 1, EP_ACCUM, 32, P8>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_t<R, 2, EP_FINAL_RK, 32, P8>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM, P8>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK, P8>, carve, maxs);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp<R>, dyn, (int)sizeof(MlpWalkSmem));
     return e;
 }
@@ -1381,7 +1426,7 @@ static int persistent_grid(K kernel, int threads, size_t smem, int items)
     return std::max(1, std::min(items, std::max(1, per_sm) * sms));
 }
 
-template <class R>
+template <class R, bool P8>
 static void batch_grids(cfd_ctx* ctx, const int totals[MAP_COUNT])
 {
     const bool mixed = sizeof(R) == sizeof(float);
@@ -1390,16 +1435,23 @@ static void batch_grids(cfd_ctx* ctx, const int totals[MAP_COUNT])
                          : persistent_grid(kb_prim<double>, 128, 0, totals[MAP_NODE]);
     mg[MAP_VISC + 0] = persistent_grid(kb_visc_flux25<R, 32>, 256, visc25_smem_bytes<R>(), totals[MAP_VISC + 0]);
     mg[MAP_VISC + 1] = persistent_grid(kb_visc_flux25<R, 64>, 256, visc25_smem_bytes<R>(), totals[MAP_VISC + 1]);
-    mg[MAP_VISC + 2] = persistent_grid(kb_visc_flux_tiles<R>, 128, 0, totals[MAP_VISC + 2]);
-    mg[MAP_SX + 0] = persistent_grid(kb_sweep_x<R, 64, EP_STORE>, 64, 0, totals[MAP_SX + 0]);
-    mg[MAP_SX + 1] = persistent_grid(kb_sweep_x<R, 128, EP_STORE>, 128, 0, totals[MAP_SX + 1]);
+    mg[MAP_VISC + 2] = persistent_grid(kb_visc_flux_tiles<R, P8>, 128, 0, totals[MAP_VISC + 2]);
+    if constexpr (sizeof(R) == sizeof(float))
+        if (sensor_fusable(ctx))
+            mg[MAP_VISC + 2] = persistent_grid(kb_visc_flux_tiles<R, P8, true>, 128, 0, totals[MAP_VISC + 2]);
+    mg[MAP_SX + 0] = persistent_grid(kb_sweep_x<R, 64, EP_STORE, P8>, 64, 0, totals[MAP_SX + 0]);
+    mg[MAP_SX + 1] = persistent_grid(kb_sweep_x<R, 128, EP_STORE, P8>, 128, 0, totals[MAP_SX + 1]);
     mg[MAP_SX + 2] = persistent_grid(kb_sweep_xw<R, EP_STORE>, XW, 0, totals[MAP_SX + 2]);
-    mg[MAP_T1 + 0] = persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, 16>, 256, tile_smem_bytes<R, 16>(), totals[MAP_T1 + 0]);
-    mg[MAP_T1 + 1] = persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, 32>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T1 + 1]);
-    mg[MAP_T1 + 2] = persistent_grid(kb_sweep_w<R, 1, EP_ACCUM>, 256, walk_smem_bytes<R>(), totals[MAP_T1 + 2]);
-    mg[MAP_T2 + 0] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 16>, 256, tile_smem_bytes<R, 16>(), totals[MAP_T2 + 0]);
-    mg[MAP_T2 + 1] = persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 32>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T2 + 1]);
-    mg[MAP_T2 + 2] = persistent_grid(kb_sweep_w<R, 2, EP_FINAL_RK>, 256, walk_smem_bytes<R>(), totals[MAP_T2 + 2]);
+    mg[MAP_T1 + 0] =
+        persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, 16, P8>, 256, tile_smem_bytes<R, 16>(), totals[MAP_T1 + 0]);
+    mg[MAP_T1 + 1] =
+        persistent_grid(kb_sweep_t<R, 1, EP_ACCUM, 32, P8>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T1 + 1]);
+    mg[MAP_T1 + 2] = persistent_grid(kb_sweep_w<R, 1, EP_ACCUM, P8>, 256, walk_smem_bytes<R>(), totals[MAP_T1 + 2]);
+    mg[MAP_T2 + 0] =
+        persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 16, P8>, 256, tile_smem_bytes<R, 16>(), totals[MAP_T2 + 0]);
+    mg[MAP_T2 + 1] =
+        persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 32, P8>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T2 + 1]);
+    mg[MAP_T2 + 2] = persistent_grid(kb_sweep_w<R, 2, EP_FINAL_RK, P8>, 256, walk_smem_bytes<R>(), totals[MAP_T2 + 2]);
     mg[MAP_MLP] = persistent_grid(kb_sensor_mlp<R>, 256, sizeof(MlpWalkSmem), totals[MAP_MLP]);
 }
 
@@ -1473,12 +1525,27 @@ static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids
             int* pre = ctx->d_maps + (size_t)k * per_kind;
             ctx->maps[s][k] = BatchMap{ctx->d_tbl[s], pre, pre + nb + 1, nb};
         }
+    // every block periodic in every direction with 8th-order viscous terms:
+    // the viscous tiles (both forms) and the FP32 xi and tile sweeps take the
+    // instantiations without order and closure decisions, as a single block does
+    bool p8 = ctx->ph.viscous && params[0].visc_order == 8;
+    for (int b = 0; b < nb; ++b)
+        for (int d = 0; d < 3; ++d) p8 = p8 && ctx->sub[b]->g.per[d];
+    ctx->batch_p8 = p8;
     if (params[0].precision == CFD_FP32_BULK) {
-        CU((batch_kernel_attrs<float>()));
-        batch_grids<float>(ctx, totals);
+        if (p8) {
+            CU((batch_kernel_attrs<float, true>()));
+            batch_grids<float, true>(ctx, totals);
+        } else {
+            CU((batch_kernel_attrs<float, false>()));
+            batch_grids<float, false>(ctx, totals);
+        }
     } else {
-        CU((batch_kernel_attrs<double>()));
-        batch_grids<double>(ctx, totals);
+        CU((batch_kernel_attrs<double, false>()));
+        batch_grids<double, false>(ctx, totals);
+        // the FP64 viscous tiles take the P8 instantiation (sweeps do not)
+        if (p8) ctx->map_grid[MAP_VISC + 2] = persistent_grid(kb_visc_flux_tiles<double, true>, 128, 0,
+                                                              totals[MAP_VISC + 2]);
     }
     CU(cudaStreamSynchronize(ctx->stream));
     return CFD_OK;
@@ -1584,10 +1651,16 @@ extern "C" cfd_status cfd_create_batch(cfd_ctx** out, int nblocks, const cfd_gri
     return CFD_OK;
 }
 
+// the FP32 plain sensor rides in the ensemble's viscous node tiles (variant 2)
+static bool batch_sensor_fused(const cfd_ctx* ctx, int visc_var)
+{
+    return sensor_fusable(ctx) && visc_var == 2;
+}
+
 // one persistent launch of kernel kind `kind` (KIND_*) in variant `var` for
 // stage s of the ensemble
-template <class R>
-static cfd_status launch_batch_kind(cfd_ctx* ctx, int s, int kind, int var)
+template <class R, bool P8>
+static cfd_status launch_batch_kind_t(cfd_ctx* ctx, int s, int kind, int var)
 {
     const cudaStream_t st = ctx->stream;
     const BatchMap* m = ctx->maps[s];
@@ -1596,29 +1669,46 @@ static cfd_status launch_batch_kind(cfd_ctx* ctx, int s, int kind, int var)
     case KIND_VISC:
         if (var == 0) kb_visc_flux25<R, 32><<<mg[MAP_VISC], 256, visc25_smem_bytes<R>(), st>>>(m[MAP_VISC]);
         else if (var == 1) kb_visc_flux25<R, 64><<<mg[MAP_VISC + 1], 256, visc25_smem_bytes<R>(), st>>>(m[MAP_VISC + 1]);
+        else if (batch_sensor_fused(ctx, var)) {
+            if constexpr (sizeof(R) == sizeof(float)) {
+                if (ctx->batch_p8)
+                    kb_visc_flux_tiles<R, true, true><<<mg[MAP_VISC + 2], dim3(32, 4), 0, st>>>(m[MAP_VISC + 2]);
+                else kb_visc_flux_tiles<R, false, true><<<mg[MAP_VISC + 2], dim3(32, 4), 0, st>>>(m[MAP_VISC + 2]);
+            }
+        } else if (ctx->batch_p8) kb_visc_flux_tiles<R, true><<<mg[MAP_VISC + 2], dim3(32, 4), 0, st>>>(m[MAP_VISC + 2]);
         else kb_visc_flux_tiles<R><<<mg[MAP_VISC + 2], dim3(32, 4), 0, st>>>(m[MAP_VISC + 2]);
         break;
     case KIND_SX:
-        if (var == 0) kb_sweep_x<R, 64, EP_STORE><<<mg[MAP_SX], 64, 0, st>>>(m[MAP_SX]);
-        else if (var == 1) kb_sweep_x<R, 128, EP_STORE><<<mg[MAP_SX + 1], 128, 0, st>>>(m[MAP_SX + 1]);
+        if (var == 0) kb_sweep_x<R, 64, EP_STORE, P8><<<mg[MAP_SX], 64, 0, st>>>(m[MAP_SX]);
+        else if (var == 1) kb_sweep_x<R, 128, EP_STORE, P8><<<mg[MAP_SX + 1], 128, 0, st>>>(m[MAP_SX + 1]);
         else kb_sweep_xw<R, EP_STORE><<<mg[MAP_SX + 2], XW, 0, st>>>(m[MAP_SX + 2]);
         break;
     case KIND_T1:
-        if (var == 0) kb_sweep_t<R, 1, EP_ACCUM, 16><<<mg[MAP_T1], 256, tile_smem_bytes<R, 16>(), st>>>(m[MAP_T1]);
+        if (var == 0)
+            kb_sweep_t<R, 1, EP_ACCUM, 16, P8><<<mg[MAP_T1], 256, tile_smem_bytes<R, 16>(), st>>>(m[MAP_T1]);
         else if (var == 1)
-            kb_sweep_t<R, 1, EP_ACCUM, 32><<<mg[MAP_T1 + 1], 256, tile_smem_bytes<R, 32>(), st>>>(m[MAP_T1 + 1]);
-        else kb_sweep_w<R, 1, EP_ACCUM><<<mg[MAP_T1 + 2], 256, walk_smem_bytes<R>(), st>>>(m[MAP_T1 + 2]);
+            kb_sweep_t<R, 1, EP_ACCUM, 32, P8><<<mg[MAP_T1 + 1], 256, tile_smem_bytes<R, 32>(), st>>>(m[MAP_T1 + 1]);
+        else kb_sweep_w<R, 1, EP_ACCUM, P8><<<mg[MAP_T1 + 2], 256, walk_smem_bytes<R>(), st>>>(m[MAP_T1 + 2]);
         break;
     default:
         if (var == 0)
-            kb_sweep_t<R, 2, EP_FINAL_RK, 16><<<mg[MAP_T2], 256, tile_smem_bytes<R, 16>(), st>>>(m[MAP_T2]);
+            kb_sweep_t<R, 2, EP_FINAL_RK, 16, P8><<<mg[MAP_T2], 256, tile_smem_bytes<R, 16>(), st>>>(m[MAP_T2]);
         else if (var == 1)
-            kb_sweep_t<R, 2, EP_FINAL_RK, 32><<<mg[MAP_T2 + 1], 256, tile_smem_bytes<R, 32>(), st>>>(m[MAP_T2 + 1]);
-        else kb_sweep_w<R, 2, EP_FINAL_RK><<<mg[MAP_T2 + 2], 256, walk_smem_bytes<R>(), st>>>(m[MAP_T2 + 2]);
+            kb_sweep_t<R, 2, EP_FINAL_RK, 32, P8><<<mg[MAP_T2 + 1], 256, tile_smem_bytes<R, 32>(), st>>>(
+                m[MAP_T2 + 1]);
+        else kb_sweep_w<R, 2, EP_FINAL_RK, P8><<<mg[MAP_T2 + 2], 256, walk_smem_bytes<R>(), st>>>(m[MAP_T2 + 2]);
         break;
     }
     LAUNCH_CHECK();
     return CFD_OK;
+}
+
+// the sweeps take the P8 instantiations in FP32 only (as for one block)
+template <class R>
+static cfd_status launch_batch_kind(cfd_ctx* ctx, int s, int kind, int var)
+{
+    if (sizeof(R) == sizeof(float) && ctx->batch_p8) return launch_batch_kind_t<R, true>(ctx, s, kind, var);
+    return launch_batch_kind_t<R, false>(ctx, s, kind, var);
 }
 
 template <class R>
@@ -1637,12 +1727,17 @@ static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
             if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
             kb_sensor_mlp<R><<<ctx->map_grid[MAP_MLP], 256, sizeof(MlpWalkSmem), st>>>(m[MAP_MLP], ctx->mlp,
                                                                                        kBatchMlpTZ);
+            LAUNCH_CHECK();
         } else if (mixed) {
-            kb_sensor32<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+            // (the viscous node tiles may form these classes instead)
+            if (!batch_sensor_fused(ctx, ctx->bvar[KIND_VISC])) {
+                kb_sensor32<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+                LAUNCH_CHECK();
+            }
         } else {
             kb_sensor<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+            LAUNCH_CHECK();
         }
-        LAUNCH_CHECK();
     }
     if (ev) cudaEventRecord(ev[2], st);
     if (ctx->ph.viscous) {
@@ -1706,6 +1801,12 @@ static cfd_status batch_autotune_t(cfd_ctx* ctx)
         for (int var = 0; var < kBatchVariants && st == CFD_OK; ++var) {
             for (int rep = 0; rep < 4 && st == CFD_OK; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, ctx->stream);
+                // viscous variants that leave the FP32 plain sensor to its own
+                // launch are timed with it
+                if (kind == KIND_VISC && sensor_fusable(ctx) && !batch_sensor_fused(ctx, var)) {
+                    kb_sensor32<<<ctx->map_grid[MAP_NODE], 128, 0, ctx->stream>>>(ctx->maps[0][MAP_NODE]);
+                    LAUNCH_CHECK();
+                }
                 st = launch_batch_kind<R>(ctx, 0, kind, var);
             }
             cudaEventRecord(e1, ctx->stream);

@@ -1485,7 +1485,11 @@ __device__ __forceinline__ void visc_node_flux(const Geo& g, const Phys& ph, lon
 // P8: every direction periodic and the viscous order 8 (known at compile
 // time: the derivatives take the interior stencil with no order or closure
 // decisions; the same operations as the general path)
-template <class R, int YB = 0, bool P8 = false>
+// SENS (FP32 only): the node's plain shock-sensor class (Eq. 42-43, the
+// operations of sensor32_body in the same order) is formed here too, from the
+// pressures at m-1 and m+1 of the stencil offsets the derivatives use; the
+// stage then needs no separate sensor launch
+template <class R, int YB = 0, bool P8 = false, bool SENS = false>
 __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
 {
     const Geo& g = A.g;
@@ -1545,6 +1549,7 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
                 if (in_range(A.err, np, N)) {
 #pragma unroll
                     for (int var = 0; var < 4; ++var) prefetch_l2(P + (long long)(var < 3 ? var + 1 : 5) * N + np);
+                    if constexpr (SENS) prefetch_l2(P + 4 * N + np);
                 }
             }
         }
@@ -1568,6 +1573,22 @@ __device__ __forceinline__ void visc_node_body(const SweepArgs& A, uint3 vb)
             }
         }
         visc_node_flux<R>(g, ph, n, i, j, dq, P[5 * N + n], P[N + n], P[2 * N + n], P[3 * N + n], Fv);
+        if constexpr (SENS) {
+            static_assert(sizeof(R) == sizeof(float), "the fused sensor is the FP32 one");
+            const float* __restrict__ p = (const float*)P + 4 * N + n;
+            const float p0 = p[0];
+            float th = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int m = pos[d];
+                if (!P8 && !g.per[d] && (m == 0 || m == nd[d] - 1)) continue;  // reading R4
+                const float pm = p[off[d][3]];
+                const float pp = p[off[d][5]];
+                const float p2 = p0 + p0;
+                th += fabsf((p2 - pm) - pp) / ((pm + p2) + pp);
+            }
+            A.cls_io[n] = th <= ph.th1f ? 0 : (th <= ph.th2f ? 1 : 2);
+        }
     }
 }
 
@@ -2494,7 +2515,7 @@ constexpr size_t walk_smem_bytes()
            (size_t)WS_RING * 5 * 32 * sizeof(R) + (size_t)WS_RING * 32;
 }
 
-template <class R, int DIR, int EP>
+template <class R, int DIR, int EP, bool P8 = false>
 __device__ __forceinline__ void sweep_w_body(const SweepArgs& A, uint3 vb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2594,7 +2615,7 @@ __device__ __forceinline__ void sweep_w_body(const SweepArgs& A, uint3 vb)
             if (A.Fv) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    val[c + 1] += dcentral_tile<R>(A.ph.vorder, per, n, m, [&](int mm) {
+                    val[c + 1] += dvisc<R, P8>(A.ph.vorder, per, n, m, [&](int mm) {
                         return sv[(((mm - (ms - 4)) & (WV_RING - 1)) * 4 + c) * 32 + lane];
                     });
             }
@@ -3284,8 +3305,8 @@ __global__ void k_prim(SweepArgs A) { prim_body<RT>(A, blockIdx); }
 __global__ void k_prim_mixed(SweepArgs A) { prim_mixed_body<false>(A, blockIdx); }
 __global__ void k_sensor(SweepArgs A) { sensor_body<false>(A, blockIdx); }
 __global__ void k_sensor32(SweepArgs A) { sensor32_body<false>(A, blockIdx); }
-template <class R, int YB = 0, bool P8 = false>
-__global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R, YB, P8>(A, blockIdx); }
+template <class R, int YB = 0, bool P8 = false, bool SENS = false>
+__global__ void __launch_bounds__(256) k_visc_flux(SweepArgs A) { visc_node_body<R, YB, P8, SENS>(A, blockIdx); }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) k_visc_flux25(SweepArgs A) { visc25_body<R, TZ>(A, blockIdx); }
 template <class R, int BX, int EP, bool CHAR = false, bool P8 = false>
@@ -3336,6 +3357,30 @@ __device__ __forceinline__ int batch_find(const BatchMap& m, int item, uint3* v)
     return lo;
 }
 
+// the item range [lo, hi) and tile grid (gx, gy) of the block a CTA worked
+// on last: the next item usually lies in the same block, and then needs no
+// search over the prefix sums
+struct BatchRange {
+    int lo, hi, gx, gy;
+};
+
+__device__ __forceinline__ int batch_find_cached(const BatchMap& m, int item, uint3* v, int cached, BatchRange& r)
+{
+    if (cached < 0 || item < r.lo || item >= r.hi) {
+        cached = batch_find(m, item, v);
+        r.lo = __ldg(m.prefix + cached);
+        r.hi = __ldg(m.prefix + cached + 1);
+        r.gx = __ldg(m.gdim + 3 * cached);
+        r.gy = __ldg(m.gdim + 3 * cached + 1);
+        return cached;
+    }
+    const int local = item - r.lo;
+    v->x = local % r.gx;
+    v->y = (local / r.gx) % r.gy;
+    v->z = local / (r.gx * r.gy);
+    return cached;
+}
+
 // CONTIG: each CTA takes a contiguous range of items (node kernels: its
 // items stay in one block); otherwise items are dealt round-robin, so CTAs
 // that run at the same time work on neighbouring tiles and share their halos
@@ -3345,13 +3390,14 @@ __device__ __forceinline__ int batch_find(const BatchMap& m, int item, uint3* v)
     __shared__ __align__(16) SweepArgs sA;                                                            \
     constexpr int AW = (int)(sizeof(SweepArgs) / sizeof(int));                                        \
     int cached = -1;                                                                                  \
+    BatchRange rng{0, 0, 1, 1};                                                                       \
     const int total = __ldg(m.prefix + m.nb);                                                         \
     const int per_cta = CONTIG ? (total + gridDim.x - 1) / gridDim.x : 1;                             \
     const int item_end = CONTIG ? min(total, ((int)blockIdx.x + 1) * per_cta) : total;                \
     const int item_step = CONTIG ? 1 : (int)gridDim.x;                                                \
     for (int item = blockIdx.x * per_cta; item < item_end; item += item_step) {                       \
         uint3 v;                                                                                      \
-        const int b = batch_find(m, item, &v);                                                        \
+        const int b = batch_find_cached(m, item, &v, cached, rng);                                    \
         if (b != cached) {                                                                            \
             __syncthreads();                                                                          \
             const int* src = reinterpret_cast<const int*>(m.tbl + b);                                 \
@@ -3381,24 +3427,33 @@ __global__ void __launch_bounds__(256, 2) kb_sensor_mlp(BatchMap m, MlpArgs W, i
 }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((visc25_body<R, TZ>), true, false) }
-template <class R>
-__global__ void __launch_bounds__(128) kb_visc_flux_tiles(BatchMap m) { BATCH_LOOP((visc_node_body<R, 4>), false, false) }
-template <class R, int BX, int EP>
-__global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m) { BATCH_LOOP((sweep_x_body<R, BX, EP>), true, false) }
+// P8: every block periodic in every direction with 8th-order viscous terms
+// (the instantiations without order and closure decisions, as for one block)
+// SENS (FP32): the tiles also write the plain sensor's classes
+template <class R, bool P8 = false, bool SENS = false>
+__global__ void __launch_bounds__(128) kb_visc_flux_tiles(BatchMap m)
+{
+    BATCH_LOOP((visc_node_body<R, 4, P8, SENS>), false, false)
+}
+template <class R, int BX, int EP, bool P8 = false>
+__global__ void __launch_bounds__(BX) kb_sweep_x(BatchMap m)
+{
+    BATCH_LOOP((sweep_x_body<R, BX, EP, false, P8>), true, false)
+}
 // walking xi sweep over whole lines (items: one x-line of one block)
 template <class R, int EP>
 __device__ __forceinline__ void sweep_xw_line(const SweepArgs& A, uint3 vb) { sweep_xw_body<R, EP>(A, vb, 1 << 30); }
 template <class R, int EP>
 __global__ void __launch_bounds__(XW) kb_sweep_xw(BatchMap m) { BATCH_LOOP((sweep_xw_line<R, EP>), true, false) }
-template <class R, int DIR, int EP, int TL>
+template <class R, int DIR, int EP, int TL, bool P8 = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (TL == 16 ? 4 : 3) : 1) kb_sweep_t(BatchMap m)
 {
-    BATCH_LOOP((sweep_t_body<R, DIR, EP, TL>), true, false)
+    BATCH_LOOP((sweep_t_body<R, DIR, EP, TL, false, P8>), true, false)
 }
-template <class R, int DIR, int EP>
+template <class R, int DIR, int EP, bool P8 = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) kb_sweep_w(BatchMap m)
 {
-    BATCH_LOOP((sweep_w_body<R, DIR, EP>), true, false)
+    BATCH_LOOP((sweep_w_body<R, DIR, EP, P8>), true, false)
 }
 
 }  // namespace cfdk

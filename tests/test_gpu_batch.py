@@ -144,6 +144,41 @@ def test_batch_variants_bit_identical(precision):
             assert np.array_equal(o[b], outs[0][b]), b
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_periodic_batch_matches_single_block_contexts(orc, precision):
+    """An ensemble whose blocks are all periodic with 8th-order viscous terms
+    takes the instantiations for periodic lines (viscous tiles; FP32 xi and
+    tile sweeps): every variant still gives each block the bits of its own
+    context, and the FP64 form matches the oracle."""
+    from paper_2209_15333_gb300.solver import BatchSolver, Solver
+    mets, params, states = _blocks(precision)
+    shapes, bcs = SHAPES[:4], BCS[:4]
+    mets, params, states = mets[:4], params[:4], states[:4]
+    dt = 5e-4
+    refs = []
+    for b, sh in enumerate(shapes):
+        with Solver(sh, mets[b], **params[b]) as s:
+            s.set_state(states[b])
+            s.step(dt, 3)
+            refs.append(s.get_state())
+    for v in ((2, 0, 0, 0), (2, 1, 1, 1), (0, 2, 2, 2)):
+        with BatchSolver(shapes, mets, params, bcs=bcs) as bs:
+            for b, U in enumerate(states):
+                bs.set_state(U, block=b)
+            bs.set_sweep_variant(0, *VISC_V[v[0]])
+            bs.set_sweep_variant(3, *XI_V[v[1]])
+            bs.set_sweep_variant(1, *ETA_V[v[2]])
+            bs.set_sweep_variant(2, *ETA_V[v[3]])
+            bs.step(dt, 3)
+            for b in range(len(shapes)):
+                assert np.array_equal(bs.get_state(block=b), refs[b]), (v, b)
+    if precision == 0:
+        c = orc.Case(*shapes[1], **{k: v for k, v in params[1].items() if k != "precision"})
+        M = cases.expand_metrics(mets[1], shapes[1][::-1])
+        Uo = orc.step(c, M, states[1], dt, 3)
+        assert field_rel_err(refs[1], Uo) <= 1e-11
+
+
 def test_batch_rejects_mismatched_blocks():
     from paper_2209_15333_gb300 import _lib
     from paper_2209_15333_gb300.solver import BatchSolver

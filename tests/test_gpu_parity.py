@@ -256,15 +256,20 @@ SWEEP_VARIANTS = [((0, 0), (0, 128), 0), ((1, 0), (0, 5), 1), ((1, 128), (1, 32)
                   ((0, 0), (2, 0), 3), ((1, 0), (2, 8), 0), ((1, 256), (2, 13), 3)]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_sweep_variants_bit_identical(orc, precision):
+@pytest.mark.parametrize("precision,walled", [(0, True), (1, True), (1, False)])
+def test_sweep_variants_bit_identical(orc, precision, walled):
     """The per-segment and walking xi sweeps, the streaming, tiled and
     walking eta/zeta sweeps (any segment / tile length) and the node-parallel
-    and 2.5-D viscous kernels give identical bits; the autotuner only changes
-    speed.  Lines of 300 xi nodes span several walking chunks and segments."""
+    and 2.5-D viscous kernels give identical bits, and so do the sensor
+    classes (in FP32 the node-parallel and tiled viscous kernels also form the
+    plain sensor's classes, the 2.5-D ones leave them to the sensor kernel);
+    the autotuner only changes speed.  Lines of 300 xi nodes span several
+    walking chunks and segments; the periodic box takes the instantiations
+    for periodic lines with 8th-order viscous terms."""
     from paper_2209_15333_gb300.solver import Solver
     sh = (300, 21, 26)
-    bc = dict(bc_lo=(0, 3, 0), bc_hi=(0, 3, 0))   # one non-periodic direction too
+    # one non-periodic direction too, or every direction periodic
+    bc = dict(bc_lo=(0, 3, 0), bc_hi=(0, 3, 0)) if walled else dict(bc_lo=(0, 0, 0), bc_hi=(0, 0, 0))
     met = cases.uniform_metrics(*sh)
     U = turbulence_field(sh, 61)
     outs = []
@@ -277,11 +282,13 @@ def test_sweep_variants_bit_identical(orc, precision):
             s.set_sweep_variant(0, vk, 0)
             assert s.sweep_variant(3) == (xk, xs)
             L = s.rhs()
+            cls = s.flags()
             s.step(1e-3, 2)
-            outs.append((L, s.get_state()))
-    for L, V in outs[1:]:
-        assert np.array_equal(L, outs[0][0])
-        assert np.array_equal(V, outs[0][1])
+            outs.append((L, s.get_state(), cls, s.flags()))
+    assert len(np.unique(outs[0][2])) >= 2  # UD7 and WENO nodes occur
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
     if precision == 0:
         c = orc.Case(*sh, Re=150.0, Ma=0.5, scheme=3, theta1=0.004, theta2=0.012, **bc)
         Lo = orc.rhs(c, cases.expand_metrics(met, sh[::-1]), orc.apply_bc(c, cases.expand_metrics(met, sh[::-1]), U))
