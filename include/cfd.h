@@ -349,6 +349,12 @@ cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const
    nodes in x-y tiles (param ignored).  Ensembles offer three variants per
    kernel kind: viscous (2, 32), (1, 64), (3, 0); xi (0, 64), (0, 128),
    (1, 0); eta and zeta (1, 16), (1, 32), (2, 64).
+   dir 4 selects the learned sensor's classifier (single contexts and
+   ensembles; not tuned, and leaves the tuning alone): kind 0 runs the three
+   layers per warp with mma.sync, kind 1 (the default) per CTA on the tcgen05
+   tensor cores with the accumulators in tensor memory (param ignored).  The two forms add
+   the biases at different points of the FP32 accumulation, so a logit can
+   differ in its last bits between them.
    By default a context times the candidates on its first cfd_rhs / cfd_step
    and keeps the fastest; cfd_set_sweep_variant fixes one and turns the
    tuning off.  Choices are cached in the process and in a text file (the

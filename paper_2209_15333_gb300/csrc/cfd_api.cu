@@ -74,7 +74,9 @@ struct cfd_ctx {
     void* mlp_buf = nullptr;                    // w1, w2, w3 (bf16), b1, b2, b3 (f32), fallback counter
     void* powtab_buf = nullptr;                 // the power law's tables (double, then float)
     MlpArgs mlp{};
-    bool mlp_on = false;              // 0 node-parallel, 1 2.5-D TZ 64, 2 2.5-D TZ 32 (autotuned)
+    bool mlp_on = false;
+    int mlp_impl = 1;                 // learned sensor's classifier: 0 mma.sync per warp, 1 tcgen05 per CTA
+    int mlp_tc_grid = 0;              // persistent grid of the ensemble's tcgen05 walk
     bool tuned = false;
     // ensemble of blocks (cfd_create_batch): one single-block context per block
     // plus the tables that drive one persistent launch per kernel kind
@@ -853,12 +855,18 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
             // 32 x 8 columns walking zeta; the walk length balances the
             // waves of resident CTAs against the 7 planes each walk stages
             // before its first output
-            const size_t smem = sizeof(MlpWalkSmem);
-            static int per_sm[2] = {0, 0};
-            int& ps = per_sm[sizeof(R) == 4];
+            const bool tc = ctx->mlp_impl == 1;
+            const size_t smem = tc ? sizeof(MlpTcSmem) : sizeof(MlpWalkSmem);
+            static int per_sm[2][2] = {{0, 0}, {0, 0}};
+            int& ps = per_sm[tc][sizeof(R) == 4];
             if (!ps) {
-                cudaFuncSetAttribute(k_sensor_mlp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp<R>, 256, smem);
+                if (tc) {
+                    cudaFuncSetAttribute(k_sensor_mlp_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp_tc<R>, 256, smem);
+                } else {
+                    cudaFuncSetAttribute(k_sensor_mlp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp<R>, 256, smem);
+                }
                 ps = std::max(1, ps);
             }
             int sms = kSMs;
@@ -874,7 +882,8 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
                 if (cost < best) best = cost, tz = cz;
             }
             const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + tz - 1) / tz);
-            k_sensor_mlp<R><<<grid, 256, smem, sst>>>(A, ctx->mlp, tz);
+            if (tc) k_sensor_mlp_tc<R><<<grid, 256, smem, sst>>>(A, ctx->mlp, tz);
+            else k_sensor_mlp<R><<<grid, 256, smem, sst>>>(A, ctx->mlp, tz);
         } else if (mixed) {
             k_sensor32<<<nl.grid, nl.block, 0, sst>>>(A);
         } else {
@@ -1164,6 +1173,12 @@ static int batch_variant_in(int dir, int kind, int param);
 extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int param)
 {
     if (!ctx) return fail(nullptr, CFD_EINVAL, "null context");
+    if (dir == 4) {  // the learned sensor's classifier (not tuned; leaves the tuning alone)
+        if (kind < 0 || kind > 1) return fail(ctx, CFD_EINVAL, "classifier kind must be 0 (mma.sync) or 1 (tcgen05)");
+        ctx->mlp_impl = kind;
+        ctx->graph_valid = false;
+        return CFD_OK;
+    }
     if (!ctx->sub.empty()) {
         const int var = dir >= 0 && dir <= 3 ? batch_variant_in(dir, kind, param) : -1;
         if (var < 0) return fail(ctx, CFD_EINVAL, "not an ensemble kernel variant");
@@ -1202,7 +1217,12 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
 
 extern "C" cfd_status cfd_get_sweep_variant(cfd_ctx* ctx, int dir, int* kind, int* param)
 {
-    if (!ctx || !kind || !param || dir < 0 || dir > 3) return fail(ctx, CFD_EINVAL, "bad argument");
+    if (!ctx || !kind || !param || dir < 0 || dir > 4) return fail(ctx, CFD_EINVAL, "bad argument");
+    if (dir == 4) {
+        *kind = ctx->mlp_impl;
+        *param = 0;
+        return CFD_OK;
+    }
     if (!ctx->sub.empty()) {
         batch_variant_out(dir, ctx->bvar[dir == 0 ? KIND_VISC : (dir == 3 ? KIND_SX : (dir == 1 ? KIND_T1 : KIND_T2))],
                           kind, param);
@@ -1233,6 +1253,7 @@ static cfd_status read_err(cfd_ctx* ctx)
         CU(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
         if (h & 2) return fail(ctx, CFD_ECUDA, "index out of bounds (caught by the bounds-checked build)");
         if (h & 8) return fail(ctx, CFD_ECUDA, "a tensor-memory-accelerator copy did not complete in time");
+        if (h & 16) return fail(ctx, CFD_ECUDA, "a tensor-core (tcgen05) layer did not complete in time");
         return fail(ctx, CFD_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN) met on the device");
     }
     return CFD_OK;
@@ -1412,6 +1433,7 @@ static cudaError_t batch_kernel_attrs()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 1, EP_ACCUM, P8>, carve, maxs);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK, P8>, carve, maxs);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp<R>, dyn, (int)sizeof(MlpWalkSmem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp_tc<R>, dyn, (int)sizeof(MlpTcSmem));
     return e;
 }
 
@@ -1453,6 +1475,7 @@ static void batch_grids(cfd_ctx* ctx, const int totals[MAP_COUNT])
         persistent_grid(kb_sweep_t<R, 2, EP_FINAL_RK, 32, P8>, 256, tile_smem_bytes<R, 32>(), totals[MAP_T2 + 1]);
     mg[MAP_T2 + 2] = persistent_grid(kb_sweep_w<R, 2, EP_FINAL_RK, P8>, 256, walk_smem_bytes<R>(), totals[MAP_T2 + 2]);
     mg[MAP_MLP] = persistent_grid(kb_sensor_mlp<R>, 256, sizeof(MlpWalkSmem), totals[MAP_MLP]);
+    ctx->mlp_tc_grid = persistent_grid(kb_sensor_mlp_tc<R>, 256, sizeof(MlpTcSmem), totals[MAP_MLP]);
 }
 
 static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids, const double* const* metrics,
@@ -1725,8 +1748,12 @@ static cfd_status enqueue_batch_stage(cfd_ctx* ctx, int s, cudaEvent_t* ev)
     if (mixed || ctx->prm.scheme == CFD_HYBRID) {
         if (ctx->prm.sensor == CFD_SENSOR_MLP) {
             if (!ctx->mlp_on) return fail(ctx, CFD_EINVAL, "learned sensor selected but no weights set");
-            kb_sensor_mlp<R><<<ctx->map_grid[MAP_MLP], 256, sizeof(MlpWalkSmem), st>>>(m[MAP_MLP], ctx->mlp,
-                                                                                       kBatchMlpTZ);
+            if (ctx->mlp_impl == 1)
+                kb_sensor_mlp_tc<R><<<ctx->mlp_tc_grid, 256, sizeof(MlpTcSmem), st>>>(m[MAP_MLP], ctx->mlp,
+                                                                                      kBatchMlpTZ);
+            else
+                kb_sensor_mlp<R><<<ctx->map_grid[MAP_MLP], 256, sizeof(MlpWalkSmem), st>>>(m[MAP_MLP], ctx->mlp,
+                                                                                           kBatchMlpTZ);
             LAUNCH_CHECK();
         } else if (mixed) {
             // (the viscous node tiles may form these classes instead)

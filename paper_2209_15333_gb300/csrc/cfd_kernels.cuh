@@ -13,6 +13,7 @@
 //   metf         [31][M] float   the same metrics rounded once, read by the FP32 kernels
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda.h>  // CUtensorMap (tensor-memory-accelerator descriptors); no driver calls here
 
@@ -783,12 +784,214 @@ struct MlpWalkSmem {
     MlpWeightsSmem w;
 };
 
-// one column's walk (vb: column x, column y, zeta segment); the weights are
-// staged in S.w before the call
-template <class RT>
-__device__ __forceinline__ void sensor_mlp_col(const SweepArgs& A, const MlpArgs& W, MlpWalkSmem& S, uint3 vb,
-                                               int tz)
+// ---------------------------------------------------------------------------
+// The same three layers on the fifth-generation tensor cores (tcgen05, inline
+// PTX).  A CTA's 256 feature rows (its 32 x 8 nodes of one plane) form two
+// M = 128 tiles; one thread issues the MMAs of a layer (bf16 operands from
+// shared memory, FP32 accumulators in tensor memory) and commits them to an
+// mbarrier; every warp then reads its own 32 rows back (tcgen05.ld: warp w
+// reaches lanes 32 (w mod 4) ..), adds the biases, applies ReLU and writes the
+// next layer's bf16 operand.  Operands are K-major without swizzle: "core
+// matrices" of 8 rows x 16 bytes stored contiguously, the K-adjacent ones 128
+// bytes apart (leading byte offset), the 8-row groups KC x 128 bytes apart
+// (stride byte offset), KC = K / 8.  Biases are added to the accumulators
+// after the products (the warp-level form starts from them), so the two
+// forms can differ in the last bits of a logit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor (start address, leading and stride byte
+// offsets in 16-byte units, descriptor version 1, no swizzle)
+__device__ __forceinline__ uint64_t tc_smem_desc(const void* p, uint32_t lbo, uint32_t sbo)
 {
+    const uint64_t a = smem_u32(p);
+    return ((a >> 4) & 0x3FFFull) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), bf16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N / 8 at bit 17, M / 16 at bit 24
+constexpr uint32_t tc_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)acc)
+        : "memory");
+}
+// arrive on the mbarrier once every MMA this thread issued has completed
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 32 columns of this thread's tensor-memory lane (load and its wait in one
+// statement, so that no use of v can be scheduled before the wait)
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld_x4(uint32_t taddr, float (&v)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"(taddr)
+                 : "memory");
+}
+// tensor-memory columns of one CTA (a power of two >= 32), allocated by warp 0
+constexpr uint32_t MLP_TMEM_COLS = 64;
+__device__ __forceinline__ void tmem_alloc_warp(uint32_t* slot)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n\t"
+                 "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::"r"(smem_u32(slot)),
+                 "r"(MLP_TMEM_COLS)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_warp(uint32_t base)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(MLP_TMEM_COLS) : "memory");
+}
+
+// shared memory of the tensor-core walk: the p / rho ring of the warp-level
+// form, the operand tile and the weights, all in the core-matrix layout.  The
+// operand tile holds the features (K = 48) and, once a layer's MMAs have
+// completed, the hidden activations that feed the next (K = 32): 65 KB, three
+// CTAs per SM
+struct MlpTcSmem {
+    float ring[MW_RING][2][MW_PL];
+    alignas(16) uint16_t ax[2 * 16 * 6 * 64];  // [tile][row group][K chunk][8 x 8]
+    alignas(16) uint16_t w1[4 * 6 * 64];       // [n group][K chunk][8 x 8], N = 32, K = 48
+    alignas(16) uint16_t w2[4 * 4 * 64];       // N = 32, K = 32
+    alignas(16) uint16_t w3[2 * 4 * 64];       // N = 16 (rows 3..15 zero), K = 32
+    float b[32 + 32 + 8];
+    uint64_t bar;
+    uint32_t tmem;
+};
+// element (row, k) of a core-matrix tile with KC chunks of 8 along K
+__device__ __forceinline__ int tc_off(int row, int k, int KC)
+{
+    return (((row >> 3) * KC + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+// weights to shared memory, the mbarrier, and the CTA's tensor memory
+__device__ __forceinline__ void mlp_tc_setup(MlpTcSmem& S, const MlpArgs& W)
+{
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int e = t; e < 32 * MLP_KP; e += nt) S.w1[tc_off(e / MLP_KP, e % MLP_KP, 6)] = W.w1[e];
+    for (int e = t; e < 32 * 32; e += nt) S.w2[tc_off(e / 32, e % 32, 4)] = W.w2[e];
+    for (int e = t; e < 16 * 32; e += nt) S.w3[tc_off(e / 32, e % 32, 4)] = e < 8 * 32 ? W.w3[e] : (uint16_t)0;
+    for (int e = t; e < 72; e += nt) S.b[e] = e < 32 ? W.b1[e] : (e < 64 ? W.b2[e - 32] : W.b3[e - 64]);
+    if (t == 0) {
+        mbar_init(&S.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (t < 32) tmem_alloc_warp(&S.tmem);
+    fence_proxy_async_smem();  // the weights, for the tensor cores' reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+__device__ __forceinline__ void mlp_tc_teardown(MlpTcSmem& S)
+{
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        tmem_dealloc_warp(S.tmem);
+    }
+}
+
+// bias, ReLU and bf16 packing of one row's 32 accumulators into the hidden tile
+__device__ __forceinline__ void mlp_tc_hidden(MlpTcSmem& S, const float (&v)[32], const float* bias, int tile, int rr)
+{
+    uint16_t* h = S.ax + tile * (16 * 4 * 64);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t q[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            q[e] = relu_bf16x2(pack_bf16x2(v[8 * c + 2 * e] + bias[8 * c + 2 * e], v[8 * c + 2 * e + 1] + bias[8 * c + 2 * e + 1]));
+        *reinterpret_cast<uint4*>(h + tc_off(rr, 8 * c, 4)) = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+}
+
+// one layer's MMAs for both row tiles (thread 0), committed to the mbarrier;
+// then every thread waits for them (bounded; flag 16 of the error word if
+// they did not complete)
+template <int KC, int N>
+__device__ __forceinline__ bool mlp_tc_layer(MlpTcSmem& S, const uint16_t* a, const uint16_t* b, uint32_t& phase,
+                                             int* err)
+{
+    if (threadIdx.x == 0) {
+        tc_fence_after();
+        constexpr uint32_t idesc = tc_idesc_bf16(128, N);
+#pragma unroll
+        for (int tile = 0; tile < 2; ++tile)
+#pragma unroll
+            for (int ks = 0; ks < KC / 2; ++ks)
+                tc_mma_bf16(S.tmem + (uint32_t)(tile * 32), tc_smem_desc(a + tile * (16 * KC * 64) + ks * 128, 128, KC * 128),
+                            tc_smem_desc(b + ks * 128, 128, KC * 128), idesc, ks > 0);
+        tc_commit(&S.bar);
+    }
+    const bool ok = mbar_wait_bounded(&S.bar, phase & 1u, TW_WAIT_LIMIT);
+    ++phase;
+    if (!ok && err) atomicOr(err, 16);
+    tc_fence_after();
+    return ok;
+}
+
+// the class of this thread's row (row = warp * 32 + lane of the feature tile
+// S.ax, written by the caller); -1 where the top softmax probability is below
+// conf_min, not finite, or a wait gave up.  Every thread of the CTA calls it.
+__device__ __forceinline__ int mlp_classify_tc(MlpTcSmem& S, float conf_min, uint32_t& phase, int* err)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = w >> 2, rr = (w & 3) * 32 + lane;
+    const uint32_t trow = S.tmem + ((uint32_t)((w & 3) * 32) << 16) + (uint32_t)(tile * 32);
+    fence_proxy_async_smem();  // this thread's feature rows, for the tensor cores
+    __syncthreads();
+    bool ok = mlp_tc_layer<6, 32>(S, S.ax, S.w1, phase, err);
+    float v[32];
+    tmem_ld_x32(trow, v);
+    mlp_tc_hidden(S, v, S.b, tile, rr);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    ok = mlp_tc_layer<4, 32>(S, S.ax, S.w2, phase, err) && ok;
+    tmem_ld_x32(trow, v);
+    // (the completed MMAs have read their operand: the tile is free)
+    mlp_tc_hidden(S, v, S.b + 32, tile, rr);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    ok = mlp_tc_layer<4, 16>(S, S.ax, S.w3, phase, err) && ok;
+    float lg[4];
+    tmem_ld_x4(trow, lg);
+    tc_fence_before();  // the next plane's MMAs overwrite these columns
+    const float c0 = lg[0] + S.b[64], c1 = lg[1] + S.b[65], c2 = lg[2] + S.b[66];
+    const float mx = fmaxf(c0, fmaxf(c1, c2));
+    const float z = __expf(c0 - mx) + __expf(c1 - mx) + __expf(c2 - mx);
+    const int arg = c0 >= c1 ? (c0 >= c2 ? 0 : 2) : (c1 >= c2 ? 1 : 2);
+    return (ok && 1.0f / z >= conf_min && isfinite(z)) ? arg : -1;
+}
+
+// one column's walk (vb: column x, column y, zeta segment); the weights are
+// staged before the call.  SM = MlpWalkSmem: each warp classifies its rows
+// with mma.sync; SM = MlpTcSmem: the CTA classifies its 256 rows with tcgen05
+// (phase: the CTA's count of completed mbarrier phases)
+template <class RT, class SM>
+__device__ __forceinline__ void sensor_mlp_col(const SweepArgs& A, const MlpArgs& W, SM& S, uint3 vb, int tz,
+                                               uint32_t& phase)
+{
+    constexpr bool TC = std::is_same<SM, MlpTcSmem>::value;
     const Geo& g = A.g;
     const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -834,7 +1037,16 @@ __device__ __forceinline__ void sensor_mlp_col(const SweepArgs& A, const MlpArgs
     const int i = x0 + tx, j = y0 + ty;
     const bool own = i < nx && j < ny;
     const int ctr = (ty + 3) * MW_X + tx + 3;  // the node in a staged plane
-    uint16_t* sxw = S.sx + ty * 32 * MLP_ROW;   // this warp's feature rows
+    // this thread's feature row: chunks of 8 features, 16 bytes each
+    uint4* row;
+    if constexpr (TC) {
+        const int rr = (ty & 3) * 32 + tx;  // row within tile ty / 4
+        row = reinterpret_cast<uint4*>(S.ax + (ty >> 2) * (16 * 6 * 64) + tc_off(rr, 0, 6));
+    } else {
+        row = reinterpret_cast<uint4*>(S.sx + (ty * 32 + tx) * MLP_ROW);
+    }
+    // consecutive chunks of a row: 16 bytes apart, or one core matrix (128 bytes)
+    constexpr int CS = TC ? 8 : 1;
     for (int z = z0; z < z1; ++z) {
         // plane z+4 is read by the outputs up to z1-1 while z+4 <= z1+2
         const bool more = z + 4 <= z1 + 2;
@@ -845,7 +1057,6 @@ __device__ __forceinline__ void sensor_mlp_col(const SweepArgs& A, const MlpArgs
         // finiteness for all (x * 0 is 0 for finite x, NaN otherwise)
         const float* c0 = S.ring[z & (MW_RING - 1)][0];
         const float inv[2] = {1.0f / c0[ctr], 1.0f / c0[MW_PL + ctr]};
-        uint4* row = reinterpret_cast<uint4*>(sxw + tx * MLP_ROW);
         float zc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         uint32_t w[4];
         float lo = 0.0f;
@@ -867,21 +1078,26 @@ __device__ __forceinline__ void sensor_mlp_col(const SweepArgs& A, const MlpArgs
                     zc[e & 3] = fmaf(o[q], 0.0f, zc[e & 3]);
                     if (e & 1) w[(e >> 1) & 3] = pack_bf16x2(lo, o[q]);
                     else lo = o[q];
-                    if ((e & 7) == 7) row[e >> 3] = make_uint4(w[0], w[1], w[2], w[3]);
+                    if ((e & 7) == 7) row[(e >> 3) * CS] = make_uint4(w[0], w[1], w[2], w[3]);
                 }
             }
         // features 42..47 are zero padding
         w[1] = pack_bf16x2(lo, 0.0f);
-        row[5] = make_uint4(w[0], w[1], 0u, 0u);
+        row[5 * CS] = make_uint4(w[0], w[1], 0u, 0u);
         // plane z+4 takes the slot of plane z-4 (no reader since the last barrier)
         if (more) store_plane(z + 4, nxt);
         const bool bad = !own || !((zc[0] + zc[1]) + (zc[2] + zc[3]) == 0.0f);
         if (bad) {
 #pragma unroll
-            for (int q = 0; q < MLP_KP / 8; ++q) row[q] = make_uint4(0u, 0u, 0u, 0u);
+            for (int q = 0; q < MLP_KP / 8; ++q) row[q * CS] = make_uint4(0u, 0u, 0u, 0u);
         }
-        __syncwarp();
-        const int cls = mlp_classify_warp(sxw, S.w, W.conf_min);
+        int cls;
+        if constexpr (TC) {
+            cls = mlp_classify_tc(S, W.conf_min, phase, A.err);
+        } else {
+            __syncwarp();
+            cls = mlp_classify_warp(S.sx + ty * 32 * MLP_ROW, S.w, W.conf_min);
+        }
         if (own) {
             const long long n = (long long)i + (long long)nx * ((long long)j + (long long)ny * z);
             int c = cls;
@@ -901,7 +1117,19 @@ __global__ void __launch_bounds__(256, 2) k_sensor_mlp(SweepArgs A, MlpArgs W, i
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlpWalkSmem& S = *reinterpret_cast<MlpWalkSmem*>(smem_raw);
     mlp_stage_weights(S.w, W);
-    sensor_mlp_col<RT>(A, W, S, blockIdx, tz);
+    uint32_t phase = 0;
+    sensor_mlp_col<RT>(A, W, S, blockIdx, tz, phase);
+}
+// the walk with the layers on tcgen05 (tensor memory held for the CTA's life)
+template <class RT>
+__global__ void __launch_bounds__(256, 3) k_sensor_mlp_tc(SweepArgs A, MlpArgs W, int tz)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpTcSmem& S = *reinterpret_cast<MlpTcSmem*>(smem_raw);
+    mlp_tc_setup(S, W);
+    uint32_t phase = 0;
+    sensor_mlp_col<RT>(A, W, S, blockIdx, tz, phase);
+    mlp_tc_teardown(S);
 }
 
 // the 42 features of every node (for training data and tests), [42][N] float
@@ -3422,8 +3650,20 @@ __global__ void __launch_bounds__(256, 2) kb_sensor_mlp(BatchMap m, MlpArgs W, i
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlpWalkSmem& S = *reinterpret_cast<MlpWalkSmem*>(smem_raw);
     mlp_stage_weights(S.w, W);
-    auto body = [&](const SweepArgs& A, uint3 v) { sensor_mlp_col<RT>(A, W, S, v, tz); };
+    uint32_t phase = 0;
+    auto body = [&](const SweepArgs& A, uint3 v) { sensor_mlp_col<RT>(A, W, S, v, tz, phase); };
     BATCH_LOOP(body, true, false)
+}
+template <class RT>
+__global__ void __launch_bounds__(256, 3) kb_sensor_mlp_tc(BatchMap m, MlpArgs W, int tz)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpTcSmem& S = *reinterpret_cast<MlpTcSmem*>(smem_raw);
+    mlp_tc_setup(S, W);
+    uint32_t phase = 0;
+    auto body = [&](const SweepArgs& A, uint3 v) { sensor_mlp_col<RT>(A, W, S, v, tz, phase); };
+    BATCH_LOOP(body, true, false)
+    mlp_tc_teardown(S);
 }
 template <class R, int TZ>
 __global__ void __launch_bounds__(256) kb_visc_flux25(BatchMap m) { BATCH_LOOP((visc25_body<R, TZ>), true, false) }

@@ -78,8 +78,8 @@ def _mlp_weights(seed):
             rng.normal(0, 0.1, 32), rng.normal(0, 0.1, 32), rng.normal(0, 0.1, 3))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batch_learned_sensor_matches_single_block_contexts(precision):
+@pytest.mark.parametrize("precision,impl", [(0, 0), (1, 0), (1, 1)])
+def test_batch_learned_sensor_matches_single_block_contexts(precision, impl):
     """The learned sensor in an ensemble (one launch walks the zeta columns
     of all blocks, with partial columns, clamped lines and ragged segments)
     gives every block the classes, fallbacks and state of its own context."""
@@ -91,6 +91,7 @@ def test_batch_learned_sensor_matches_single_block_contexts(precision):
         for b, U in enumerate(states):
             bs.set_state(U, block=b)
         bs.set_sensor_mlp(*W, conf_min=0.6)
+        bs.set_sweep_variant(4, impl, 0)
         bs.sensor_fallbacks()
         bs.step(dt, 3)
         got = [bs.get_state(block=b) for b in range(len(SHAPES))]
@@ -103,6 +104,7 @@ def test_batch_learned_sensor_matches_single_block_contexts(precision):
         with Solver(sh, mets[b], bc_lo=lo, bc_hi=hi, **params[b]) as s:
             s.set_state(states[b])
             s.set_sensor_mlp(*W, conf_min=0.6)
+            s.set_sweep_variant(4, impl, 0)
             s.step(dt, 3)
             assert np.array_equal(s.flags(), cls[b]), b
             assert np.array_equal(s.get_state(), got[b]), b

@@ -103,8 +103,13 @@ MLP_CASES = [(0, (40, 24, 20), 0, 0), (1, (40, 24, 20), 0, 0), (1, (132, 12, 10)
              (1, (45, 13, 27), 0, 3), (1, (33, 9, 70), 3, 3)]
 
 
+# the classifier: 0 mma.sync per warp, 1 tcgen05 per CTA (tensor memory)
+IMPLS = [0, 1]
+
+
+@pytest.mark.parametrize("impl", IMPLS)
 @pytest.mark.parametrize("precision,sh,xbc,zbc", MLP_CASES)
-def test_mlp_classes_match_numpy_forward_pass(precision, sh, xbc, zbc):
+def test_mlp_classes_match_numpy_forward_pass(precision, sh, xbc, zbc, impl):
     from paper_2209_15333_gb300.solver import Solver
     U = turbulence_field(sh, 92) if zbc == 0 else steep_field(sh, 92)
     W = random_weights(5)
@@ -113,6 +118,8 @@ def test_mlp_classes_match_numpy_forward_pass(precision, sh, xbc, zbc):
         s.set_state(U)
         F = s.sensor_features()
         s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=0.0)
+        s.set_sweep_variant(4, impl, 0)
+        assert s.sweep_variant(4) == (impl, 0)
         s.rhs()
         got = s.flags().ravel()
         assert s.sensor_fallbacks() == 0
@@ -126,7 +133,8 @@ def test_mlp_classes_match_numpy_forward_pass(precision, sh, xbc, zbc):
     assert len(np.unique(want)) >= 2
 
 
-def test_mlp_fallback_to_plain_sensor():
+@pytest.mark.parametrize("impl", IMPLS)
+def test_mlp_fallback_to_plain_sensor(impl):
     from paper_2209_15333_gb300.solver import Solver
     sh = (32, 16, 16)
     U = turbulence_field(sh, 93)
@@ -138,6 +146,7 @@ def test_mlp_fallback_to_plain_sensor():
         W = random_weights(6, scale=0.5)
         # small logits: no softmax probability rounds to 1, so every node falls back
         s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=1.0)
+        s.set_sweep_variant(4, impl, 0)
         s.rhs()
         assert np.array_equal(s.flags(), plain)
         assert s.sensor_fallbacks() == plain.size
@@ -171,3 +180,32 @@ def test_packaged_model_against_plain_sensor():
           % ((plain > 0).mean(), mis, unsafe, fb))
     assert (plain > 0).any()
     assert mis < 0.01 and unsafe < 0.002 and fb < 0.05
+
+
+def test_mlp_classifier_forms_agree():
+    """The two classifiers (mma.sync per warp, tcgen05 per CTA) on the same
+    features: the same classes wherever the top logit leads by more than the
+    accumulation-order tolerance, over several planes and partial columns."""
+    from paper_2209_15333_gb300.solver import Solver
+    sh = (70, 20, 40)
+    U = steep_field(sh, 94)
+    W = random_weights(8)
+    got = []
+    for impl in IMPLS:
+        with Solver(sh, cases.uniform_metrics(*sh), precision=1, scheme=3, Re=100.0) as s:
+            s.set_state(U)
+            F = s.sensor_features()
+            s.set_sensor_mlp(W["w1"], W["w2"], W["w3"], W["b1"], W["b2"], W["b3"], conf_min=0.0)
+            s.set_sweep_variant(4, impl, 0)
+            s.rhs()
+            got.append(s.flags().ravel())
+    logits = mlp_numpy(F, W)
+    srt = np.sort(logits, axis=1)
+    sure = (srt[:, -1] - srt[:, -2]) > 1e-2 * (1.0 + np.abs(logits).max(axis=1))
+    assert sure.mean() > 0.9
+    assert np.array_equal(got[0][sure], got[1][sure])
+    assert (got[0] != got[1]).mean() < 1e-3
+    with Solver(sh, cases.uniform_metrics(*sh), precision=1) as s:
+        from paper_2209_15333_gb300 import _lib as L
+        with pytest.raises(L.CfdError):
+            s.set_sweep_variant(4, 2, 0)
