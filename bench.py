@@ -533,6 +533,8 @@ def rooflines(form, r, N, peaks, fma, src_hash, world):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_per_node": ALG_BYTES_PER_POINT_STAGE, "kernel_ms": prof}
         cb = MIXED_BYTES_LEARNED_SENSOR if (form == "mixed_learned" and dom == "sensor") else MIXED_BYTES[dom]
+        if form == "mixed" and dom == "visc_flux" and r["variants"]["visc"][0] in (0, 3):
+            cb += MIXED_BYTES["sensor"]  # the node-flux kernels also form the plain sensor's classes
         kc = cb * N / (prof[dom] * 1e-3) / 1e9
         roof["kernel_compulsory"] = {"kernel": dom, "bytes_per_node": cb, "achieved_gbs": kc,
                                      "frac": kc / peaks["hbm_gbs"]}
