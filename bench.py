@@ -61,25 +61,25 @@ ALG_BYTES_PER_POINT_STAGE = 40.0 + 80.0 / 3.0 + 40.0
 # it; the RHS epilogue for zeta, as cfd_profile_stage runs it); valid only
 # for the kernel sources with hash prefix "src".
 NCU_TRAFFIC = {
-    "src": "56404054b551", "nodes": 256 ** 3,
-    "fp64": {"prim": [{"variant": None, "bytes_per_launch": 1554651648}],
-             "sensor": [{"variant": None, "bytes_per_launch": 145527296}],
-             "visc_flux": [{"variant": [0, 0], "bytes_per_launch": 2155866368}],
-             "sweep_xi": [{"variant": [1, 0], "bytes_per_launch": 1864078080}],
-             "sweep_eta": [{"variant": [2, 0], "bytes_per_launch": 2574135296}],
-             "sweep_zeta": [{"variant": [2, 64], "bytes_per_launch": 2699531520}]},
+    "src": "b90c10119ebc", "nodes": 256 ** 3,
+    "fp64": {"prim": [{"variant": None, "bytes_per_launch": 1554652672}],
+             "sensor": [{"variant": None, "bytes_per_launch": 145433856}],
+             "visc_flux": [{"variant": [0, 0], "bytes_per_launch": 2157005056}],
+             "sweep_xi": [{"variant": [1, 0], "bytes_per_launch": 1863278336}],
+             "sweep_eta": [{"variant": [2, 0], "bytes_per_launch": 2574391040}],
+             "sweep_zeta": [{"variant": [2, 64], "bytes_per_launch": 2696522496}]},
     # FP32 bulk, plain sensor: the node-parallel (0) and tiled (3) viscous
     # kernels also form the sensor's classes (no sensor launch of its own)
-    "mixed": {"prim": [{"variant": None, "bytes_per_launch": 1111162880}],
-              "visc_flux": [{"variant": [0, 0], "bytes_per_launch": 1114860288},
-                            {"variant": [3, 0], "bytes_per_launch": 1122803968}],
-              "sweep_xi": [{"variant": [0, 0], "bytes_per_launch": 923160320}],
-              "sweep_eta": [{"variant": [1, 16], "bytes_per_launch": 1390886400}],
-              "sweep_zeta": [{"variant": [1, 16], "bytes_per_launch": 1882916096}]},
+    "mixed": {"prim": [{"variant": None, "bytes_per_launch": 1111171072}],
+              "visc_flux": [{"variant": [0, 0], "bytes_per_launch": 1114907392},
+                            {"variant": [3, 0], "bytes_per_launch": 1122263808}],
+              "sweep_xi": [{"variant": [0, 0], "bytes_per_launch": 923300864}],
+              "sweep_eta": [{"variant": [1, 16], "bytes_per_launch": 1390976768}],
+              "sweep_zeta": [{"variant": [1, 16], "bytes_per_launch": 1883188224}]},
     # learned sensor (tcgen05 classifier) and the viscous tiles without the
     # plain sensor; the sweeps are those of "mixed"
-    "mixed_learned": {"sensor": [{"variant": None, "bytes_per_launch": 149446656}],
-                      "visc_flux": [{"variant": [3, 0], "bytes_per_launch": 1029201664}]},
+    "mixed_learned": {"sensor": [{"variant": None, "bytes_per_launch": 149448448}],
+                      "visc_flux": [{"variant": [3, 0], "bytes_per_launch": 1029302784}]},
 }
 
 

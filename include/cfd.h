@@ -351,9 +351,10 @@ cfd_status cfd_rhs_noalloc(const cfd_grid* grid, const cfd_params* params, const
    (1, 0); eta and zeta (1, 16), (1, 32), (2, 64).
    dir 4 selects the learned sensor's classifier (single contexts and
    ensembles; not tuned, and leaves the tuning alone): kind 0 runs the three
-   layers per warp with mma.sync (the ensembles' default), kind 1 per CTA on
-   the tcgen05 tensor cores with the accumulators in tensor memory (the
-   single contexts' default; param ignored).  The two forms add
+   layers per warp with mma.sync, kind 1 per CTA on the tcgen05 tensor cores
+   with the accumulators in tensor memory (param ignored).  Single contexts
+   use kind 1; an ensemble with the learned sensor times both on its first
+   cfd_step and keeps the faster, unless one was fixed here.  The two forms add
    the biases at different points of the FP32 accumulation, so a logit can
    differ in its last bits between them.
    By default a context times the candidates on its first cfd_rhs / cfd_step

@@ -76,6 +76,7 @@ struct cfd_ctx {
     MlpArgs mlp{};
     bool mlp_on = false;
     int mlp_impl = 1;                 // learned sensor's classifier: 0 mma.sync per warp, 1 tcgen05 per CTA
+    bool mlp_tuned = false;           // ensembles: classifier timed (or fixed by cfd_set_sweep_variant)
     int mlp_tc_grid = 0;              // persistent grid of the ensemble's tcgen05 walk
     bool tuned = false;
     // ensemble of blocks (cfd_create_batch): one single-block context per block
@@ -860,11 +861,18 @@ static cfd_status run_stage_t(cfd_ctx* ctx, const double* Uin, const double* Un,
             static int per_sm[2][2] = {{0, 0}, {0, 0}};
             int& ps = per_sm[tc][sizeof(R) == 4];
             if (!ps) {
+                // (the shared-memory carveout preference first: without it the
+                // occupancy query assumed one CTA per SM, and the walks were
+                // sized for that)
+                const auto carve = cudaFuncAttributePreferredSharedMemoryCarveout;
+                const int maxs = (int)cudaSharedmemCarveoutMaxShared;
                 if (tc) {
                     cudaFuncSetAttribute(k_sensor_mlp_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    cudaFuncSetAttribute(k_sensor_mlp_tc<R>, carve, maxs);
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp_tc<R>, 256, smem);
                 } else {
                     cudaFuncSetAttribute(k_sensor_mlp<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    cudaFuncSetAttribute(k_sensor_mlp<R>, carve, maxs);
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_sensor_mlp<R>, 256, smem);
                 }
                 ps = std::max(1, ps);
@@ -1176,6 +1184,7 @@ extern "C" cfd_status cfd_set_sweep_variant(cfd_ctx* ctx, int dir, int kind, int
     if (dir == 4) {  // the learned sensor's classifier (not tuned; leaves the tuning alone)
         if (kind < 0 || kind > 1) return fail(ctx, CFD_EINVAL, "classifier kind must be 0 (mma.sync) or 1 (tcgen05)");
         ctx->mlp_impl = kind;
+        ctx->mlp_tuned = true;
         ctx->graph_valid = false;
         return CFD_OK;
     }
@@ -1434,6 +1443,8 @@ static cudaError_t batch_kernel_attrs()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sweep_w<R, 2, EP_FINAL_RK, P8>, carve, maxs);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp<R>, dyn, (int)sizeof(MlpWalkSmem));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp_tc<R>, dyn, (int)sizeof(MlpTcSmem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp<R>, carve, maxs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_sensor_mlp_tc<R>, carve, maxs);
     return e;
 }
 
@@ -1858,6 +1869,57 @@ static cfd_status batch_autotune_t(cfd_ctx* ctx)
     return st;
 }
 
+// Ensembles with the learned sensor: time both classifiers (mma.sync and
+// tcgen05) once on the live work list and keep the faster.  The trial launches
+// count no fallbacks, and the classes the mixed recovery reads next are saved
+// and restored around them.
+template <class R>
+static cfd_status batch_tune_mlp_t(cfd_ctx* ctx)
+{
+    const cudaStream_t st = ctx->stream;
+    const BatchMap* m = ctx->maps[0];
+    for (cfd_ctx* sb : ctx->sub)
+        CU(cudaMemcpyAsync(sb->b.cls_tune, sb->b.cls, sb->g.N, cudaMemcpyDeviceToDevice, st));
+    // primitives of the state, which the features read
+    if (sizeof(R) == sizeof(float)) kb_prim_mixed<<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+    else kb_prim<double><<<ctx->map_grid[MAP_NODE], 128, 0, st>>>(m[MAP_NODE]);
+    LAUNCH_CHECK();
+    MlpArgs W = ctx->mlp;
+    W.fallbacks = nullptr;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    cfd_status res = CFD_OK;
+    for (int impl = 0; impl < 2 && res == CFD_OK; ++impl) {
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, st);
+            if (impl == 1)
+                kb_sensor_mlp_tc<R><<<ctx->mlp_tc_grid, 256, sizeof(MlpTcSmem), st>>>(m[MAP_MLP], W, kBatchMlpTZ);
+            else
+                kb_sensor_mlp<R><<<ctx->map_grid[MAP_MLP], 256, sizeof(MlpWalkSmem), st>>>(m[MAP_MLP], W, kBatchMlpTZ);
+            ++ctx->launches;
+            if (cudaGetLastError() != cudaSuccess) res = fail(ctx, CFD_ECUDA, "classifier trial launch");
+        }
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) res = fail(ctx, CFD_ECUDA, "classifier timing");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (res == CFD_OK && ms < best) {
+            best = ms;
+            ctx->mlp_impl = impl;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (res != CFD_OK) return res;
+    for (cfd_ctx* sb : ctx->sub)
+        CU(cudaMemcpyAsync(sb->b.cls, sb->b.cls_tune, sb->g.N, cudaMemcpyDeviceToDevice, st));
+    ctx->mlp_tuned = true;
+    ctx->graph_valid = false;
+    return read_err(ctx);
+}
+
 static cfd_status batch_autotune(cfd_ctx* ctx)
 {
     if (ctx->tuned) return CFD_OK;
@@ -1984,6 +2046,9 @@ extern "C" cfd_status cfd_step(cfd_ctx* ctx, double dt, int nsteps)
     LAUNCH_CHECK();
     {
         cfd_status st = ctx->sub.empty() ? autotune(ctx) : batch_autotune(ctx);
+        if (st != CFD_OK) return st;
+        if (!ctx->sub.empty() && ctx->mlp_on && !ctx->mlp_tuned && ctx->prm.sensor == CFD_SENSOR_MLP)
+            st = ctx->prm.precision == CFD_FP32_BULK ? batch_tune_mlp_t<float>(ctx) : batch_tune_mlp_t<double>(ctx);
         if (st != CFD_OK) return st;
     }
     if (!ctx->graph_valid) {

@@ -114,6 +114,33 @@ def test_batch_learned_sensor_matches_single_block_contexts(precision, impl):
     assert len(kinds) >= 2
 
 
+def test_batch_classifier_timed_once():
+    """With the learned sensor and no classifier fixed, an ensemble times both
+    classifiers on its first step and keeps one; the run then gives the bits
+    (states, classes, fallbacks) of the same ensemble with that classifier fixed."""
+    from paper_2209_15333_gb300.solver import BatchSolver
+    mets, params, states = _blocks(1)
+    W = _mlp_weights(12)
+    runs = []
+    for fixed in (None, "picked"):
+        with BatchSolver(SHAPES, mets, params, bcs=BCS) as bs:
+            for b, U in enumerate(states):
+                bs.set_state(U, block=b)
+            bs.set_sensor_mlp(*W, conf_min=0.6)
+            if fixed is not None:
+                bs.set_sweep_variant(4, runs[0][0], 0)
+            bs.sensor_fallbacks()
+            bs.step(5e-4, 2)
+            impl = bs.sweep_variant(4)[0]
+            runs.append((impl, [bs.get_state(block=b) for b in range(len(SHAPES))],
+                         [bs.flags(block=b) for b in range(len(SHAPES))], bs.sensor_fallbacks()))
+    assert runs[0][0] in (0, 1) and runs[1][0] == runs[0][0]
+    for b in range(len(SHAPES)):
+        assert np.array_equal(runs[0][1][b], runs[1][1][b]), b
+        assert np.array_equal(runs[0][2][b], runs[1][2][b]), b
+    assert runs[0][3] == runs[1][3]
+
+
 # ensemble variants as (kind, param): viscous (dir 0), xi (dir 3), eta/zeta (dirs 1, 2)
 VISC_V = [(2, 32), (1, 64), (3, 0)]
 XI_V = [(0, 64), (0, 128), (1, 0)]
