@@ -1509,10 +1509,10 @@ static cfd_status create_batch_inner(cfd_ctx* ctx, int nb, const cfd_grid* grids
     CU(cudaMemsetAsync(ctx->t, 0, sizeof(double), ctx->stream));
     ctx->ph = Phys{};
     ctx->ph.viscous = params[0].Re > 0.0;
-    // ensembles classify with mma.sync by default: the persistent tcgen05 walk
-    // over short segments of small blocks measured slower (1.54 against 0.83 ms
-    // per stage on 48 blocks of 32..128 nodes per axis), while a single box
-    // gains from it (0.56 against 0.62 ms at 256^3)
+    // the classifier an ensemble starts with; with the learned sensor its first
+    // step times both and keeps the faster (on 48 blocks of 32..128 nodes per
+    // axis the persistent tcgen05 walk measured 1.54 against 0.83 ms per stage,
+    // while a single 256^3 box gains from it, 0.56 against 0.62 ms)
     ctx->mlp_impl = 0;
     for (int b = 0; b < nb; ++b) {
         cfd_ctx* sb = new (std::nothrow) cfd_ctx();
