@@ -41,6 +41,8 @@ GAMMA = 1.4
 KERNEL_NAMES = ["prim", "sensor", "visc_flux", "sweep_xi", "sweep_eta", "sweep_zeta"]
 FORMS = {"fp64": dict(precision=0, learned=False), "mixed": dict(precision=1, learned=False),
          "mixed_learned": dict(precision=1, learned=True)}
+# the learned sensor's classifier (cfd_get_sweep_variant, dir 4)
+CLASSIFIERS = {0: "mma.sync", 1: "tcgen05"}
 
 # Algorithmic work per node of each kernel, counted from the method's
 # operations (FMA = 2 flops; division, square root, power = 1):
@@ -384,6 +386,8 @@ def run_form(args, form, U, met, params, world, local, dt):
     prof = s.profile_stage(3)
     variants = {"visc": s.sweep_variant(0), "xi": s.sweep_variant(3), "eta": s.sweep_variant(1),
                 "zeta": s.sweep_variant(2)}
+    if FORMS[form]["learned"]:
+        variants["classifier"] = CLASSIFIERS[s.sweep_variant(4)[0]]
     s.close()
     r = dict(value=value, ms=ms, launches=launches, clocks=clk, class_fraction=[float(x) for x in frac],
              e2e=job_throughput(world, N, args.steps, e2e_s), prof=prof, U1=U1, variants=variants)
@@ -491,7 +495,7 @@ def run_ensemble(args, world):
     learned = {"value": job_throughput(world, nodes, args.steps, ms_l * 1e-3), "unit": "point-stage/s",
                "ms_per_step": ms_l / args.steps, "gpu_launches": launches_l,
                "fallback_fraction": bs.sensor_fallbacks() / (3.0 * args.steps * nodes),
-               "kernel_ms": bs.profile_stage(3)}
+               "kernel_ms": bs.profile_stage(3), "classifier": CLASSIFIERS[bs.sweep_variant(4)[0]]}
     bs.close()
     return {"workload": "48 periodic isotropic-turbulence blocks, dims i.i.d. from {32,48,64,96,128}, "
                         "Mt in [0.3,0.7], hybrid, viscous, FP32 bulk / FP64 state",
