@@ -195,7 +195,9 @@ cfd_status cfd_set_blowing(cfd_ctx* ctx, double amp, double x0, double x1, doubl
  * b1[32], b2[32], b3[3] float.  NULL weights switch back to the plain
  * sensor.  On an ensemble the weights apply to every block: one launch per
  * stage walks the zeta columns of all blocks, and cfd_sensor_fallbacks
- * counts the fallbacks of the ensemble's steps over all blocks.
+ * counts the fallbacks of the ensemble's steps over all blocks.  The three
+ * layers run per CTA on the tcgen05 tensor cores (accumulators in tensor
+ * memory) or per warp with mma.sync: cfd_set_sweep_variant, dir 4.
  */
 cfd_status cfd_set_sensor_mlp(cfd_ctx* ctx, const void* weights_bf16, const float* biases,
                               float conf_min);
